@@ -1,0 +1,162 @@
+/*
+ * mergeshuffle.h -- C ABI of the GB300 MergeShuffle library (libmergeshuffle.so).
+ *
+ * MergeShuffle (Bacher, Bodini, Hollender, Lumbroso, arXiv 1508.03167) permutes an array
+ * uniformly at random: split it into q = 2^c base blocks, shuffle each block with Fisher-Yates
+ * (Algorithm 1), then merge adjacent blocks level by level (Algorithm 3) with the random merge
+ * of Algorithm 2 -- coins interleave the two halves until one runs out, and the leftovers are
+ * placed by random insertion.
+ *
+ * Result definition ("MS-Philox v1"). The output is a pure function of (input, n, seed, B):
+ *   - block split of the appendix listing: c = smallest integer with floor(n / 2^c) <= B,
+ *     block i = [floor(n*i/2^c), floor(n*(i+1)/2^c));
+ *   - merge r of level l joins blocks [2pr, 2pr+p) and [2pr+p, 2pr+2p), p = 2^l;
+ *   - the merge interleaves the halves stably (coin t = 0: next unused element of the first half,
+ *     1: of the second half) until a coin asks for an exhausted half at step T; the other half's
+ *     remaining elements follow in order; then for i = T..N-1, swap positions i and m_i,
+ *     m_i uniform in {0..i} (Algorithm 2's second loop);
+ *   - coin t of merge (l, r) is bit t%32 of word (t/32)%4 of Philox4x32-10(counter =
+ *     (t/128, r, 0x10000|l, 0), key = (lo32(seed), hi32(seed)));
+ *   - a uniform draw in [0, R) for stream (tag, level, id, pos) takes b = ceil(log2 R) bits
+ *     per attempt, floor(32/b) attempts per 32-bit word; word j is word pos%4 of
+ *     Philox4x32-10((pos/4, id, tag<<16|level, j)); the first attempt below R is returned.
+ *     Tags: 2 = merge tail (pos = position in the merged range), 3 = base-block Fisher-Yates
+ *     (level 0, id = block index, pos = i of Algorithm 1).
+ * The same definition is implemented independently by the CPU oracle of the test suite.
+ * Changing B changes the result; the fusion depth, launch shape, stream and batching do not.
+ *
+ * Memory. The library never allocates device memory and never synchronises a stream unless
+ * an entry point says so. The caller passes a device workspace of ms_workspace_bytes() bytes
+ * (256-byte aligned); it holds the second ping-pong buffer of n*w bytes plus O(n/4096 + tails)
+ * bytes of plan scratch. Total device footprint: 2*n*w bytes + scratch.
+ *
+ * Errors. Argument errors are returned synchronously. Launch failures return MS_ERR_CUDA
+ * (the CUDA error is not cleared). Nothing traps on the device.
+ */
+#ifndef MERGESHUFFLE_H
+#define MERGESHUFFLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_INVALID = 1,     /* bad argument: n, w, B, pointer alignment, workspace too small */
+  MS_ERR_UNSUPPORTED = 2, /* valid request this build does not handle (e.g. B > MS_MAX_B) */
+  MS_ERR_NOMEM = 3,       /* a host-side staging allocation failed */
+  MS_ERR_CUDA = 4,        /* a CUDA call or launch failed */
+  MS_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up (batched form) */
+} ms_status;
+
+/* Largest cutoff B the shared-memory base-block kernel accepts. */
+#define MS_MAX_B 4096u
+
+/* cudaStream_t, passed as an opaque pointer (NULL = the legacy default stream). */
+typedef void *ms_stream_t;
+
+/* Flags (ms_params.flags). */
+#define MS_FLAG_TAIL_SEQUENTIAL 0x1u /* merge tails: one thread per merge, in place (slow path;
+                                        the result is identical) */
+#define MS_FLAG_PROFILE 0x2u         /* time every kernel of the call with CUDA events on its
+                                        stream; read with ms_profile_read */
+
+typedef struct {
+  uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B) */
+  int32_t fuse_depth;  /* merge levels done in shared memory per tile; -1 = automatic */
+  uint32_t flags;      /* MS_FLAG_* */
+  uint32_t tile_bytes; /* shared-memory bytes per tile buffer for the automatic fusion depth;
+                          0 = default (48 KiB) */
+} ms_params;
+
+/* The resolved execution plan of one call (informational; filled by ms_plan_info). */
+typedef struct {
+  uint64_t n;
+  uint32_t w;
+  uint32_t B;
+  uint32_t c;            /* levels: q = 2^c base blocks */
+  uint32_t fuse_depth;   /* d: levels 0..d-1 run in shared memory inside the base-block kernel */
+  uint32_t hbm_levels;   /* c - d merge levels that stream through HBM */
+  uint32_t passes;       /* HBM read+write passes over the array: 1 + hbm_levels (0 if n <= 1) */
+  uint64_t tiles;        /* CTAs of the base-block kernel */
+  uint64_t tile_max;     /* largest tile (elements) */
+  size_t workspace_bytes;
+  uint32_t kernel_launches; /* kernels this library launches for one call */
+  uint32_t reserved;
+} ms_plan;
+
+/* Per-kernel-class timing accumulated over calls made with MS_FLAG_PROFILE. */
+#define MS_PROFILE_KINDS 16
+typedef struct {
+  uint32_t kinds;                        /* number of valid entries */
+  char names[MS_PROFILE_KINDS][24];      /* "leaf", "count", "scan", ..., "gather", ... */
+  uint64_t launches[MS_PROFILE_KINDS];   /* launches recorded */
+  double ms[MS_PROFILE_KINDS];           /* summed event-to-event milliseconds */
+} ms_profile;
+
+/* Default parameters: B = 1024, automatic fusion depth, no flags. */
+void ms_default_params(ms_params *p);
+
+/* Plan for (n, w, p); returns MS_ERR_INVALID / MS_ERR_UNSUPPORTED for bad arguments. */
+ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *p, ms_plan *out);
+
+/* Workspace bytes ms_shuffle / ms_perm need for (n, w, p); 0 if the arguments are invalid. */
+size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *p);
+
+/*
+ * Permute d_data[0..n) in place, uniformly at random (Algorithm 3 of the paper), stream-ordered.
+ *   d_data  device pointer to n elements of w bytes (w in {4, 8, 16}); w-byte aligned
+ *           (16-byte aligned for w = 16). Elements are moved as opaque w-byte records.
+ *   n       0 <= n <= 2^32 - 1 (the paper's 32-bit n); n <= 1 returns MS_OK and launches
+ *           nothing.
+ *   seed    64-bit key of every Philox stream.
+ *   d_ws    device workspace of at least ms_workspace_bytes(n, w, p) bytes, 256-byte aligned;
+ *           owned by the caller, contents ignored on entry, scratch on exit.
+ *   p       parameters (NULL = ms_default_params).
+ *   stream  CUDA stream; the call only enqueues work.
+ */
+ms_status ms_shuffle(void *d_data, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,
+                     size_t ws_bytes, const ms_params *p, ms_stream_t stream);
+
+/*
+ * Fill d_out[0..n) with a uniformly random permutation of 0..n-1 (the problem statement of the
+ * paper's introduction): the result equals ms_shuffle applied to the identity with the same
+ * (n, seed, B), but the first pass generates the identity instead of reading it.
+ *   d_out   device pointer to n uint32 values, 4-byte aligned.
+ *   Other arguments as for ms_shuffle with w = 4.
+ */
+ms_status ms_perm(uint32_t *d_out, uint64_t n, uint64_t seed, void *d_ws, size_t ws_bytes,
+                  const ms_params *p, ms_stream_t stream);
+
+/*
+ * End-to-end form for callers whose data lives in host memory: copy h_data (n*w bytes; pinned
+ * memory gives full copy bandwidth) into the device workspace, shuffle it there, copy it back,
+ * and synchronise the stream before returning.
+ *   d_ws   device workspace of at least ms_host_workspace_bytes(n, w, p) bytes (it holds both
+ *          ping-pong buffers).
+ */
+size_t ms_host_workspace_bytes(uint64_t n, uint32_t w, const ms_params *p);
+ms_status ms_shuffle_host(void *h_data, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,
+                          size_t ws_bytes, const ms_params *p, ms_stream_t stream);
+ms_status ms_perm_host(uint32_t *h_out, uint64_t n, uint64_t seed, void *d_ws, size_t ws_bytes,
+                       const ms_params *p, ms_stream_t stream);
+
+/*
+ * Collect the timings of every launch recorded since the last reset (waits for the recorded
+ * events; process-wide state, not thread-safe) and optionally reset the record.
+ */
+ms_status ms_profile_read(ms_profile *out, int reset);
+
+/* Human-readable name of a status code (static storage). */
+const char *ms_status_string(ms_status s);
+
+/* Library version string (static storage). */
+const char *ms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MERGESHUFFLE_H */

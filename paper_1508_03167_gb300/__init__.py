@@ -1,0 +1,272 @@
+"""GB300 MergeShuffle (arXiv 1508.03167): Python binding of libmergeshuffle.
+
+The binding only marshals arguments: every step of the shuffle runs in the CUDA kernels of the
+shared library (built in-tree for sm_103a; see ``_build.py``). PyTorch supplies device memory and
+streams. The C entry points are exposed under their C names (``ms_shuffle``, ``ms_perm``, ...);
+``shuffle_`` / ``perm`` / ``shuffle_host`` are conveniences over them for torch tensors.
+There is no CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
+    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_MAX_B", "MsParams",
+    "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
+    "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
+    "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
+    "ms_status_string", "ms_version", "params", "plan", "shuffle_", "perm", "shuffle_host",
+    "perm_host", "workspace",
+]
+
+MS_OK, MS_ERR_INVALID, MS_ERR_UNSUPPORTED, MS_ERR_NOMEM, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
+MS_FLAG_TAIL_SEQUENTIAL = 0x1
+MS_FLAG_PROFILE = 0x2
+MS_MAX_B = 4096
+
+
+class MsParams(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_uint32), ("fuse_depth", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("tile_bytes", ctypes.c_uint32)]
+
+
+class MsPlan(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("w", ctypes.c_uint32), ("B", ctypes.c_uint32),
+                ("c", ctypes.c_uint32), ("fuse_depth", ctypes.c_uint32),
+                ("hbm_levels", ctypes.c_uint32), ("passes", ctypes.c_uint32),
+                ("tiles", ctypes.c_uint64), ("tile_max", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class MsProfile(ctypes.Structure):
+    _fields_ = [("kinds", ctypes.c_uint32), ("names", (ctypes.c_char * 24) * 16),
+                ("launches", ctypes.c_uint64 * 16), ("ms", ctypes.c_double * 16)]
+
+    def as_dict(self) -> dict:
+        return {self.names[k].value.decode(): {"launches": int(self.launches[k]),
+                                              "ms": float(self.ms[k])}
+                for k in range(self.kinds)}
+
+
+class MsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what} failed: {ms_status_string(status)} ({status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    from . import _build
+
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) libmergeshuffle.so and declare its C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import _build
+
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32, u64, i32, sz, vp = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                 ctypes.c_size_t, ctypes.c_void_p)
+        P = ctypes.POINTER(MsParams)
+        L.ms_default_params.argtypes = [P]
+        L.ms_default_params.restype = None
+        L.ms_plan_info.argtypes = [u64, u32, P, ctypes.POINTER(MsPlan)]
+        L.ms_plan_info.restype = i32
+        L.ms_workspace_bytes.argtypes = [u64, u32, P]
+        L.ms_workspace_bytes.restype = sz
+        L.ms_shuffle.argtypes = [vp, u64, u32, u64, vp, sz, P, vp]
+        L.ms_shuffle.restype = i32
+        L.ms_perm.argtypes = [vp, u64, u64, vp, sz, P, vp]
+        L.ms_perm.restype = i32
+        L.ms_host_workspace_bytes.argtypes = [u64, u32, P]
+        L.ms_host_workspace_bytes.restype = sz
+        L.ms_shuffle_host.argtypes = [vp, u64, u32, u64, vp, sz, P, vp]
+        L.ms_shuffle_host.restype = i32
+        L.ms_perm_host.argtypes = [vp, u64, u64, vp, sz, P, vp]
+        L.ms_perm_host.restype = i32
+        L.ms_profile_read.argtypes = [ctypes.POINTER(MsProfile), i32]
+        L.ms_profile_read.restype = i32
+        L.ms_status_string.argtypes = [i32]
+        L.ms_status_string.restype = ctypes.c_char_p
+        L.ms_version.argtypes = []
+        L.ms_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+# ------------------------------------------------------------------ C entry points ----------
+def _p(p):
+    return ctypes.byref(p) if p is not None else None
+
+
+def ms_default_params() -> MsParams:
+    p = MsParams()
+    lib().ms_default_params(ctypes.byref(p))
+    return p
+
+
+def ms_plan_info(n: int, w: int, p: MsParams | None = None) -> MsPlan:
+    out = MsPlan()
+    st = lib().ms_plan_info(n, w, _p(p), ctypes.byref(out))
+    if st != MS_OK:
+        raise MsError(st, "ms_plan_info")
+    return out
+
+
+def ms_workspace_bytes(n: int, w: int, p: MsParams | None = None) -> int:
+    return int(lib().ms_workspace_bytes(n, w, _p(p)))
+
+
+def ms_host_workspace_bytes(n: int, w: int, p: MsParams | None = None) -> int:
+    return int(lib().ms_host_workspace_bytes(n, w, _p(p)))
+
+
+def ms_shuffle(d_data: int, n: int, w: int, seed: int, d_ws: int, ws_bytes: int,
+               p: MsParams | None = None, stream: int = 0) -> int:
+    return int(lib().ms_shuffle(d_data, n, w, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_perm(d_out: int, n: int, seed: int, d_ws: int, ws_bytes: int,
+            p: MsParams | None = None, stream: int = 0) -> int:
+    return int(lib().ms_perm(d_out, n, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_shuffle_host(h_data: int, n: int, w: int, seed: int, d_ws: int, ws_bytes: int,
+                    p: MsParams | None = None, stream: int = 0) -> int:
+    return int(lib().ms_shuffle_host(h_data, n, w, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_perm_host(h_out: int, n: int, seed: int, d_ws: int, ws_bytes: int,
+                 p: MsParams | None = None, stream: int = 0) -> int:
+    return int(lib().ms_perm_host(h_out, n, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_profile_read(reset: bool = True) -> MsProfile:
+    out = MsProfile()
+    st = lib().ms_profile_read(ctypes.byref(out), 1 if reset else 0)
+    if st != MS_OK:
+        raise MsError(st, "ms_profile_read")
+    return out
+
+
+def profile(reset: bool = True) -> dict:
+    """Per-kernel-class launch counts and summed milliseconds of profiled calls."""
+    return ms_profile_read(reset).as_dict()
+
+
+def ms_status_string(st: int) -> str:
+    return lib().ms_status_string(st).decode()
+
+
+def ms_version() -> str:
+    return lib().ms_version().decode()
+
+
+# ------------------------------------------------------------------ torch conveniences -------
+def params(B: int = 1024, fuse_depth: int = -1, flags: int = 0, tile_bytes: int = 0) -> MsParams:
+    return MsParams(B, fuse_depth, flags, tile_bytes)
+
+
+def plan(n: int, w: int = 4, **kw) -> dict:
+    return ms_plan_info(n, w, params(**kw)).as_dict()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _width(x) -> tuple[int, int]:
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    n = x.shape[0] if x.dim() > 0 else 0
+    if n == 0:
+        return 0, 4
+    w = x.numel() * x.element_size() // n
+    return n, w
+
+
+def workspace(n: int, w: int = 4, device=None, host: bool = False, **kw):
+    """Allocate a device workspace (torch's caching allocator) for a call with these sizes."""
+    import torch
+
+    p = params(**kw)
+    nbytes = ms_host_workspace_bytes(n, w, p) if host else ms_workspace_bytes(n, w, p)
+    if nbytes == 0:
+        raise MsError(MS_ERR_INVALID, "workspace sizing")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def shuffle_(x, seed: int, B: int = 1024, fuse_depth: int = -1, flags: int = 0,
+             tile_bytes: int = 0, ws=None, stream=None):
+    """Permute the rows of a contiguous CUDA tensor in place (rows of 4, 8 or 16 bytes)."""
+    n, w = _width(x)
+    p = params(B, fuse_depth, flags, tile_bytes)
+    if n == 0:
+        return x
+    if ws is None:
+        ws = workspace(n, w, x.device, B=B, fuse_depth=fuse_depth, flags=flags,
+                       tile_bytes=tile_bytes)
+    st = ms_shuffle(x.data_ptr(), n, w, seed, ws.data_ptr(), ws.numel(), p, _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_shuffle")
+    return x
+
+
+def perm(n: int, seed: int, B: int = 1024, fuse_depth: int = -1, flags: int = 0,
+         tile_bytes: int = 0, device=None, out=None, ws=None, stream=None):
+    """A uniformly random permutation of 0..n-1 as an int32 CUDA tensor (uint32 bit pattern)."""
+    import torch
+
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=device or "cuda")
+    p = params(B, fuse_depth, flags, tile_bytes)
+    if ws is None:
+        ws = workspace(n, 4, out.device, B=B, fuse_depth=fuse_depth, flags=flags,
+                       tile_bytes=tile_bytes)
+    st = ms_perm(out.data_ptr(), n, seed, ws.data_ptr(), ws.numel(), p, _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_perm")
+    return out
+
+
+def shuffle_host(h, seed: int, ws, B: int = 1024, fuse_depth: int = -1, flags: int = 0,
+                 tile_bytes: int = 0, stream=None):
+    """Shuffle a contiguous host tensor (ideally pinned) through the device; synchronous."""
+    n, w = _width(h)
+    st = ms_shuffle_host(h.data_ptr(), n, w, seed, ws.data_ptr(), ws.numel(),
+                         params(B, fuse_depth, flags, tile_bytes), _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_shuffle_host")
+    return h
+
+
+def perm_host(h_out, seed: int, ws, B: int = 1024, fuse_depth: int = -1, flags: int = 0,
+              tile_bytes: int = 0, stream=None):
+    n = h_out.shape[0]
+    st = ms_perm_host(h_out.data_ptr(), n, seed, ws.data_ptr(), ws.numel(),
+                      params(B, fuse_depth, flags, tile_bytes), _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_perm_host")
+    return h_out

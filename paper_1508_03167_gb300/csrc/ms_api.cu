@@ -1,0 +1,384 @@
+// ms_api.cu -- the C ABI of libmergeshuffle (declared in include/mergeshuffle.h) and the host
+// planner: block split and cutoff rule of the appendix listing of arXiv 1508.03167, the choice
+// of how many low merge levels run inside shared memory, and the workspace layout.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "mergeshuffle.h"
+#include "ms_plan.h"
+
+namespace msk {
+namespace {
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+uint64_t ceil_scaled(uint64_t n, uint32_t shift, uint32_t c) {
+  // ceil(n * 2^shift / 2^c) for shift <= c
+  const uint64_t q = 1ull << c;
+  return ((n << shift) + q - 1) >> c;
+}
+
+uint32_t unit_capacity(uint64_t n, uint32_t c, uint32_t d) {
+  uint32_t cap = 0;
+  for (uint32_t lam = 0; lam < d; ++lam) {
+    const uint64_t Mt = 1ull << (d - lam - 1);
+    const uint64_t Nmax = ceil_scaled(n, lam + 1, c);
+    const uint64_t units = Mt * ((Nmax + 31) / 32);
+    if (units > cap) cap = static_cast<uint32_t>(units);
+  }
+  return cap;
+}
+
+size_t leaf_smem_bytes(uint64_t tile_max, uint32_t w, uint32_t d, uint32_t unit_cap) {
+  return round_up((d > 0 ? 2 : 1) * tile_max * w + 2ull * unit_cap * 4, 16);
+}
+
+}  // namespace
+
+int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t tile_bytes,
+              uint32_t flags, Plan *out) {
+  Plan p;
+  if (w != 4 && w != 8 && w != 16) return 1;
+  if (B == 0) return 1;
+  if (n > 0xFFFFFFFFull) return 1;
+  if (B > kMaxB) return 2;
+  p.n = n;
+  p.w = w;
+  p.B = B;
+  p.flags = flags;
+  if (tile_bytes == 0) tile_bytes = kDefaultTileBytes;
+  uint32_t c = 0;
+  while ((n >> c) > B) ++c;
+  p.c = c;
+  p.q = 1ull << c;
+  if (n <= 1) {
+    p.ws_bytes = 256;
+    *out = p;
+    return 0;
+  }
+  // fusion depth: the deepest d whose tile fits the shared-memory budget
+  const uint32_t dmax = c < kMaxFuse ? c : kMaxFuse;
+  uint32_t d = 0;
+  if (fuse_depth < 0) {
+    for (uint32_t t = 0; t <= dmax; ++t) {
+      if (ceil_scaled(n, t, c) * w <= tile_bytes &&
+          leaf_smem_bytes(ceil_scaled(n, t, c), w, t, unit_capacity(n, c, t)) <= kSmemLimit)
+        d = t;
+    }
+  } else {
+    d = static_cast<uint32_t>(fuse_depth) < dmax ? static_cast<uint32_t>(fuse_depth) : dmax;
+    while (d > 0 &&
+           leaf_smem_bytes(ceil_scaled(n, d, c), w, d, unit_capacity(n, c, d)) > kSmemLimit)
+      --d;
+  }
+  p.d = d;
+  p.tiles = p.q >> d;
+  p.tile_max = static_cast<uint32_t>(ceil_scaled(n, d, c));
+  p.unit_cap = unit_capacity(n, c, d);
+  p.leaf_smem = leaf_smem_bytes(p.tile_max, w, d, p.unit_cap);
+  if (p.leaf_smem > kSmemLimit) return 2;
+
+  // HBM levels d..c-1
+  p.nlevels = c - d;
+  uint64_t zc_cap = 0, minfo_cap = 0, kcap_max = 0;
+  uint32_t hbits_max = 0;
+  for (uint32_t i = 0; i < p.nlevels; ++i) {
+    LevelPlan &lv = p.levels[i];
+    lv.level = d + i;
+    const uint64_t M = p.q >> (lv.level + 1);
+    const uint64_t Nmax = ceil_scaled(n, lv.level + 1, c);
+    lv.M = static_cast<uint32_t>(M);
+    lv.Nmax = static_cast<uint32_t>(Nmax);
+    lv.J = static_cast<uint32_t>((Nmax + kChunk - 1) / kChunk);
+    // Tail capacity: E[N - T] is about sqrt(2N/pi) per merge and its spread about sqrt(N);
+    // the sum over the level's merges is bounded by the mean plus eight spreads.
+    const double per = std::ceil(std::sqrt(2.0 * static_cast<double>(Nmax) / 3.14159265358979)) + 2.0;
+    double kc = static_cast<double>(M) * per +
+                8.0 * std::ceil(std::sqrt(static_cast<double>(M) * static_cast<double>(Nmax))) +
+                1024.0;
+    const double cap_all = static_cast<double>(M) * static_cast<double>(Nmax);
+    if (kc > cap_all) kc = cap_all;
+    lv.kcap = static_cast<uint32_t>(kc);
+    uint32_t hb = 10;
+    while ((1ull << hb) < 2ull * lv.kcap) ++hb;
+    lv.hbits = hb;
+    zc_cap = std::max<uint64_t>(zc_cap, M * lv.J);
+    minfo_cap = std::max<uint64_t>(minfo_cap, M);
+    kcap_max = std::max<uint64_t>(kcap_max, lv.kcap);
+    hbits_max = std::max(hbits_max, hb);
+  }
+  p.zc_cap = static_cast<uint32_t>(zc_cap);
+  p.minfo_cap = static_cast<uint32_t>(minfo_cap);
+  p.kcap_max = static_cast<uint32_t>(kcap_max);
+  p.hbits_max = hbits_max;
+
+  size_t off = 0;
+  p.off_buf = off;
+  if (p.nlevels > 0) off += round_up(n * w, 256);
+  if (p.nlevels > 0) {
+    p.off_zc = off;     off += round_up(zc_cap * 4, 256);
+    p.off_minfo = off;  off += round_up(minfo_cap * 16, 256);
+    p.off_ctrl = off;   off += 256;
+    p.off_mv = off;     off += round_up(kcap_max * 4, 256);
+    p.off_hkeys = off;  off += round_up((1ull << hbits_max) * 8, 256);
+    p.off_hvals = off;  off += round_up((1ull << hbits_max) * 4, 256);
+    p.off_pdst = off;   off += round_up(2 * kcap_max * 4, 256);
+    p.off_psrc = off;   off += round_up(2 * kcap_max * 4, 256);
+    p.off_ptmp = off;   off += round_up(2 * kcap_max * w, 256);
+  }
+  p.ws_bytes = off > 256 ? off : 256;
+  *out = p;
+  return 0;
+}
+
+}  // namespace msk
+
+using msk::Plan;
+
+namespace {
+
+const char *const kKindNames[msk::kKindNum] = {
+    "leaf", "count", "scan", "kscan", "hash_clear", "tail_insert", "tail_resolve",
+    "gather", "tail_sequential", "patch_read", "patch_write"};
+
+// Process-wide event recorder used when MS_FLAG_PROFILE is set.
+class EventProfiler final : public msk::Prof {
+ public:
+  void begin(int kind, cudaStream_t s) override {
+    Rec r;
+    r.kind = kind;
+    r.a = take();
+    r.b = take();
+    cudaEventRecord(r.a, s);
+    recs_.push_back(r);
+  }
+  void end(cudaStream_t s) override {
+    if (!recs_.empty()) cudaEventRecord(recs_.back().b, s);
+  }
+  ms_status read(ms_profile *out, bool reset) {
+    std::memset(out, 0, sizeof *out);
+    out->kinds = msk::kKindNum;
+    for (int k = 0; k < msk::kKindNum; ++k)
+      std::strncpy(out->names[k], kKindNames[k], sizeof out->names[k] - 1);
+    for (const Rec &r : recs_) {
+      if (cudaEventSynchronize(r.b) != cudaSuccess) return MS_ERR_CUDA;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return MS_ERR_CUDA;
+      out->launches[r.kind] += 1;
+      out->ms[r.kind] += ms;
+    }
+    if (reset) {
+      for (const Rec &r : recs_) {
+        pool_.push_back(r.a);
+        pool_.push_back(r.b);
+      }
+      recs_.clear();
+    }
+    return MS_OK;
+  }
+
+ private:
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  cudaEvent_t take() {
+    if (!pool_.empty()) {
+      cudaEvent_t e = pool_.back();
+      pool_.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  std::vector<Rec> recs_;
+  std::vector<cudaEvent_t> pool_;
+};
+
+EventProfiler &profiler() {
+  static EventProfiler p;
+  return p;
+}
+std::mutex g_prof_mu;
+
+ms_params resolve(const ms_params *p) {
+  ms_params r;
+  ms_default_params(&r);
+  if (p) r = *p;
+  return r;
+}
+
+ms_status plan_for(uint64_t n, uint32_t w, const ms_params *p, Plan *plan) {
+  const ms_params r = resolve(p);
+  const int rc = msk::make_plan(n, w, r.B, r.fuse_depth, r.tile_bytes, r.flags, plan);
+  if (rc == 1) return MS_ERR_INVALID;
+  if (rc == 2) return MS_ERR_UNSUPPORTED;
+  return MS_OK;
+}
+
+msk::Buffers buffers_for(const Plan &p, void *data, void *ws) {
+  char *base = static_cast<char *>(ws);
+  msk::Buffers b;
+  b.data = data;
+  b.other = base + p.off_buf;
+  b.zc = reinterpret_cast<uint32_t *>(base + p.off_zc);
+  b.minfo = reinterpret_cast<uint4 *>(base + p.off_minfo);
+  b.ctrl = reinterpret_cast<uint32_t *>(base + p.off_ctrl);
+  b.mv = reinterpret_cast<uint32_t *>(base + p.off_mv);
+  b.hkeys = reinterpret_cast<unsigned long long *>(base + p.off_hkeys);
+  b.hvals = reinterpret_cast<uint32_t *>(base + p.off_hvals);
+  b.pdst = reinterpret_cast<uint32_t *>(base + p.off_pdst);
+  b.psrc = reinterpret_cast<uint32_t *>(base + p.off_psrc);
+  b.ptmp = base + p.off_ptmp;
+  return b;
+}
+
+ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
+              size_t ws_bytes, const ms_params *params, cudaStream_t s) {
+  Plan p;
+  const ms_status st = plan_for(n, w, params, &p);
+  if (st != MS_OK) return st;
+  if (n <= 1) {
+    if (perm && n == 1) {
+      const uint32_t zero = 0;
+      if (cudaMemcpyAsync(data, &zero, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MS_ERR_CUDA;
+      // the source lives on this stack frame: wait until the copy has consumed it
+      if (cudaStreamSynchronize(s) != cudaSuccess) return MS_ERR_CUDA;
+    }
+    return MS_OK;
+  }
+  if (data == nullptr) return MS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(data) % w != 0) return MS_ERR_INVALID;
+  if (ws_bytes < p.ws_bytes) return MS_ERR_INVALID;
+  if (p.ws_bytes > 256 && (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
+    return MS_ERR_INVALID;
+  const msk::Buffers b = buffers_for(p, data, ws);
+  std::unique_lock<std::mutex> prof_lock(g_prof_mu, std::defer_lock);
+  if (p.flags & MS_FLAG_PROFILE) {
+    prof_lock.lock();
+    p.prof = &profiler();
+  }
+  void *cur = (p.nlevels % 2 == 0) ? data : b.other;
+  if (msk::launch_leaf(p, data, cur, perm, seed, s) != cudaSuccess) return MS_ERR_CUDA;
+  for (uint32_t i = 0; i < p.nlevels; ++i) {
+    void *dst = (cur == data) ? b.other : data;
+    if (msk::launch_level(p, p.levels[i], cur, dst, b, seed, s) != cudaSuccess)
+      return MS_ERR_CUDA;
+    cur = dst;
+  }
+  return MS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ms_default_params(ms_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->B = 1024;
+  p->fuse_depth = -1;
+  p->flags = 0;
+  p->tile_bytes = 0;
+}
+
+ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *params, ms_plan *out) {
+  if (!out) return MS_ERR_INVALID;
+  Plan p;
+  const ms_status st = plan_for(n, w, params, &p);
+  if (st != MS_OK) return st;
+  std::memset(out, 0, sizeof *out);
+  out->n = p.n;
+  out->w = p.w;
+  out->B = p.B;
+  out->c = p.c;
+  out->fuse_depth = p.d;
+  out->hbm_levels = p.nlevels;
+  out->passes = n <= 1 ? 0u : 1u + p.nlevels;
+  out->tiles = n <= 1 ? 0u : p.tiles;
+  out->tile_max = n <= 1 ? n : p.tile_max;
+  out->workspace_bytes = p.ws_bytes;
+  out->kernel_launches = n <= 1 ? 0u : 1u + 9u * p.nlevels;
+  return MS_OK;
+}
+
+ms_status ms_profile_read(ms_profile *out, int reset) {
+  if (!out) return MS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  return profiler().read(out, reset != 0);
+}
+
+size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *params) {
+  Plan p;
+  if (plan_for(n, w, params, &p) != MS_OK) return 0;
+  return p.ws_bytes;
+}
+
+ms_status ms_shuffle(void *d_data, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,
+                     size_t ws_bytes, const ms_params *p, ms_stream_t stream) {
+  return run(d_data, false, n, w, seed, d_ws, ws_bytes, p, static_cast<cudaStream_t>(stream));
+}
+
+ms_status ms_perm(uint32_t *d_out, uint64_t n, uint64_t seed, void *d_ws, size_t ws_bytes,
+                  const ms_params *p, ms_stream_t stream) {
+  return run(d_out, true, n, 4, seed, d_ws, ws_bytes, p, static_cast<cudaStream_t>(stream));
+}
+
+size_t ms_host_workspace_bytes(uint64_t n, uint32_t w, const ms_params *params) {
+  const size_t inner = ms_workspace_bytes(n, w, params);
+  if (inner == 0) return 0;
+  return msk::round_up(n * w, 256) + inner;
+}
+
+static ms_status host_form(void *h, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,
+                           size_t ws_bytes, const ms_params *params, cudaStream_t s) {
+  const size_t need = ms_host_workspace_bytes(n, w, params);
+  if (need == 0) return MS_ERR_INVALID;
+  if (n == 0) return MS_OK;
+  if (h == nullptr || d_ws == nullptr || ws_bytes < need) return MS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) return MS_ERR_INVALID;
+  const size_t front = msk::round_up(n * w, 256);
+  void *d_buf = d_ws;
+  void *inner = static_cast<char *>(d_ws) + front;
+  if (!perm && cudaMemcpyAsync(d_buf, h, n * w, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return MS_ERR_CUDA;
+  const ms_status st = run(d_buf, perm, n, w, seed, inner, ws_bytes - front, params, s);
+  if (st != MS_OK) return st;
+  if (cudaMemcpyAsync(h, d_buf, n * w, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return MS_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MS_ERR_CUDA;
+  return MS_OK;
+}
+
+ms_status ms_shuffle_host(void *h_data, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,
+                          size_t ws_bytes, const ms_params *p, ms_stream_t stream) {
+  return host_form(h_data, false, n, w, seed, d_ws, ws_bytes, p,
+                   static_cast<cudaStream_t>(stream));
+}
+
+ms_status ms_perm_host(uint32_t *h_out, uint64_t n, uint64_t seed, void *d_ws, size_t ws_bytes,
+                       const ms_params *p, ms_stream_t stream) {
+  return host_form(h_out, true, n, 4, seed, d_ws, ws_bytes, p,
+                   static_cast<cudaStream_t>(stream));
+}
+
+const char *ms_status_string(ms_status s) {
+  switch (s) {
+    case MS_OK: return "MS_OK";
+    case MS_ERR_INVALID: return "MS_ERR_INVALID";
+    case MS_ERR_UNSUPPORTED: return "MS_ERR_UNSUPPORTED";
+    case MS_ERR_NOMEM: return "MS_ERR_NOMEM";
+    case MS_ERR_CUDA: return "MS_ERR_CUDA";
+    case MS_ERR_TIMEOUT: return "MS_ERR_TIMEOUT";
+  }
+  return "MS_ERR_UNKNOWN";
+}
+
+const char *ms_version(void) { return "mergeshuffle-gb300 0.1 (MS-Philox v1, sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+"""Host-side checks of the C ABI (no GPU compute): the library loads, exports every entry point
+include/mergeshuffle.h declares, plans the configurations of the workloads correctly and rejects
+bad arguments synchronously. Also checks that the oracle and the CUDA path share no code."""
+from __future__ import annotations
+
+import os
+import re
+
+import pytest
+
+import paper_1508_03167_gb300 as ms
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions() -> list[str]:
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(ms_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ms.lib()
+    names = _declared_functions()
+    assert "ms_shuffle" in names and "ms_perm" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings():
+    assert "MS-Philox v1" in ms.ms_version()
+    assert ms.ms_status_string(ms.MS_OK) == "MS_OK"
+    assert ms.ms_status_string(ms.MS_ERR_INVALID) == "MS_ERR_INVALID"
+
+
+def test_default_params():
+    p = ms.ms_default_params()
+    assert p.B == 1024 and p.fuse_depth == -1 and p.flags == 0
+
+
+@pytest.mark.parametrize("n,B,c", [(2**20, 1024, 10), (2**30, 1024, 20), (300_000_017, 1024, 19),
+                                   (2049, 1024, 1), (1024, 1024, 0), (5, 1, 2), (8, 1, 3)])
+def test_plan_levels_follow_the_cutoff_rule(n, B, c):
+    p = ms.ms_plan_info(n, 4, ms.params(B=B))
+    assert p.c == c
+    assert p.fuse_depth <= c
+    assert p.hbm_levels == c - p.fuse_depth
+    assert p.passes == 1 + p.hbm_levels
+    assert p.tiles == (1 << c) >> p.fuse_depth
+
+
+def test_plan_fusion_depth_and_workspace():
+    p = ms.ms_plan_info(2**30, 4, ms.params(B=1024))
+    # 48 KiB tiles of 4-byte elements hold 2^13 elements: 8 base blocks of 1024
+    assert p.fuse_depth == 3
+    assert p.tile_max == 8192
+    ws = ms.ms_workspace_bytes(2**30, 4, ms.params(B=1024))
+    assert ws >= 2**30 * 4
+    assert ws < 2**30 * 4 * 1.25
+    assert ms.ms_host_workspace_bytes(2**30, 4, ms.params(B=1024)) >= ws + 2**30 * 4
+    # forced depth is honoured (capped by c)
+    assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=0)).fuse_depth == 0
+    assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2)).fuse_depth == 2
+    assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9)).fuse_depth == 2
+
+
+def test_plan_records():
+    p = ms.ms_plan_info(300_000_017, 16, ms.params(B=1024))
+    assert p.c == 19 and p.w == 16
+    assert p.tile_max * 16 <= 48 * 1024
+
+
+@pytest.mark.parametrize("n,w,B,status", [(100, 3, 16, ms.MS_ERR_INVALID),
+                                          (100, 4, 0, ms.MS_ERR_INVALID),
+                                          (2**32, 4, 16, ms.MS_ERR_INVALID),
+                                          (100, 4, 5000, ms.MS_ERR_UNSUPPORTED)])
+def test_invalid_arguments_are_rejected_synchronously(n, w, B, status):
+    with pytest.raises(ms.MsError) as e:
+        ms.ms_plan_info(n, w, ms.params(B=B))
+    assert e.value.status == status
+    assert ms.ms_workspace_bytes(n, w, ms.params(B=B)) == 0
+    # the compute entry points validate before touching any device state
+    assert ms.ms_shuffle(0x1000, n, w, 1, 0, 0, ms.params(B=B), 0) == status
+
+
+def test_small_workspace_is_rejected():
+    need = ms.ms_workspace_bytes(10**6, 4, ms.params(B=64))
+    assert ms.ms_shuffle(0x1000, 10**6, 4, 1, 0x10000, need - 1, ms.params(B=64), 0) == \
+        ms.MS_ERR_INVALID
+    assert ms.ms_shuffle(0x1002, 10**6, 4, 1, 0x10000, need, ms.params(B=64), 0) == \
+        ms.MS_ERR_INVALID  # misaligned data
+
+
+def test_trivial_sizes_launch_nothing():
+    # n <= 1 needs no device work at all for shuffle
+    assert ms.ms_shuffle(0, 0, 4, 1, 0, 0, None, 0) == ms.MS_OK
+    assert ms.ms_shuffle(0x1000, 1, 16, 1, 0, 0, None, 0) == ms.MS_OK
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    pkg = os.path.join(ROOT, "paper_1508_03167_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "ms_oracle" not in text, f
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_1508_03167_gb300" not in text, f
+            assert "mergeshuffle.h" not in text, f

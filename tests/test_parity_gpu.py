@@ -1,0 +1,118 @@
+"""GPU <-> oracle parity through the C ABI: bit-exact on every seed, size, cutoff and width.
+
+Sizes span several tiles and ragged tails (non-power-of-two n gives base blocks of two sizes and
+uneven merge halves at every level). The result must not depend on the fusion depth, the tile
+size or the tail strategy: only (input, n, seed, B) define it."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1508_03167_gb300 as ms
+from paper_1508_03167_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def gpu_perm(n: int, seed: int, B: int, fuse_depth: int = -1, flags: int = 0,
+             tile_bytes: int = 0) -> np.ndarray:
+    torch = _torch()
+    p = ms.params(B, fuse_depth, flags, tile_bytes)
+    out = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    nbytes = ms.ms_workspace_bytes(n, 4, p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_perm(out.data_ptr(), n, seed, ws.data_ptr(), nbytes, p,
+                    torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    return out[:n].cpu().numpy().view(np.uint32)
+
+
+def gpu_shuffle(arr: np.ndarray, seed: int, B: int, fuse_depth: int = -1, flags: int = 0,
+                tile_bytes: int = 0) -> np.ndarray:
+    torch = _torch()
+    n = arr.shape[0]
+    w = arr.nbytes // n
+    p = ms.params(B, fuse_depth, flags, tile_bytes)
+    x = torch.from_numpy(arr.view(np.uint8).reshape(n, w).copy()).cuda()
+    nbytes = ms.ms_workspace_bytes(n, w, p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_shuffle(x.data_ptr(), n, w, seed, ws.data_ptr(), nbytes, p,
+                       torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().view(arr.dtype).reshape(arr.shape)
+
+
+SIZES = [2, 3, 7, 31, 32, 33, 100, 1000, 1023, 1024, 1025, 2047, 2049, 4097, 10007, 65537,
+         100003, 262147]
+
+
+@pytest.mark.parametrize("B", [1, 3, 16, 64, 1024])
+def test_perm_matches_oracle_sweep(B):
+    for n in SIZES:
+        for seed in (0, 7, 2**63 + 5):
+            want, _ = oracle.perm(n, seed, B)
+            got = gpu_perm(n, seed, B)
+            assert np.array_equal(got, want), (n, B, seed)
+
+
+def test_perm_c1_workload():
+    """perm(2^20) of the identity, seed 1, B = 1024 (the small configuration)."""
+    want, _ = oracle.perm(1 << 20, 1, 1024)
+    got = gpu_perm(1 << 20, 1, 1024)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,B", [(1 << 20, 1024), (100003, 16), (262147, 5), (4133, 1)])
+def test_result_independent_of_fusion_depth_and_tiles(n, B):
+    want, _ = oracle.perm(n, 11, B)
+    for d in (0, 1, 2, 3, 5):
+        assert np.array_equal(gpu_perm(n, 11, B, fuse_depth=d), want), d
+    for tb in (4096, 16384, 98304):
+        assert np.array_equal(gpu_perm(n, 11, B, tile_bytes=tb), want), tb
+
+
+@pytest.mark.parametrize("n,B", [(1 << 20, 1024), (262147, 16), (65537, 1)])
+def test_sequential_tail_path_is_identical(n, B):
+    want, _ = oracle.perm(n, 3, B)
+    got = gpu_perm(n, 3, B, fuse_depth=0, flags=ms.MS_FLAG_TAIL_SEQUENTIAL)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("n,B", [(5, 2), (1000, 3), (4099, 64), (100003, 1024), (300017, 1024)])
+def test_shuffle_widths_match_oracle(w, n, B):
+    if w == 16:
+        arr = inputs.records16(n)
+    elif w == 8:
+        arr = inputs.values_u64(n, 3)
+    else:
+        arr = inputs.identity_u32(n) * np.uint32(2654435761)
+    want, _ = oracle.shuffle(arr, 5, B)
+    got = gpu_shuffle(arr, 5, B)
+    assert np.array_equal(got, want)
+
+
+def test_shuffle_is_data_oblivious_on_gpu():
+    n, B, seed = 300017, 1024, 9
+    rec = inputs.records16(n)
+    p = gpu_perm(n, seed, B)
+    got = gpu_shuffle(rec, seed, B)
+    assert np.array_equal(got, rec[p])
+
+
+def test_edge_sizes():
+    for n in (0, 1):
+        assert gpu_perm(n, 1, 4).tolist() == list(range(n))
+    # n exactly B, B + 1, 2B, 2B + 1
+    for n in (64, 65, 128, 129):
+        want, _ = oracle.perm(n, 2, 64)
+        assert np.array_equal(gpu_perm(n, 2, 64), want)
