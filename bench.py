@@ -1,0 +1,398 @@
+"""Benchmark of the MergeShuffle hot path on GB300 (one JSON line on rank 0).
+
+Workload (default "scale"): one step = perm(n = 2^30) of the uint32 identity plus a shuffle of
+n = 300,000,017 16-byte records {u32 key = index, 12-byte splitmix64 payload}, seed 7, both in
+HBM before the timed region. value = elements permuted per second over both calls (Gelem/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (single-threaded C restatement of the paper) on a bounded
+sample of the same workload. Under torchrun (N > 1) each rank runs an independent replica of
+the workload (the path has no cross-GPU step); the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_PERM = 1 << 30
+N_REC = 300_000_017
+SEED = 7
+DEFAULT_B = {"perm": 64, "rec": 64}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--B-perm", type=int, default=DEFAULT_B["perm"])
+    ap.add_argument("--B-rec", type=int, default=DEFAULT_B["rec"])
+    ap.add_argument("--tile-bytes", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: perm 2^26 + 2^24+17 records (inputs still above L2)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing -----
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks ------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.reader = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        loaded = sorted(sm)
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm -----------------
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1508_03167_gb300 as ms
+    from paper_1508_03167_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    n_perm = (1 << 26) if args.small else N_PERM
+    n_rec = (1 << 24) + 17 if args.small else N_REC
+    seed = SEED + rank
+    flags = ms.MS_FLAG_PROFILE
+    p_perm = ms.params(B=args.B_perm, tile_bytes=args.tile_bytes, flags=flags)
+    p_rec = ms.params(B=args.B_rec, tile_bytes=args.tile_bytes, flags=flags)
+    plan_perm = ms.ms_plan_info(n_perm, 4, p_perm)
+    plan_rec = ms.ms_plan_info(n_rec, 16, p_rec)
+
+    out = torch.empty(n_perm, dtype=torch.int32, device=dev)
+    ws_perm = torch.empty(ms.ms_workspace_bytes(n_perm, 4, p_perm), dtype=torch.uint8, device=dev)
+    rec_host = torch.from_numpy(inputs.records16(n_rec))
+    rec = rec_host.to(dev)
+    ws_rec = torch.empty(ms.ms_workspace_bytes(n_rec, 16, p_rec), dtype=torch.uint8, device=dev)
+
+    def step():
+        st = ms.ms_perm(out.data_ptr(), n_perm, seed, ws_perm.data_ptr(), ws_perm.numel(),
+                        p_perm, sh)
+        if st != ms.MS_OK:
+            raise ms.MsError(st, "ms_perm")
+        st = ms.ms_shuffle(rec.data_ptr(), n_rec, 16, seed, ws_rec.data_ptr(), ws_rec.numel(),
+                           p_rec, sh)
+        if st != ms.MS_OK:
+            raise ms.MsError(st, "ms_shuffle")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ms.profile(reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    t_ms = allreduce_max(t_ms, world)
+    prof = ms.profile(reset=True)
+
+    elems = n_perm + n_rec
+    value = world * elems / (t_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the streaming gather of each HBM merge level):
+    # algorithmic bytes per launch = read n*w + write n*w
+    g = prof["gather"]
+    launches_per_step_perm = plan_perm.hbm_levels
+    launches_per_step_rec = plan_rec.hbm_levels
+    gather_bytes = args.steps * (launches_per_step_perm * 2 * n_perm * 4 +
+                                 launches_per_step_rec * 2 * n_rec * 16)
+    peaks = measured_peaks()
+    achieved = gather_bytes / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else 0.0
+    roofline = {
+        "bound": "hbm",
+        "kernel": "gather (HBM merge level)",
+        "achieved": round(achieved, 1),
+        "peak": peaks["hbm_gbs"],
+        "peak_source": peaks["source"],
+        "unit": "GB/s",
+        "frac": round(achieved / peaks["hbm_gbs"], 4),
+        "traffic": None,
+        "algorithmic_bytes_per_launch": {"perm": 2 * n_perm * 4, "rec": 2 * n_rec * 16},
+        "avg_launch_ms": round(g["ms"] / max(g["launches"], 1), 4),
+        "whole_path_frac": round(
+            (plan_perm.passes * 2 * n_perm * 4 + plan_rec.passes * 2 * n_rec * 16) / 1e9
+            / (t_ms * 1e-3) / peaks["hbm_gbs"], 4),
+    }
+    kernel_ms = {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}
+    launches = args.steps * (plan_perm.kernel_launches + plan_rec.kernel_launches)
+
+    # end to end through the host-buffer entry points: H2D of the input, the shuffle, D2H of
+    # the result, every step
+    e2e = None
+    if not args.no_e2e:
+        del ws_perm, ws_rec
+        torch.cuda.empty_cache()
+        hp = torch.empty(n_perm, dtype=torch.int32, pin_memory=True)
+        hr = torch.empty((n_rec, 4), dtype=torch.int32, pin_memory=True)
+        hr.copy_(rec_host)
+        q_perm = ms.params(B=args.B_perm, tile_bytes=args.tile_bytes)
+        q_rec = ms.params(B=args.B_rec, tile_bytes=args.tile_bytes)
+        wsh_perm = torch.empty(ms.ms_host_workspace_bytes(n_perm, 4, q_perm), dtype=torch.uint8,
+                               device=dev)
+        wsh_rec = torch.empty(ms.ms_host_workspace_bytes(n_rec, 16, q_rec), dtype=torch.uint8,
+                              device=dev)
+
+        def e2e_step():
+            st = ms.ms_perm_host(hp.data_ptr(), n_perm, seed, wsh_perm.data_ptr(),
+                                 wsh_perm.numel(), q_perm, sh)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, "ms_perm_host")
+            st = ms.ms_shuffle_host(hr.data_ptr(), n_rec, 16, seed, wsh_rec.data_ptr(),
+                                    wsh_rec.numel(), q_rec, sh)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, "ms_shuffle_host")
+
+        e2e_step()
+        k2 = max(2, min(args.steps, 5))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        t_e2e = (time.perf_counter() - t0) / k2
+        t_e2e = allreduce_max(t_e2e, world)
+        e2e = {"value": round(world * elems / t_e2e / 1e9, 4), "unit": "Gelem/s",
+               "h2d_bytes_per_step": n_rec * 16, "d2h_bytes_per_step": n_perm * 4 + n_rec * 16,
+               "ms_per_step": round(t_e2e * 1e3, 3), "steps": k2}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    line = {
+        "metric": "Gelem/s",
+        "value": round(value, 4),
+        "unit": "Gelem/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {
+            "workload": ("plain MergeShuffle at scale: perm of n=2^30 uint32 identity + shuffle of "
+                         "n=300000017 16-byte records {u32 key, 12-byte splitmix64 payload}, seed 7"
+                         if not args.small else "small profiling case: perm 2^26 + 2^24+17 records"),
+            "n_perm": n_perm, "n_rec": n_rec, "seed": SEED,
+            "B_perm": args.B_perm, "B_rec": args.B_rec,
+            "fuse_depth_perm": plan_perm.fuse_depth, "fuse_depth_rec": plan_rec.fuse_depth,
+            "passes_perm": plan_perm.passes, "passes_rec": plan_rec.passes,
+            "l2": "inputs larger than L2 (4.3 GB and 4.8 GB arrays), no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "profiled_events": "CUDA event pair around every kernel during the timed region",
+        },
+        "roofline": roofline,
+        "kernel_ms_per_step": kernel_ms,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ CPU oracle --------------
+def cpu_baseline(args) -> dict:
+    """The oracle as it stands on one host core, on a bounded sample of the workload."""
+    import oracle
+    from paper_1508_03167_gb300 import inputs
+
+    n1 = 1 << 23
+    n2 = 1 << 21
+    rec = inputs.records16(n2)
+    t0 = time.perf_counter()
+    oracle.perm(n1, SEED, args.B_perm)
+    oracle.shuffle(rec, SEED, args.B_rec)
+    dt = time.perf_counter() - t0
+    return {"value": round((n1 + n2) / dt / 1e9, 6), "unit": "Gelem/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"perm(2^23) u32 + shuffle(2^21) 16-byte records, B={args.B_perm}/"
+                      f"{args.B_rec}, single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle timed on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1508_03167_gb300 import inputs
+
+    n1 = 1 << 21
+    n2 = 1 << 19
+    rec = inputs.records16(n2)
+
+    def step():
+        oracle.perm(n1, SEED, args.B_perm)
+        oracle.shuffle(rec, SEED, args.B_rec)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (n1 + n2) / dt / 1e9
+    sample = (f"per step: perm(2^21) u32 + shuffle(2^19) 16-byte records of the same workload, "
+              f"B={args.B_perm}/{args.B_rec}, single-threaded C oracle")
+    line = {
+        "impl": "reference",
+        "metric": "Gelem/s",
+        "value": round(value, 6),
+        "unit": "Gelem/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "plain MergeShuffle at scale (bounded CPU sample)",
+                   "n_perm_sample": n1, "n_rec_sample": n2, "seed": SEED},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
