@@ -145,6 +145,30 @@ ms_status ms_perm_host(uint32_t *h_out, uint64_t n, uint64_t seed, void *d_ws, s
                        const ms_params *p, ms_stream_t stream);
 
 /*
+ * ms_perm_static -- ms_perm for callers that cannot allocate device memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * Some callers have device pointers for their own inputs and outputs but no way to obtain more
+ * device memory: a plugin whose host application owns every device allocation, or code that runs
+ * under a fixed device-memory budget with no allocator of its own. This entry point needs no
+ * workspace argument: its scratch is a fixed MS_STATIC_SCRATCH_BYTES (16 MiB) array compiled
+ * into the library, which every GPU that loads the library holds until the process exits.
+ *   d_out   device pointer to n uint32 values (the caller's output), 4-byte aligned.
+ *   n       at most MS_STATIC_MAX_N (2^21); larger n, or parameters whose plan needs more
+ *           scratch than the array holds, return MS_ERR_UNSUPPORTED without touching the device.
+ *   p, stream, seed  as for ms_perm; the result is identical to ms_perm's.
+ * Set-up: the first call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). All calls
+ * on a device share the one array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on it; serialise them.
+ */
+#define MS_STATIC_MAX_N (1ull << 21)
+#define MS_STATIC_SCRATCH_BYTES (16ull << 20)
+ms_status ms_perm_static(uint32_t *d_out, uint64_t n, uint64_t seed, const ms_params *p,
+                         ms_stream_t stream);
+
+/*
  * Collect the timings of every launch recorded since the last reset (waits for the recorded
  * events; process-wide state, not thread-safe) and optionally reset the record.
  */

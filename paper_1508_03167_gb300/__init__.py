@@ -18,7 +18,7 @@ __all__ = [
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
     "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
-    "ms_status_string", "ms_version", "params", "plan", "shuffle_", "perm", "shuffle_host",
+    "ms_status_string", "ms_version", "ms_perm_static", "MS_STATIC_MAX_N", "params", "plan", "shuffle_", "perm", "shuffle_host",
     "perm_host", "workspace",
 ]
 
@@ -26,6 +26,7 @@ MS_OK, MS_ERR_INVALID, MS_ERR_UNSUPPORTED, MS_ERR_NOMEM, MS_ERR_CUDA, MS_ERR_TIM
 MS_FLAG_TAIL_SEQUENTIAL = 0x1
 MS_FLAG_PROFILE = 0x2
 MS_MAX_B = 4096
+MS_STATIC_MAX_N = 1 << 21
 
 
 class MsParams(ctypes.Structure):
@@ -102,6 +103,8 @@ def lib() -> ctypes.CDLL:
         L.ms_shuffle_host.restype = i32
         L.ms_perm_host.argtypes = [vp, u64, u64, vp, sz, P, vp]
         L.ms_perm_host.restype = i32
+        L.ms_perm_static.argtypes = [vp, u64, u64, P, vp]
+        L.ms_perm_static.restype = i32
         L.ms_profile_read.argtypes = [ctypes.POINTER(MsProfile), i32]
         L.ms_profile_read.restype = i32
         L.ms_status_string.argtypes = [i32]
@@ -157,6 +160,12 @@ def ms_shuffle_host(h_data: int, n: int, w: int, seed: int, d_ws: int, ws_bytes:
 def ms_perm_host(h_out: int, n: int, seed: int, d_ws: int, ws_bytes: int,
                  p: MsParams | None = None, stream: int = 0) -> int:
     return int(lib().ms_perm_host(h_out, n, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_perm_static(d_out: int, n: int, seed: int, p: MsParams | None = None,
+                   stream: int = 0) -> int:
+    """ms_perm with the library's fixed 16 MiB device scratch (no workspace, no allocation)."""
+    return int(lib().ms_perm_static(d_out, n, seed, _p(p), stream))
 
 
 def ms_profile_read(reset: bool = True) -> MsProfile:
