@@ -29,7 +29,7 @@ if ROOT not in sys.path:
 N_PERM = 1 << 30
 N_REC = 300_000_017
 SEED = 7
-DEFAULT_B = {"perm": 64, "rec": 64}
+DEFAULT_B = {"perm": 128, "rec": 128}
 
 
 def parse():
@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--B-perm", type=int, default=DEFAULT_B["perm"])
     ap.add_argument("--B-rec", type=int, default=DEFAULT_B["rec"])
     ap.add_argument("--tile-bytes", type=int, default=0)
+    ap.add_argument("--fuse-depth", type=int, default=0,
+                    help="merge levels fused into the base-block kernel (-1: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true",
@@ -147,6 +149,12 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def g_levels(ms, n, w, p) -> int:
+    """Merge levels of the plan that run through the global streaming gather."""
+    plan = ms.ms_plan_info(n, w, p)
+    return plan.global_levels
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -162,8 +170,10 @@ def run_ours(args, world, rank, local):
     n_rec = (1 << 24) + 17 if args.small else N_REC
     seed = SEED + rank
     flags = ms.MS_FLAG_PROFILE
-    p_perm = ms.params(B=args.B_perm, tile_bytes=args.tile_bytes, flags=flags)
-    p_rec = ms.params(B=args.B_rec, tile_bytes=args.tile_bytes, flags=flags)
+    p_perm = ms.params(B=args.B_perm, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes,
+                       flags=flags)
+    p_rec = ms.params(B=args.B_rec, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes,
+                      flags=flags)
     plan_perm = ms.ms_plan_info(n_perm, 4, p_perm)
     plan_rec = ms.ms_plan_info(n_rec, 16, p_rec)
 
@@ -212,10 +222,10 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (the streaming gather of each HBM merge level):
     # algorithmic bytes per launch = read n*w + write n*w
     g = prof["gather"]
-    launches_per_step_perm = plan_perm.hbm_levels
-    launches_per_step_rec = plan_rec.hbm_levels
-    gather_bytes = args.steps * (launches_per_step_perm * 2 * n_perm * 4 +
-                                 launches_per_step_rec * 2 * n_rec * 16)
+    # bytes per gather launch: each global merge level reads and writes its array once
+    nglob_perm = g_levels(ms, n_perm, 4, p_perm)
+    nglob_rec = g_levels(ms, n_rec, 16, p_rec)
+    gather_bytes = args.steps * (nglob_perm * 2 * n_perm * 4 + nglob_rec * 2 * n_rec * 16)
     peaks = measured_peaks()
     achieved = gather_bytes / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else 0.0
     roofline = {
@@ -245,8 +255,8 @@ def run_ours(args, world, rank, local):
         hp = torch.empty(n_perm, dtype=torch.int32, pin_memory=True)
         hr = torch.empty((n_rec, 4), dtype=torch.int32, pin_memory=True)
         hr.copy_(rec_host)
-        q_perm = ms.params(B=args.B_perm, tile_bytes=args.tile_bytes)
-        q_rec = ms.params(B=args.B_rec, tile_bytes=args.tile_bytes)
+        q_perm = ms.params(B=args.B_perm, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes)
+        q_rec = ms.params(B=args.B_rec, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes)
         wsh_perm = torch.empty(ms.ms_host_workspace_bytes(n_perm, 4, q_perm), dtype=torch.uint8,
                                device=dev)
         wsh_rec = torch.empty(ms.ms_host_workspace_bytes(n_rec, 16, q_rec), dtype=torch.uint8,

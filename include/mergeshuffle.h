@@ -63,6 +63,10 @@ typedef void *ms_stream_t;
                                         the result is identical) */
 #define MS_FLAG_PROFILE 0x2u         /* time every kernel of the call with CUDA events on its
                                         stream; read with ms_profile_read */
+#define MS_FLAG_GLOBAL_LEVELS 0x4u   /* run every HBM merge level through the global plan (no
+                                        CTA-local levels; the result is identical) */
+#define MS_FLAG_CTA_LEVELS 0x8u      /* small merge levels finish per CTA rather than per warp
+                                        (the result is identical) */
 
 typedef struct {
   uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B) */
@@ -85,7 +89,8 @@ typedef struct {
   uint64_t tile_max;     /* largest tile (elements) */
   size_t workspace_bytes;
   uint32_t kernel_launches; /* kernels this library launches for one call */
-  uint32_t reserved;
+  uint32_t global_levels;   /* HBM levels that use the global plan and streaming gather; the
+                               other hbm_levels - global_levels finish inside a CTA or a warp */
 } ms_plan;
 
 /* Per-kernel-class timing accumulated over calls made with MS_FLAG_PROFILE. */

@@ -14,19 +14,22 @@ import threading
 
 __all__ = [
     "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
-    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_MAX_B", "MsParams",
+    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_MAX_B", "MsParams",
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
     "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
-    "ms_status_string", "ms_version", "ms_perm_static", "MS_STATIC_MAX_N", "params", "plan", "shuffle_", "perm", "shuffle_host",
+    "ms_status_string", "ms_version", "ms_perm_static", "MS_STATIC_MAX_N", "MS_STATIC_SCRATCH_BYTES", "params", "plan", "shuffle_", "perm", "shuffle_host",
     "perm_host", "workspace",
 ]
 
 MS_OK, MS_ERR_INVALID, MS_ERR_UNSUPPORTED, MS_ERR_NOMEM, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
 MS_FLAG_TAIL_SEQUENTIAL = 0x1
 MS_FLAG_PROFILE = 0x2
+MS_FLAG_GLOBAL_LEVELS = 0x4
+MS_FLAG_CTA_LEVELS = 0x8
 MS_MAX_B = 4096
 MS_STATIC_MAX_N = 1 << 21
+MS_STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class MsParams(ctypes.Structure):
@@ -40,7 +43,7 @@ class MsPlan(ctypes.Structure):
                 ("hbm_levels", ctypes.c_uint32), ("passes", ctypes.c_uint32),
                 ("tiles", ctypes.c_uint64), ("tile_max", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("global_levels", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

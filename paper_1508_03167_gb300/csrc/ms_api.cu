@@ -21,19 +21,60 @@ uint64_t ceil_scaled(uint64_t n, uint32_t shift, uint32_t c) {
   return ((n << shift) + q - 1) >> c;
 }
 
-uint32_t unit_capacity(uint64_t n, uint32_t c, uint32_t d) {
-  uint32_t cap = 0;
-  for (uint32_t lam = 0; lam < d; ++lam) {
-    const uint64_t Mt = 1ull << (d - lam - 1);
-    const uint64_t Nmax = ceil_scaled(n, lam + 1, c);
-    const uint64_t units = Mt * ((Nmax + 31) / 32);
-    if (units > cap) cap = static_cast<uint32_t>(units);
-  }
-  return cap;
+// Shared-memory layout of the base-block kernel (one CTA of 8 warps per tile of 2^d base
+// blocks): buffer 0 holds the base blocks at an odd stride (conflict-free Fisher-Yates) and
+// later a contiguous level; buffer 1 the other level; then the auxiliary arrays (coin words,
+// their zero prefixes, precomputed tail draws) of each warp, aliased by the CTA's own.
+struct LeafSmem {
+  uint32_t d, dw, leaf_max, stride, buf0, tile_max;
+  uint32_t ucap_w, tcap_w, ucap_c, tcap_c, aux_w;
+  size_t bytes;
+};
+
+uint32_t level_units(uint64_t n, uint32_t c, uint32_t gl, uint32_t lam) {
+  const uint64_t Mt = 1ull << (gl - lam - 1);
+  const uint64_t Nmax = ceil_scaled(n, lam + 1, c);
+  return static_cast<uint32_t>(Mt * ((Nmax + 31) / 32));
 }
 
-size_t leaf_smem_bytes(uint64_t tile_max, uint32_t w, uint32_t d, uint32_t unit_cap) {
-  return round_up((d > 0 ? 2 : 1) * tile_max * w + 2ull * unit_cap * 4, 16);
+// levels done by single warps: at most 5 (16 merges per warp level) and a warp tile of at most
+// 2048 elements
+uint32_t warp_levels_max(uint32_t leaf_max) {
+  uint32_t dw = 0;
+  while (dw < 5 && (static_cast<uint64_t>(leaf_max) << (dw + 1)) <= 2048) ++dw;
+  return dw;
+}
+
+LeafSmem leaf_smem(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
+  LeafSmem L;
+  const uint64_t q = 1ull << c;
+  L.d = d;
+  L.leaf_max = static_cast<uint32_t>((n + q - 1) >> c);
+  L.stride = L.leaf_max | 1u;
+  L.dw = std::min(d, warp_levels_max(L.leaf_max));
+  const uint64_t tile_max = ceil_scaled(n, d, c);
+  L.tile_max = static_cast<uint32_t>(tile_max);
+  const uint64_t padded = (1ull << d) * L.stride;
+  L.buf0 = static_cast<uint32_t>(std::max<uint64_t>(padded, tile_max));
+  L.ucap_w = 1;
+  for (uint32_t lam = 0; lam < L.dw; ++lam)
+    L.ucap_w = std::max(L.ucap_w, level_units(n, c, L.dw, lam));
+  L.ucap_c = 1;
+  for (uint32_t lam = L.dw; lam < d; ++lam)
+    L.ucap_c = std::max(L.ucap_c, level_units(n, c, d, lam));
+  const uint64_t wtile = ceil_scaled(n, L.dw, c);
+  L.tcap_w = static_cast<uint32_t>((wtile / 4 + 16) & ~1ull);
+  L.tcap_c = static_cast<uint32_t>((tile_max / 4 + 16) & ~1ull);
+  L.aux_w = static_cast<uint32_t>(round_up(2ull * L.ucap_w * 4 + 2ull * L.tcap_w, 16));
+  const size_t aux_c = round_up(2ull * L.ucap_c * 4 + 2ull * L.tcap_c, 16);
+  const size_t aux = std::max<size_t>(8ull * L.aux_w, aux_c);
+  L.bytes = round_up(static_cast<size_t>(L.buf0) * w + tile_max * w + aux, 16);
+  return L;
+}
+
+bool leaf_fits(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
+  const LeafSmem L = leaf_smem(n, c, d, w);
+  return L.bytes <= kSmemLimit && L.tile_max < 65536 && d - L.dw <= 3;
 }
 
 }  // namespace
@@ -63,22 +104,34 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   const uint32_t dmax = c < kMaxFuse ? c : kMaxFuse;
   uint32_t d = 0;
   if (fuse_depth < 0) {
-    for (uint32_t t = 0; t <= dmax; ++t) {
-      if (ceil_scaled(n, t, c) * w <= tile_bytes &&
-          leaf_smem_bytes(ceil_scaled(n, t, c), w, t, unit_capacity(n, c, t)) <= kSmemLimit)
-        d = t;
-    }
+    for (uint32_t t = 0; t <= dmax; ++t)
+      if (ceil_scaled(n, t, c) * w <= tile_bytes && leaf_fits(n, c, t, w)) d = t;
   } else {
     d = static_cast<uint32_t>(fuse_depth) < dmax ? static_cast<uint32_t>(fuse_depth) : dmax;
-    while (d > 0 &&
-           leaf_smem_bytes(ceil_scaled(n, d, c), w, d, unit_capacity(n, c, d)) > kSmemLimit)
-      --d;
+    while (d > 0 && !leaf_fits(n, c, d, w)) --d;
   }
   p.d = d;
   p.tiles = p.q >> d;
   p.tile_max = static_cast<uint32_t>(ceil_scaled(n, d, c));
-  p.unit_cap = unit_capacity(n, c, d);
-  p.leaf_smem = leaf_smem_bytes(p.tile_max, w, d, p.unit_cap);
+  const LeafSmem L = leaf_smem(n, c, d, w);
+  p.dw = L.dw;
+  p.leaf_max = L.leaf_max;
+  p.leaf_stride = L.stride;
+  p.buf0_elems = L.buf0;
+  p.ucap_w = L.ucap_w;
+  p.tcap_w = L.tcap_w;
+  p.ucap_c = L.ucap_c;
+  p.tcap_c = L.tcap_c;
+  p.aux_w = L.aux_w;
+  p.leaf_smem = L.bytes;
+  if (d == 0) {
+    // Fisher-Yates only: up to 32 blocks per one-warp CTA within 96 KiB of shared memory
+    const uint64_t per_block = static_cast<uint64_t>(L.stride) * w;
+    uint64_t per = (96ull * 1024) / per_block;
+    if (per > 32) per = 32;
+    if (per < 1) per = 1;
+    p.fy_per_cta = static_cast<uint32_t>(per);
+  }
   if (p.leaf_smem > kSmemLimit) return 2;
 
   // HBM levels d..c-1
@@ -105,10 +158,48 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     uint32_t hb = 10;
     while ((1ull << hb) < 2ull * lv.kcap) ++hb;
     lv.hbits = hb;
-    zc_cap = std::max<uint64_t>(zc_cap, M * lv.J);
-    minfo_cap = std::max<uint64_t>(minfo_cap, M);
-    kcap_max = std::max<uint64_t>(kcap_max, lv.kcap);
-    hbits_max = std::max(hbits_max, hb);
+    // local mode when a merge (and up to 16 of them) fits one CTA's staging buffer
+    lv.local = false;
+    lv.warp_local = false;
+    lv.warp_bytes = 0;
+    lv.mlog = 0;
+    if (Nmax * w <= kWarpSpanBytes && !(flags & (MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS))) {
+      uint32_t m = 0;
+      while (m < kLocalMaxMergesLog && (Nmax << (m + 1)) * w <= kWarpSpanBytes &&
+             (M >> (m + 1)) >= 1)
+        ++m;
+      lv.local = true;
+      lv.warp_local = true;
+      lv.mlog = m;
+      lv.span_max = static_cast<uint32_t>(ceil_scaled(n, lv.level + 1 + m, c));
+      lv.ucap = level_units(n, c, lv.level + 1 + m, lv.level);
+      lv.tcap = static_cast<uint32_t>((lv.span_max / 4 + 16) & ~1u);
+      lv.warp_bytes = static_cast<uint32_t>(round_up(
+          static_cast<size_t>(lv.span_max) * w + 2ull * lv.ucap * 4 + 2ull * lv.tcap, 16));
+      lv.smem = 0;
+      lv.kcap = 0;
+      lv.hbits = 10;
+    } else if (Nmax * w <= kLocalSpanBytes && !(flags & MS_FLAG_GLOBAL_LEVELS)) {
+      uint32_t m = 0;
+      while (m < kLocalMaxMergesLog && (Nmax << (m + 1)) * w <= kLocalSpanBytes &&
+             (M >> (m + 1)) >= 1)
+        ++m;
+      lv.local = true;
+      lv.mlog = m;
+      lv.span_max = static_cast<uint32_t>(ceil_scaled(n, lv.level + 1 + m, c));
+      lv.ucap = level_units(n, c, lv.level + 1 + m, lv.level);
+      lv.tcap = static_cast<uint32_t>((lv.span_max / 4 + 16) & ~1u);
+      lv.smem = round_up(static_cast<size_t>(lv.span_max) * w + 2ull * lv.ucap * 4 +
+                             2ull * lv.tcap, 16);
+      lv.kcap = 0;
+      lv.hbits = 10;
+    }
+    if (!lv.local) {
+      zc_cap = std::max<uint64_t>(zc_cap, M * lv.J);
+      minfo_cap = std::max<uint64_t>(minfo_cap, M);
+      kcap_max = std::max<uint64_t>(kcap_max, lv.kcap);
+      hbits_max = std::max(hbits_max, lv.hbits);
+    }
   }
   p.zc_cap = static_cast<uint32_t>(zc_cap);
   p.minfo_cap = static_cast<uint32_t>(minfo_cap);
@@ -118,7 +209,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   size_t off = 0;
   p.off_buf = off;
   if (p.nlevels > 0) off += round_up(n * w, 256);
-  if (p.nlevels > 0) {
+  if (p.nlevels > 0 && kcap_max > 0) {
     p.off_zc = off;     off += round_up(zc_cap * 4, 256);
     p.off_minfo = off;  off += round_up(minfo_cap * 16, 256);
     p.off_ctrl = off;   off += 256;
@@ -142,7 +233,7 @@ namespace {
 
 const char *const kKindNames[msk::kKindNum] = {
     "leaf", "count", "scan", "kscan", "hash_clear", "tail_insert", "tail_resolve",
-    "gather", "tail_sequential", "patch_read", "patch_write"};
+    "gather", "tail_sequential", "patch_read", "patch_write", "local_level"};
 
 // Process-wide event recorder used when MS_FLAG_PROFILE is set.
 class EventProfiler final : public msk::Prof {
@@ -267,8 +358,10 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   if (msk::launch_leaf(p, data, cur, perm, seed, s) != cudaSuccess) return MS_ERR_CUDA;
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     void *dst = (cur == data) ? b.other : data;
-    if (msk::launch_level(p, p.levels[i], cur, dst, b, seed, s) != cudaSuccess)
-      return MS_ERR_CUDA;
+    const msk::LevelPlan &lv = p.levels[i];
+    const cudaError_t e = lv.local ? msk::launch_local_level(p, lv, cur, dst, seed, s)
+                                   : msk::launch_level(p, lv, cur, dst, b, seed, s);
+    if (e != cudaSuccess) return MS_ERR_CUDA;
     cur = dst;
   }
   return MS_OK;
@@ -303,7 +396,14 @@ ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *params, ms_plan 
   out->tiles = n <= 1 ? 0u : p.tiles;
   out->tile_max = n <= 1 ? n : p.tile_max;
   out->workspace_bytes = p.ws_bytes;
-  out->kernel_launches = n <= 1 ? 0u : 1u + 9u * p.nlevels;
+  uint32_t launches = n <= 1 ? 0u : 1u;
+  uint32_t global = 0;
+  for (uint32_t i = 0; i < p.nlevels && n > 1; ++i) {
+    launches += p.levels[i].local ? 1u : 9u;
+    global += p.levels[i].local ? 0u : 1u;
+  }
+  out->kernel_launches = launches;
+  out->global_levels = global;
   return MS_OK;
 }
 

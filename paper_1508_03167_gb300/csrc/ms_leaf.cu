@@ -5,6 +5,18 @@
 // levels 0..d-1 of Algorithm 3 run inside shared memory with the stable random merge (Algorithm 2:
 // coin interleave until one half is exhausted, leftovers in order, then random insertion).
 // The tile is written back once, so this kernel is the first of the 1 + (c - d) HBM passes.
+//
+// Two phases, both running the same group-generic merge level:
+//   warp phase  each warp owns 2^dw consecutive base blocks (one lane per block for Fisher-Yates)
+//               and merges them through levels 0..dw-1 on its own, with warp barriers only;
+//   CTA phase   the 2^(d-dw) <= 8 warp results are merged through levels dw..d-1 by the whole
+//               CTA.
+// Base blocks sit at an odd stride in buffer 0, so the lanes of a warp (all at the same
+// Fisher-Yates step i) hit 32 different banks; merge level 0 reads that layout and writes
+// buffer 1 contiguously; later levels ping-pong between the buffers.
+// Every gather issues a batch of independent shared-memory loads before its stores; every merge
+// tail (the random insertions) has its draws computed in parallel, then one thread per merge
+// applies its swaps in order, eight at a time whenever those eight provably commute.
 #include "ms_common.cuh"
 #include "ms_device.cuh"
 #include "ms_plan.h"
@@ -13,7 +25,8 @@ namespace msk {
 namespace {
 
 constexpr int kLeafThreads = 256;
-constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr uint32_t kLeafWarps = kLeafThreads / 32;
+constexpr uint32_t kGroupMerges = 16;  // merges per level of one group (warp: dw <= 5)
 
 struct LeafArgs {
   const void *in;
@@ -22,9 +35,13 @@ struct LeafArgs {
   uint64_t q;
   uint2 key;
   uint32_t c;
-  uint32_t d;
-  uint32_t tile_max;
-  uint32_t unit_cap;
+  uint32_t d;          // fused levels
+  uint32_t dw;         // levels done by single warps
+  uint32_t tile_max;   // elements of the largest tile
+  uint32_t stride;     // odd stride of a base block in buffer 0
+  uint32_t buf0;       // elements of buffer 0
+  uint32_t ucap_w, tcap_w, ucap_c, tcap_c;  // coin-word / tail-draw capacities per group
+  uint32_t aux_w;      // bytes of one warp's auxiliary region
 };
 
 template <typename E>
@@ -34,157 +51,380 @@ __device__ __forceinline__ void swap_smem(E *a, uint32_t i, uint32_t j) {
   a[j] = t;
 }
 
-// One merge level inside the tile: X holds 2^(d-lam) shuffled blocks of 2^lam base blocks each,
-// Y receives 2^(d-lam-1) merged blocks.
-template <typename E>
-__device__ void tile_merge_level(const LeafArgs &a, uint64_t leaf0, uint64_t g0, uint32_t lam,
-                                 const E *__restrict__ X, E *__restrict__ Y, uint32_t *cw,
-                                 uint32_t *zw, uint32_t *m_s, uint32_t *m_n1, uint32_t *m_N,
-                                 uint32_t *m_T, uint32_t *m_ZT, uint32_t *scan_scratch) {
-  const uint32_t tid = threadIdx.x;
-  const uint32_t lane = tid & 31u;
-  const uint32_t warp = tid >> 5;
-  const uint32_t Mt = 1u << (a.d - lam - 1u);
-  const uint64_t rbase = leaf0 >> (lam + 1u);  // global id of the tile's first merge
-  const uint32_t Nmax = static_cast<uint32_t>(((a.n << (lam + 1u)) + a.q - 1u) >> a.c);
-  const uint32_t Wm = (Nmax + 31u) >> 5;   // coin words per merge
-  const uint32_t BPM = (Nmax + 127u) >> 7; // Philox blocks per merge
-  const uint32_t U = Mt * Wm;
+// Rejection draw in [0, R) from the slices of one word (R >= 2); false if every slice rejects.
+__device__ __forceinline__ bool draw_from_word(uint32_t word, uint32_t R, uint32_t &x) {
+  const uint32_t b = 32u - __clz(R - 1u);
+  const uint32_t mask = (b == 32u) ? 0xFFFFFFFFu : ((1u << b) - 1u);
+  const uint32_t first = word & mask;
+  if (first < R) {  // the first slice accepts with probability >= 1/2
+    x = first;
+    return true;
+  }
+  const uint32_t slices = 32u / b;
+  for (uint32_t u = 1; u < slices; ++u) {
+    const uint32_t v = (word >> (u * b)) & mask;
+    if (v < R) {
+      x = v;
+      return true;
+    }
+  }
+  return false;
+}
 
-  // merge bounds (tile-relative)
-  for (uint32_t r = tid; r < Mt; r += kLeafThreads) {
-    const uint64_t L0 = leaf0 + (static_cast<uint64_t>(r) << (lam + 1u));
+// Continuation of a draw whose word j = 0 rejected every slice: words j = 1, 2, ...
+__device__ __noinline__ uint32_t draw_continue(uint2 key, uint32_t tag, uint32_t level,
+                                               uint32_t id, uint32_t pos, uint32_t R) {
+  for (uint32_t j = 1; j < (1u << 20); ++j) {
+    const uint4 blk = philox10(make_uint4(pos >> 2, id, (tag << 16) | level, j), key);
+    uint32_t x;
+    if (draw_from_word(pick_word(blk, pos & 3u), R, x)) return x;
+  }
+  return 0u;
+}
+
+// Draw in [0, R) of stream (tag, level, id, pos) given its word j = 0.
+__device__ __forceinline__ uint32_t draw_with_word0(uint2 key, uint32_t tag, uint32_t level,
+                                                    uint32_t id, uint32_t pos, uint32_t R,
+                                                    uint32_t word0) {
+  if (R <= 1u) return 0u;
+  uint32_t x;
+  if (draw_from_word(word0, R, x)) return x;
+  return draw_continue(key, tag, level, id, pos, R);
+}
+
+// ---------------------------------------------------------------------------- groups ------
+// A group is one warp (G = 1) or the whole CTA (G = kLeafWarps).
+template <int G>
+struct Group {
+  static constexpr uint32_t kThreads = 32u * G;
+  static __device__ __forceinline__ void sync() {
+    if constexpr (G == 1) __syncwarp();
+    else __syncthreads();
+  }
+  static __device__ __forceinline__ uint32_t tid() {
+    if constexpr (G == 1) return threadIdx.x & 31u;
+    else return threadIdx.x;
+  }
+  // exclusive scan of one value per thread of the group; *total gets the group sum
+  static __device__ __forceinline__ uint32_t exscan(uint32_t v, uint32_t *scratch,
+                                                    uint32_t *total) {
+    if constexpr (G == 1) {
+      const uint32_t incl = warp_inclusive_scan(v);
+      *total = __shfl_sync(kFullMask, incl, 31);
+      return incl - v;
+    } else {
+      return block_exclusive_scan(v, scratch, total);
+    }
+  }
+};
+
+// Per-group shared-memory views.
+struct GroupSmem {
+  uint32_t *cw;   // coin words of the level
+  uint32_t *zp;   // exclusive zero prefix per coin word (over the group's level)
+  uint16_t *mv;   // precomputed tail draws
+  uint32_t ucap;  // capacity of cw / zp
+  uint32_t tcap;  // capacity of mv
+  // per merge (kGroupMerges entries): source bases of the halves (rebased by the merge's zero
+  // prefix once T is known), destination base, first-half size, size, break step, leftover base,
+  // packed tail prefix
+  uint32_t *m_a, *m_b, *m_s, *m_n1, *m_N, *m_T, *m_lb, *m_off;
+  uint32_t *scratch;  // 33 words for CTA-wide scans
+};
+
+// One merge level of Algorithm 3 over the group's region: 2^(gl-lam) merged runs of 2^lam base
+// blocks become 2^(gl-lam-1) runs. lb = global index of the region's first base block; the
+// tile-relative positions are relative to g0 (global position of the tile's first element).
+// X is read as base blocks at stride P (padded) on level 0 of the warp phase, contiguous
+// otherwise (X may also be global memory); Y is written contiguously.
+template <int G, typename E>
+__device__ __forceinline__ void merge_level(const LeafArgs &a, const GroupSmem &S, uint64_t lb,
+                                            uint64_t leaf0, uint64_t g0, uint32_t lam,
+                                            uint32_t gl, const E *X, uint32_t xcap, bool padded,
+                                            E *Y) {
+  using Gp = Group<G>;
+  constexpr uint32_t kT = Gp::kThreads;
+  // consecutive positions per lane in the gather, kLpw lanes per coin word
+  constexpr uint32_t kPos = sizeof(E) >= 16 ? 4u : 8u;
+  constexpr uint32_t kLpw = 32u / kPos;
+  const uint32_t gt = Gp::tid();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t Mt = 1u << (gl - lam - 1u);
+  const uint64_t rbase = lb >> (lam + 1u);  // global id of the region's first merge
+  const uint32_t Nmax = static_cast<uint32_t>(((a.n << (lam + 1u)) + a.q - 1u) >> a.c);
+  const uint32_t Wm = (Nmax + 31u) >> 5;    // coin words per merge
+  const uint32_t BPM = (Nmax + 127u) >> 7;  // Philox blocks per merge
+  const uint32_t U = Mt * Wm;
+  // u / Wm as a multiply-high, exact for u, Wm < 2^16 (Wm = 1 is the identity)
+  const uint32_t wm_magic = Wm > 1u ? static_cast<uint32_t>(0x100000000ull / Wm) + 1u : 0u;
+  auto merge_of = [&](uint32_t u) { return Wm > 1u ? __umulhi(u, wm_magic) : u; };
+
+  // ---- merge geometry
+  for (uint32_t r = gt; r < Mt; r += kT) {
+    const uint64_t L0 = lb + (static_cast<uint64_t>(r) << (lam + 1u));
     const uint64_t s = boundary(a.n, a.c, L0);
     const uint64_t mid = boundary(a.n, a.c, L0 + (1ull << lam));
     const uint64_t e = boundary(a.n, a.c, L0 + (2ull << lam));
-    m_s[r] = static_cast<uint32_t>(s - g0);
-    m_n1[r] = static_cast<uint32_t>(mid - s);
-    m_N[r] = static_cast<uint32_t>(e - s);
-    m_T[r] = static_cast<uint32_t>(e - s);
+    const uint32_t sl = static_cast<uint32_t>(s - g0);
+    const uint32_t n1 = static_cast<uint32_t>(mid - s);
+    S.m_s[r] = sl;
+    S.m_n1[r] = n1;
+    S.m_N[r] = static_cast<uint32_t>(e - s);
+    S.m_T[r] = static_cast<uint32_t>(e - s);
+    if (padded) {  // the halves are base blocks L0 and L0+1 of the tile at stride P
+      const uint32_t k = static_cast<uint32_t>(L0 - leaf0);
+      S.m_a[r] = k * a.stride;
+      S.m_b[r] = (k + 1u) * a.stride;
+    } else {
+      S.m_a[r] = sl;
+      S.m_b[r] = sl + n1;
+    }
   }
-  // coin words
-  for (uint32_t idx = tid; idx < Mt * BPM; idx += kLeafThreads) {
+  // ---- coin words
+  for (uint32_t idx = gt; idx < Mt * BPM; idx += kT) {
     const uint32_t r = idx / BPM;
     const uint32_t jb = idx - r * BPM;
     const uint4 blk = coin_block(a.key, lam, static_cast<uint32_t>(rbase + r), jb);
     const uint32_t base = r * Wm + 4u * jb;
-    if (4u * jb + 0u < Wm) cw[base + 0u] = blk.x;
-    if (4u * jb + 1u < Wm) cw[base + 1u] = blk.y;
-    if (4u * jb + 2u < Wm) cw[base + 2u] = blk.z;
-    if (4u * jb + 3u < Wm) cw[base + 3u] = blk.w;
+    if (4u * jb + 0u < Wm) S.cw[base + 0u] = blk.x;
+    if (4u * jb + 1u < Wm) S.cw[base + 1u] = blk.y;
+    if (4u * jb + 2u < Wm) S.cw[base + 2u] = blk.z;
+    if (4u * jb + 3u < Wm) S.cw[base + 3u] = blk.w;
   }
-  __syncthreads();
+  Gp::sync();
 
-  // zero counts per word, exclusive prefix over the whole tile level
+  // ---- zero counts per coin word and their exclusive prefix over the group's level
   {
-    const uint32_t per = (U + kLeafThreads - 1u) / kLeafThreads;
-    const uint32_t u0 = min(tid * per, U);
+    const uint32_t per = (U + kT - 1u) / kT;
+    const uint32_t u0 = min(gt * per, U);
     const uint32_t u1 = min(u0 + per, U);
     uint32_t local = 0;
     for (uint32_t u = u0; u < u1; ++u) {
-      const uint32_t r = u / Wm;
+      const uint32_t r = merge_of(u);
       const uint32_t j = u - r * Wm;
-      const uint32_t N = m_N[r];
+      const uint32_t N = S.m_N[r];
       const uint32_t valid = (32u * j >= N) ? 0u : min(32u, N - 32u * j);
-      const uint32_t z = __popc(~cw[u] & low_mask(valid));
-      zw[u] = z;
+      const uint32_t z = __popc(~S.cw[u] & low_mask(valid));
+      S.zp[u] = z;
       local += z;
     }
     uint32_t total;
-    uint32_t excl = block_exclusive_scan(local, scan_scratch, &total);
+    uint32_t excl = Gp::exscan(local, S.scratch, &total);
     for (uint32_t u = u0; u < u1; ++u) {
-      const uint32_t z = zw[u];
-      zw[u] = excl;
+      const uint32_t z = S.zp[u];
+      S.zp[u] = excl;
       excl += z;
     }
   }
-  __syncthreads();
+  Gp::sync();
 
-  // break step T of each merge: the (n1+1)-th zero or the (n2+1)-th one, whichever is first
-  for (uint32_t u = tid; u < U; u += kLeafThreads) {
-    const uint32_t r = u / Wm;
+  // ---- break step T: the (n1+1)-th zero or the (n2+1)-th one, whichever comes first
+  for (uint32_t u = gt; u < U; u += kT) {
+    const uint32_t r = merge_of(u);
     const uint32_t j = u - r * Wm;
-    const uint32_t N = m_N[r];
+    const uint32_t N = S.m_N[r];
     if (32u * j >= N) continue;
     const uint32_t valid = min(32u, N - 32u * j);
     const uint32_t vm = low_mask(valid);
-    const uint32_t word = cw[u];
-    const uint32_t Zs = zw[u] - zw[r * Wm];
+    const uint32_t word = S.cw[u];
+    const uint32_t Zs = S.zp[u] - S.zp[r * Wm];
     const uint32_t Os = 32u * j - Zs;
     const uint32_t zeros = __popc(~word & vm);
     const uint32_t ones = valid - zeros;
-    const uint32_t n1 = m_n1[r];
+    const uint32_t n1 = S.m_n1[r];
     const uint32_t n2 = N - n1;
-    if (Zs <= n1 && n1 < Zs + zeros) atomicMin(&m_T[r], 32u * j + select_set_bit(~word & vm, n1 - Zs));
-    if (Os <= n2 && n2 < Os + ones) atomicMin(&m_T[r], 32u * j + select_set_bit(word & vm, n2 - Os));
+    if (Zs <= n1 && n1 < Zs + zeros)
+      atomicMin(&S.m_T[r], 32u * j + select_set_bit(~word & vm, n1 - Zs));
+    if (Os <= n2 && n2 < Os + ones)
+      atomicMin(&S.m_T[r], 32u * j + select_set_bit(word & vm, n2 - Os));
   }
-  __syncthreads();
-  for (uint32_t r = tid; r < Mt; r += kLeafThreads) {
-    const uint32_t T = m_T[r], N = m_N[r], n1 = m_n1[r];
-    uint32_t ZT = n1;
+  Gp::sync();
+
+  // ---- per merge: rebased sources, leftover base, tail sizes (packed quads << 16 | length)
+  uint32_t packed = 0;
+  if (gt < Mt) {
+    const uint32_t r = gt;
+    const uint32_t T = S.m_T[r], N = S.m_N[r], n1 = S.m_n1[r];
+    const uint32_t zbase = S.zp[r * Wm];
+    const uint32_t A = S.m_a[r], B = S.m_b[r];
+    // position t >= T takes the rest of the half that did not run out, in order; the coin at T
+    // names the half that ran out (0: the first half)
+    uint32_t lbase = 0;
     if (T < N) {
-      const uint32_t bit = (cw[r * Wm + (T >> 5)] >> (T & 31u)) & 1u;
-      ZT = bit ? T - (N - n1) : n1;
+      const uint32_t bitT = (S.cw[r * Wm + (T >> 5)] >> (T & 31u)) & 1u;
+      lbase = bitT ? A - (N - n1) : B - n1;
     }
-    m_ZT[r] = ZT;
+    S.m_lb[r] = lbase;
+    S.m_a[r] = A - zbase;  // A + Z with Z = zp[u] - zbase + (zeros below t in word u)
+    S.m_b[r] = B + zbase;  // B + t - Z
+    const uint32_t k = N - T;
+    const uint32_t quads = k ? ((N - 1u) >> 2) - (T >> 2) + 1u : 0u;
+    packed = (quads << 16) | k;
   }
-  __syncthreads();
+  uint32_t total;
+  {
+    const uint32_t excl = Gp::exscan(packed, S.scratch, &total);
+    if (gt < Mt) S.m_off[gt] = excl;
+  }
+  Gp::sync();
 
-  // stable interleave and leftover copy: lane L of a warp places step 32j + L
-  for (uint32_t u = warp; u < U; u += kLeafWarps) {
-    const uint32_t r = u / Wm;
+  // ---- stable interleave and leftover copy: kLpw lanes per coin word, kPos positions per lane;
+  // all loads of a lane are issued before its stores
+  for (uint32_t u = gt / kLpw; u < U; u += kT / kLpw) {
+    const uint32_t r = merge_of(u);
     const uint32_t j = u - r * Wm;
-    const uint32_t N = m_N[r];
-    const uint32_t t = 32u * j + lane;
-    if (t >= N) continue;
-    const uint32_t s = m_s[r], n1 = m_n1[r], T = m_T[r];
-    uint32_t src;
-    if (t < T) {
-      const uint32_t word = cw[u];
-      const uint32_t Z = zw[u] - zw[r * Wm] + __popc(~word & low_mask(lane));
-      src = ((word >> lane) & 1u) ? s + n1 + (t - Z) : s + Z;
-    } else if (m_ZT[r] == n1) {  // first half exhausted: second half's remainder
-      src = s + n1 + (t - n1);
-    } else {                     // second half exhausted: first half's remainder
-      src = s + (t - (N - n1));
-    }
-    Y[s + t] = X[min(src, s + N - 1u)];  // clamp: stays inside the merge's range
-  }
-  __syncthreads();
-
-  // random insertion of positions T..N-1 (sequential per merge; draws computed 32 at a time)
-  for (uint32_t r = warp; r < Mt; r += kLeafWarps) {
-    const uint32_t T = m_T[r], N = m_N[r], s = m_s[r];
-    const uint32_t id = static_cast<uint32_t>(rbase + r);
-    for (uint32_t base = T; base < N; base += 32u) {
-      const uint32_t i = base + lane;
-      const uint32_t m = (i < N) ? draw_uniform(a.key, kTagTail, lam, id, i, i + 1u) : 0u;
-      const uint32_t cnt = min(32u, N - base);
-      for (uint32_t k = 0; k < cnt; ++k) {
-        const uint32_t mk = __shfl_sync(kFullMask, m, k);
-        if (lane == 0) swap_smem(Y, s + base + k, s + mk);
+    const uint32_t N = S.m_N[r];
+    const uint32_t sub = (gt % kLpw) * kPos;
+    const uint32_t t0 = 32u * j + sub;
+    if (t0 >= N) continue;
+    const uint32_t word = S.cw[u];
+    const uint32_t Zu = S.zp[u];
+    const uint32_t aa = S.m_a[r], bb = S.m_b[r], T = S.m_T[r], lbase = S.m_lb[r];
+    const uint32_t dst = S.m_s[r] + t0;
+    const uint32_t cnt = min(kPos, N - t0);
+    uint32_t z = Zu + __popc(~word & low_mask(sub));  // Z + zbase at position t0
+    E v[kPos];
+#pragma unroll
+    for (uint32_t k = 0; k < kPos; ++k) {
+      if (k < cnt) {
+        const uint32_t t = t0 + k;
+        const uint32_t bit = (word >> (sub + k)) & 1u;
+        const uint32_t src = (t < T) ? (bit ? bb + t - z : aa + z) : lbase + t;
+        z += bit ^ 1u;
+        v[k] = X[min(src, xcap - 1u)];  // clamp keeps the read inside the buffer
       }
-      __syncwarp();
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPos; ++k)
+      if (k < cnt) Y[dst + k] = v[k];
+  }
+
+  // ---- tail draws, one Philox block per four consecutive positions
+  const uint32_t Q = total >> 16;
+  const uint32_t K = total & 0xFFFFu;
+  const bool precomputed = K <= S.tcap;
+  if (precomputed) {
+    for (uint32_t gq = gt; gq < Q; gq += kT) {
+      uint32_t lo = 0, hi = Mt;  // largest r with quad offset <= gq
+      while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((S.m_off[mid] >> 16) <= gq) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t r = lo;
+      const uint32_t T = S.m_T[r], N = S.m_N[r];
+      const uint32_t quad = (T >> 2) + (gq - (S.m_off[r] >> 16));
+      const uint32_t id = static_cast<uint32_t>(rbase + r);
+      const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lam, 0u), a.key);
+      const uint32_t koff = S.m_off[r] & 0xFFFFu;
+#pragma unroll
+      for (uint32_t v = 0; v < 4u; ++v) {
+        const uint32_t i = 4u * quad + v;
+        if (i >= T && i < N)
+          S.mv[koff + (i - T)] = static_cast<uint16_t>(
+              draw_with_word0(a.key, kTagTail, lam, id, i, i + 1u, pick_word(w0, v)));
+      }
     }
   }
-  __syncthreads();
+  Gp::sync();
+
+  // ---- random insertion of positions T..N-1, in order (Algorithm 2's second loop)
+  constexpr uint32_t kBatch = sizeof(E) >= 16 ? 4u : 8u;
+  for (uint32_t r = gt; r < Mt; r += kT) {
+    const uint32_t T = S.m_T[r], N = S.m_N[r], s = S.m_s[r];
+    E *C = Y + s;
+    uint32_t i = T;
+    if (precomputed) {
+      const uint16_t *mk = S.mv + (S.m_off[r] & 0xFFFFu);  // mk[i - T] = draw of position i
+      while (i < N) {
+        if (i + kBatch <= N) {
+          // swaps (i+k, m_k) for k < kBatch commute when every m_k lies before the window and
+          // all m_k differ: then they touch 2*kBatch distinct positions
+          uint32_t m[kBatch];
+          bool ok = true;
+#pragma unroll
+          for (uint32_t k = 0; k < kBatch; ++k) {
+            m[k] = mk[i - T + k];
+            ok &= m[k] < i;
+          }
+#pragma unroll
+          for (uint32_t k = 0; k < kBatch; ++k)
+#pragma unroll
+            for (uint32_t l = k + 1; l < kBatch; ++l) ok &= m[k] != m[l];
+          if (ok) {
+            E lo[kBatch], hi[kBatch];
+#pragma unroll
+            for (uint32_t k = 0; k < kBatch; ++k) {
+              lo[k] = C[i + k];
+              hi[k] = C[m[k]];
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < kBatch; ++k) {
+              C[i + k] = hi[k];
+              C[m[k]] = lo[k];
+            }
+            i += kBatch;
+            continue;
+          }
+        }
+        swap_smem(C, i, static_cast<uint32_t>(mk[i - T]));
+        ++i;
+      }
+    } else {
+      const uint32_t id = static_cast<uint32_t>(rbase + r);
+      for (; i < N; ++i) swap_smem(C, i, draw_uniform(a.key, kTagTail, lam, id, i, i + 1u));
+    }
+  }
+  Gp::sync();
 }
 
 template <typename E, bool kPerm>
-__global__ void __launch_bounds__(kLeafThreads) leaf_kernel(LeafArgs a) {
+__global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t scan_scratch[33];
-  __shared__ uint32_t m_s[kMaxTileMerges], m_n1[kMaxTileMerges], m_N[kMaxTileMerges],
-      m_T[kMaxTileMerges], m_ZT[kMaxTileMerges];
+  __shared__ uint32_t merges[kLeafWarps][8][kGroupMerges];
 
-  E *X = reinterpret_cast<E *>(smem_raw);
-  E *Y = X + a.tile_max;
-  uint32_t *cw = reinterpret_cast<uint32_t *>(Y + (a.d > 0 ? a.tile_max : 0u));
-  uint32_t *zw = cw + a.unit_cap;
+  E *const buf0 = reinterpret_cast<E *>(smem_raw);
+  E *const buf1 = buf0 + a.buf0;
+  unsigned char *const aux = reinterpret_cast<unsigned char *>(buf1 + a.tile_max);
 
   const E *in = static_cast<const E *>(a.in);
   E *out = static_cast<E *>(a.out);
   const uint64_t tiles = a.q >> a.d;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint32_t P = a.stride;
+  const uint32_t dc = a.d - a.dw;            // CTA-phase levels
+  const uint32_t nwt = 1u << dc;             // warp tiles per CTA tile (<= 8)
+  const uint32_t wleaves = 1u << a.dw;       // base blocks per warp tile
+
+  // this warp's group views (warp phase) and the CTA's (CTA phase, aliasing warp 0's merges)
+  GroupSmem Sw;
+  {
+    unsigned char *base = aux + warp * a.aux_w;
+    Sw.cw = reinterpret_cast<uint32_t *>(base);
+    Sw.zp = Sw.cw + a.ucap_w;
+    Sw.mv = reinterpret_cast<uint16_t *>(Sw.zp + a.ucap_w);
+    Sw.ucap = a.ucap_w;
+    Sw.tcap = a.tcap_w;
+    Sw.m_a = merges[warp][0]; Sw.m_b = merges[warp][1]; Sw.m_s = merges[warp][2];
+    Sw.m_n1 = merges[warp][3]; Sw.m_N = merges[warp][4]; Sw.m_T = merges[warp][5];
+    Sw.m_off = merges[warp][6]; Sw.m_lb = merges[warp][7];
+    Sw.scratch = scan_scratch;
+  }
+  GroupSmem Sc;
+  {
+    Sc.cw = reinterpret_cast<uint32_t *>(aux);
+    Sc.zp = Sc.cw + a.ucap_c;
+    Sc.mv = reinterpret_cast<uint16_t *>(Sc.zp + a.ucap_c);
+    Sc.ucap = a.ucap_c;
+    Sc.tcap = a.tcap_c;
+    Sc.m_a = merges[0][0]; Sc.m_b = merges[0][1]; Sc.m_s = merges[0][2];
+    Sc.m_n1 = merges[0][3]; Sc.m_N = merges[0][4]; Sc.m_T = merges[0][5];
+    Sc.m_off = merges[0][6]; Sc.m_lb = merges[0][7];
+    Sc.scratch = scan_scratch;
+  }
 
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t leaf0 = tile << a.d;
@@ -192,45 +432,151 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(LeafArgs a) {
     const uint64_t g1 = boundary(a.n, a.c, leaf0 + (1ull << a.d));
     const uint32_t len = static_cast<uint32_t>(g1 - g0);
 
-    for (uint32_t i = threadIdx.x; i < len; i += kLeafThreads) {
+    if (warp < nwt) {
+      // ---------------- warp phase: base blocks [lb, lb + 2^dw) ----------------
+      const uint64_t lb = leaf0 + static_cast<uint64_t>(warp) * wleaves;
+      // load (perm: the identity is generated in place, one lane per block)
       if constexpr (kPerm) {
-        X[i] = static_cast<E>(g0 + i);
+        for (uint32_t k = lane; k < wleaves; k += 32u) {
+          const uint64_t bs = boundary(a.n, a.c, lb + k);
+          const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
+          E *blk = buf0 + (warp * wleaves + k) * P;
+          for (uint32_t i = 0; i < L; ++i) blk[i] = static_cast<E>(bs + i);
+        }
       } else {
-        X[i] = in[g0 + i];
+        for (uint32_t k = 0; k < wleaves; ++k) {
+          const uint64_t bs = boundary(a.n, a.c, lb + k);
+          const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
+          E *blk = buf0 + (warp * wleaves + k) * P;
+          for (uint32_t i = lane; i < L; i += 32u) blk[i] = in[bs + i];
+        }
+      }
+      __syncwarp();
+      // Algorithm 1, one lane per base block; one Philox block serves four positions
+      for (uint32_t k = lane; k < wleaves; k += 32u) {
+        const uint64_t leaf = lb + k;
+        const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
+                                                 boundary(a.n, a.c, leaf));
+        E *blk = buf0 + (warp * wleaves + k) * P;
+        uint4 qw = make_uint4(0, 0, 0, 0);
+        uint32_t quad = 0xFFFFFFFFu;
+        for (uint32_t i = L; i-- > 1u;) {
+          if ((i >> 2) != quad) {
+            quad = i >> 2;
+            qw = philox10(make_uint4(quad, static_cast<uint32_t>(leaf), (kTagLeaf << 16), 0u),
+                          a.key);
+          }
+          const uint32_t j = draw_with_word0(a.key, kTagLeaf, 0u, static_cast<uint32_t>(leaf),
+                                             i, i + 1u, pick_word(qw, i & 3u));
+          swap_smem(blk, i, j);
+        }
+      }
+      __syncwarp();
+      if (a.dw > 0)
+        merge_level<1, E>(a, Sw, lb, leaf0, g0, 0u, a.dw, buf0, a.buf0, true, buf1);
+    }
+    // buffer 0 switches from the padded layout to the contiguous one
+    __syncthreads();
+    E *X = (a.dw > 0) ? buf1 : buf0;
+    E *Y = (a.dw > 0) ? buf0 : buf1;
+    if (warp < nwt) {
+      const uint64_t lb = leaf0 + static_cast<uint64_t>(warp) * wleaves;
+      for (uint32_t lam = 1; lam < a.dw; ++lam) {
+        merge_level<1, E>(a, Sw, lb, leaf0, g0, lam, a.dw, X, a.tile_max, false, Y);
+        E *t = X;
+        X = Y;
+        Y = t;
+      }
+    } else if (a.dw > 1) {
+      for (uint32_t lam = 1; lam < a.dw; ++lam) {  // keep the buffer roles in step
+        E *t = X;
+        X = Y;
+        Y = t;
       }
     }
     __syncthreads();
-
-    // Algorithm 1 on every base block of the tile (one thread per block)
-    for (uint32_t k = threadIdx.x; k < (1u << a.d); k += kLeafThreads) {
-      const uint64_t leaf = leaf0 + k;
-      const uint32_t bs = static_cast<uint32_t>(boundary(a.n, a.c, leaf) - g0);
-      const uint32_t be = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1u) - g0);
-      DrawMemo memo;
-      for (uint32_t i = be - bs; i-- > 1u;) {
-        const uint32_t j = draw_uniform(a.key, kTagLeaf, 0u, static_cast<uint32_t>(leaf), i,
-                                        i + 1u, memo);
-        swap_smem(X, bs + i, bs + j);
-      }
-    }
-    __syncthreads();
-
-    for (uint32_t lam = 0; lam < a.d; ++lam) {
-      tile_merge_level<E>(a, leaf0, g0, lam, X, Y, cw, zw, m_s, m_n1, m_N, m_T, m_ZT,
-                          scan_scratch);
+    // ---------------- CTA phase: levels dw..d-1 ----------------
+    for (uint32_t lam = a.dw; lam < a.d; ++lam) {
+      const bool padded = (lam == 0);  // only when the warp phase is empty
+      merge_level<kLeafWarps, E>(a, Sc, leaf0, leaf0, g0, lam, a.d, X,
+                                 padded ? a.buf0 : a.tile_max, padded, Y);
       E *t = X;
       X = Y;
       Y = t;
     }
-
-    for (uint32_t i = threadIdx.x; i < len; i += kLeafThreads) out[g0 + i] = X[i];
+    // ---------------- store ----------------
+    // d = 0: the tile is one base block at offset 0 of buffer 0
+    const E *res = (a.d == 0) ? buf0 : X;
+    for (uint32_t i = tid; i < len; i += kLeafThreads) out[g0 + i] = res[i];
     __syncthreads();
-    // restore buffer roles for the next tile
-    if (a.d & 1u) {
-      E *t = X;
-      X = Y;
-      Y = t;
+  }
+}
+
+// Fisher-Yates only (d = 0): one warp per CTA, one lane per base block. The blocks of a CTA sit
+// at an odd stride in shared memory, so the lanes (all at the same step) hit distinct banks.
+// Loads and stores go block by block with all 32 lanes, so global accesses stay coalesced.
+// The Philox block of the next quad of positions is computed one quad ahead.
+template <typename E, bool kPerm>
+__global__ void __launch_bounds__(32) fy_kernel(LeafArgs a, uint32_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *const blocks = reinterpret_cast<E *>(smem_raw);
+  const E *in = static_cast<const E *>(a.in);
+  E *out = static_cast<E *>(a.out);
+  const uint32_t lane = threadIdx.x;
+  const uint32_t P = a.stride;
+  const uint64_t groups = (a.q + per_cta - 1) / per_cta;
+  for (uint64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
+    const uint64_t lb = gidx * per_cta;
+    const uint32_t cnt = static_cast<uint32_t>(a.q - lb < per_cta ? a.q - lb : per_cta);
+    if constexpr (kPerm) {
+      if (lane < cnt) {
+        const uint64_t bs = boundary(a.n, a.c, lb + lane);
+        const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + lane + 1) - bs);
+        E *blk = blocks + lane * P;
+        for (uint32_t i = 0; i < L; ++i) blk[i] = static_cast<E>(bs + i);
+      }
+    } else {
+      for (uint32_t k = 0; k < cnt; ++k) {
+        const uint64_t bs = boundary(a.n, a.c, lb + k);
+        const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
+        E *blk = blocks + k * P;
+        for (uint32_t i = lane; i < L; i += 32u) blk[i] = in[bs + i];
+      }
     }
+    __syncwarp();
+    if (lane < cnt) {
+      const uint64_t leaf = lb + lane;
+      const uint32_t id = static_cast<uint32_t>(leaf);
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
+                                               boundary(a.n, a.c, leaf));
+      E *blk = blocks + lane * P;
+      if (L >= 2u) {
+        uint32_t quad = (L - 1u) >> 2;
+        uint4 cur = philox10(make_uint4(quad, id, (kTagLeaf << 16), 0u), a.key);
+        uint4 nxt = cur;
+        for (uint32_t i = L - 1u; i >= 1u; --i) {
+          if ((i & 3u) == 3u || i == L - 1u) {
+            // entering quad i/4: start the Philox block of the quad below it
+            if (quad > 0) nxt = philox10(make_uint4(quad - 1u, id, (kTagLeaf << 16), 0u), a.key);
+          }
+          const uint32_t j = draw_with_word0(a.key, kTagLeaf, 0u, id, i, i + 1u,
+                                             pick_word(cur, i & 3u));
+          swap_smem(blk, i, j);
+          if ((i & 3u) == 0u) {
+            cur = nxt;
+            --quad;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t k = 0; k < cnt; ++k) {
+      const uint64_t bs = boundary(a.n, a.c, lb + k);
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
+      const E *blk = blocks + k * P;
+      for (uint32_t i = lane; i < L; i += 32u) out[bs + i] = blk[i];
+    }
+    __syncwarp();
   }
 }
 
@@ -245,8 +591,28 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
   a.key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
   a.c = p.c;
   a.d = p.d;
+  a.dw = p.dw;
   a.tile_max = p.tile_max;
-  a.unit_cap = p.unit_cap;
+  a.stride = p.leaf_stride;
+  a.buf0 = p.buf0_elems;
+  a.ucap_w = p.ucap_w;
+  a.tcap_w = p.tcap_w;
+  a.ucap_c = p.ucap_c;
+  a.tcap_c = p.tcap_c;
+  a.aux_w = p.aux_w;
+  if (p.d == 0 && p.fy_per_cta > 0) {
+    auto fk = fy_kernel<E, kPerm>;
+    const size_t smem = static_cast<size_t>(p.fy_per_cta) * p.leaf_stride * sizeof(E);
+    cudaError_t e2 = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem));
+    if (e2 != cudaSuccess) return e2;
+    const uint64_t groups = (p.q + p.fy_per_cta - 1) / p.fy_per_cta;
+    const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
+    if (p.prof) p.prof->begin(kKindLeaf, s);
+    fk<<<static_cast<unsigned>(grid), 32, smem, s>>>(a, p.fy_per_cta);
+    if (p.prof) p.prof->end(s);
+    return cudaGetLastError();
+  }
   auto kern = leaf_kernel<E, kPerm>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(p.leaf_smem));
@@ -258,7 +624,137 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
   return cudaGetLastError();
 }
 
+// One HBM merge level whose merges are small enough to finish inside one CTA: each CTA takes
+// 2^m consecutive merges (2^(m+l+1) base blocks), reads both halves of each straight from global
+// memory into a shared-memory staging copy of the merged output (same merge routine as the
+// tile phase), applies the merge tails there, and stores the span coalesced. No plan kernels,
+// hash tables or patches are needed for such levels.
+template <typename E>
+__global__ void __launch_bounds__(kLeafThreads, 2) local_level_kernel(LeafArgs a, uint32_t lam,
+                                                                      uint32_t m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t scan_scratch[33];
+  __shared__ uint32_t merges[8][kGroupMerges];
+  E *const stage = reinterpret_cast<E *>(smem_raw);
+  GroupSmem S;
+  S.cw = reinterpret_cast<uint32_t *>(stage + a.tile_max);
+  S.zp = S.cw + a.ucap_c;
+  S.mv = reinterpret_cast<uint16_t *>(S.zp + a.ucap_c);
+  S.ucap = a.ucap_c;
+  S.tcap = a.tcap_c;
+  S.m_a = merges[0]; S.m_b = merges[1]; S.m_s = merges[2]; S.m_n1 = merges[3];
+  S.m_N = merges[4]; S.m_T = merges[5]; S.m_off = merges[6]; S.m_lb = merges[7];
+  S.scratch = scan_scratch;
+  const E *in = static_cast<const E *>(a.in);
+  E *out = static_cast<E *>(a.out);
+  const uint32_t gl = m + lam + 1u;  // base blocks per span: 2^gl
+  const uint64_t spans = a.q >> gl;
+  for (uint64_t sp = blockIdx.x; sp < spans; sp += gridDim.x) {
+    const uint64_t lb = sp << gl;
+    const uint64_t g0 = boundary(a.n, a.c, lb);
+    const uint32_t len = static_cast<uint32_t>(boundary(a.n, a.c, lb + (1ull << gl)) - g0);
+    merge_level<kLeafWarps, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage);
+    for (uint32_t i = threadIdx.x; i < len; i += kLeafThreads) out[g0 + i] = stage[i];
+    __syncthreads();
+  }
+}
+
+// The same with one warp per span: each warp finishes its own 2^m small merges (warp barriers
+// only), so the SM interleaves many independent warps. 4 warps per CTA share nothing but the
+// CTA's shared memory allocation.
+constexpr uint32_t kWarpLocalWarps = 4;
+template <typename E>
+__global__ void __launch_bounds__(kWarpLocalWarps * 32, 8)
+    warp_local_level_kernel(LeafArgs a, uint32_t lam, uint32_t m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t merges[kWarpLocalWarps][8][kGroupMerges];
+  const uint32_t warp = threadIdx.x >> 5;
+  unsigned char *base = smem_raw + warp * a.aux_w;
+  E *const stage = reinterpret_cast<E *>(base);
+  GroupSmem S;
+  S.cw = reinterpret_cast<uint32_t *>(stage + a.tile_max);
+  S.zp = S.cw + a.ucap_c;
+  S.mv = reinterpret_cast<uint16_t *>(S.zp + a.ucap_c);
+  S.ucap = a.ucap_c;
+  S.tcap = a.tcap_c;
+  S.m_a = merges[warp][0]; S.m_b = merges[warp][1]; S.m_s = merges[warp][2];
+  S.m_n1 = merges[warp][3]; S.m_N = merges[warp][4]; S.m_T = merges[warp][5];
+  S.m_off = merges[warp][6]; S.m_lb = merges[warp][7];
+  S.scratch = nullptr;
+  const E *in = static_cast<const E *>(a.in);
+  E *out = static_cast<E *>(a.out);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gl = m + lam + 1u;
+  const uint64_t spans = a.q >> gl;
+  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * kWarpLocalWarps;
+  for (uint64_t sp = static_cast<uint64_t>(blockIdx.x) * kWarpLocalWarps + warp; sp < spans;
+       sp += nwarps) {
+    const uint64_t lb = sp << gl;
+    const uint64_t g0 = boundary(a.n, a.c, lb);
+    const uint32_t len = static_cast<uint32_t>(boundary(a.n, a.c, lb + (1ull << gl)) - g0);
+    merge_level<1, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage);
+    for (uint32_t i = lane; i < len; i += 32u) out[g0 + i] = stage[i];
+    __syncwarp();
+  }
+}
+
+template <typename E>
+cudaError_t launch_local_t(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                           uint64_t seed, cudaStream_t s) {
+  LeafArgs a;
+  a.in = in;
+  a.out = out;
+  a.n = p.n;
+  a.q = p.q;
+  a.key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  a.c = p.c;
+  a.d = 0;
+  a.dw = 0;
+  a.tile_max = lv.span_max;
+  a.stride = 1;
+  a.buf0 = 0;
+  a.ucap_w = 0;
+  a.tcap_w = 0;
+  a.ucap_c = lv.ucap;
+  a.tcap_c = lv.tcap;
+  a.aux_w = lv.warp_bytes;
+  if (lv.warp_local) {
+    auto wk = warp_local_level_kernel<E>;
+    const size_t smem = static_cast<size_t>(lv.warp_bytes) * kWarpLocalWarps;
+    cudaError_t e2 = cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem));
+    if (e2 != cudaSuccess) return e2;
+    const uint64_t spans = p.q >> (lv.mlog + lv.level + 1u);
+    const uint64_t blocks = (spans + kWarpLocalWarps - 1) / kWarpLocalWarps;
+    const uint64_t grid = blocks < 1048576ull ? blocks : 1048576ull;
+    if (p.prof) p.prof->begin(kKindLocal, s);
+    wk<<<static_cast<unsigned>(grid), kWarpLocalWarps * 32, smem, s>>>(a, lv.level, lv.mlog);
+    if (p.prof) p.prof->end(s);
+    return cudaGetLastError();
+  }
+  auto kern = local_level_kernel<E>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(lv.smem));
+  if (err != cudaSuccess) return err;
+  const uint64_t spans = p.q >> (lv.mlog + lv.level + 1u);
+  const uint64_t grid = spans < 1048576ull ? spans : 1048576ull;
+  if (p.prof) p.prof->begin(kKindLocal, s);
+  kern<<<static_cast<unsigned>(grid), kLeafThreads, lv.smem, s>>>(a, lv.level, lv.mlog);
+  if (p.prof) p.prof->end(s);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                               uint64_t seed, cudaStream_t s) {
+  switch (p.w) {
+    case 4: return launch_local_t<uint32_t>(p, lv, in, out, seed, s);
+    case 8: return launch_local_t<uint2>(p, lv, in, out, seed, s);
+    case 16: return launch_local_t<uint4>(p, lv, in, out, seed, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s) {

@@ -429,22 +429,40 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(LevelArgs a) {
     __syncthreads();
     const E *A = in + mb.s;  // the second half starts at A + n1
     E *C = out + mb.s;
-    for (uint32_t u = warp; u < kChunk / 32u; u += kThreads / 32) {
-      const uint32_t t = t0 + 32u * u + lane;
-      if (t >= t1) continue;
-      // source index inside the merge; the clamp keeps every load inside [s, e) even if the
-      // plan were inconsistent (parity tests would then fail instead of the load faulting)
-      uint32_t src;
-      if (t < T) {
-        const uint32_t word = cw[u];
-        const uint32_t Z = Z0 + zw[u] + __popc(~word & low_mask(lane));
-        src = ((word >> lane) & 1u) ? n1 + (t - Z) : Z;
-      } else if (first_exhausted) {
-        src = t;
-      } else {
-        src = t - (N - n1);
+    // Warp w owns coin words w, w+8, ...; lane L places step 32u + L of word u, so each store
+    // instruction writes 32 consecutive elements. All loads of a batch are issued before any
+    // store, keeping kBatch independent loads in flight per thread.
+    constexpr uint32_t kWarps = kThreads / 32;
+    constexpr uint32_t kWordsPerWarp = kChunk / 32u / kWarps;
+    constexpr uint32_t kBatch = sizeof(E) >= 16 ? 8u : 16u;
+#pragma unroll
+    for (uint32_t b0 = 0; b0 < kWordsPerWarp; b0 += kBatch) {
+      E v[kBatch];
+#pragma unroll
+      for (uint32_t k = 0; k < kBatch; ++k) {
+        const uint32_t u = warp + (b0 + k) * kWarps;
+        const uint32_t t = t0 + 32u * u + lane;
+        if (t < t1) {
+          // source index inside the merge; the clamp keeps every load inside [s, e) even if
+          // the plan were inconsistent (parity tests would then fail instead of a load faulting)
+          uint32_t src;
+          if (t < T) {
+            const uint32_t word = cw[u];
+            const uint32_t Z = Z0 + zw[u] + __popc(~word & low_mask(lane));
+            src = ((word >> lane) & 1u) ? n1 + (t - Z) : Z;
+          } else if (first_exhausted) {
+            src = t;
+          } else {
+            src = t - (N - n1);
+          }
+          v[k] = A[min(src, N - 1u)];
+        }
       }
-      C[t] = A[min(src, N - 1u)];
+#pragma unroll
+      for (uint32_t k = 0; k < kBatch; ++k) {
+        const uint32_t t = t0 + 32u * (warp + (b0 + k) * kWarps) + lane;
+        if (t < t1) C[t] = v[k];
+      }
     }
     __syncthreads();
   }

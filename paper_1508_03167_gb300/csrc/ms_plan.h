@@ -10,10 +10,13 @@
 namespace msk {
 
 constexpr uint32_t kMaxB = 4096u;             // largest cutoff (base block <= B+1 elements)
-constexpr uint32_t kMaxFuse = 10u;            // at most 2^10 base blocks per tile
-constexpr uint32_t kMaxTileMerges = 512u;     // 2^(kMaxFuse-1)
+constexpr uint32_t kMaxFuse = 9u;             // at most 2^9 base blocks per tile
+constexpr uint32_t kMaxTileMerges = 256u;     // 2^(kMaxFuse-1)
 constexpr uint32_t kChunk = 4096u;            // coin steps per HBM chunk (32 Philox blocks)
 constexpr uint32_t kDefaultTileBytes = 48u * 1024u;
+constexpr uint32_t kLocalSpanBytes = 32u * 1024u;  // staging of a local-mode merge level
+constexpr uint32_t kLocalMaxMergesLog = 4u;        // at most 16 merges per local CTA
+constexpr uint32_t kWarpSpanBytes = 8u * 1024u;    // staging of a warp-local merge span
 constexpr uint32_t kSmemLimit = 200u * 1024u; // dynamic shared memory budget of one CTA
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
@@ -30,6 +33,7 @@ enum KernelKind : int {
   kKindTailSeq,
   kKindPatchRead,
   kKindPatchWrite,
+  kKindLocal,
   kKindNum
 };
 
@@ -48,6 +52,14 @@ struct LevelPlan {
   uint32_t J;      // chunks of kChunk steps per merge
   uint32_t kcap;   // capacity for tail steps summed over the level's merges
   uint32_t hbits;  // hash table of 2^hbits slots
+  // local mode: every merge finishes inside one CTA (2^mlog merges per CTA)
+  bool local;
+  bool warp_local;      // one warp per span (no CTA barriers)
+  uint32_t warp_bytes;  // shared memory of one warp's span (warp-local mode)
+  uint32_t mlog;
+  uint32_t span_max;  // elements of the largest CTA span
+  uint32_t ucap, tcap;
+  size_t smem;
 };
 
 struct Plan {
@@ -60,6 +72,15 @@ struct Plan {
   uint64_t tiles = 0;
   uint32_t tile_max = 0;     // elements
   uint32_t unit_cap = 0;     // coin words per tile level (shared-memory arrays)
+  uint32_t leaf_max = 0;     // largest base block: ceil(n / q)
+  uint32_t leaf_stride = 0;  // odd shared-memory stride of one base block (>= leaf_max)
+  uint32_t buf0_elems = 0;   // first tile buffer: max(2^d * leaf_stride, tile_max)
+  uint32_t tail_cap = 0;     // precomputed tail draws per tile level
+  uint32_t buf1_bytes = 0;   // unused
+  uint32_t dw = 0;           // fused levels done by single warps (the rest, d - dw <= 3, by the CTA)
+  uint32_t ucap_w = 0, tcap_w = 0, ucap_c = 0, tcap_c = 0;  // per-group coin-word / draw capacity
+  uint32_t aux_w = 0;        // bytes of one warp's auxiliary shared-memory region
+  uint32_t fy_per_cta = 0;   // d = 0: base blocks per one-warp CTA of the Fisher-Yates kernel
   size_t leaf_smem = 0;      // dynamic shared memory of the base-block kernel
   uint32_t nlevels = 0;      // HBM levels
   LevelPlan levels[33];
@@ -96,5 +117,7 @@ cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uin
                         cudaStream_t s);
 cudaError_t launch_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                          const Buffers &b, uint64_t seed, cudaStream_t s);
+cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                               uint64_t seed, cudaStream_t s);
 
 }  // namespace msk

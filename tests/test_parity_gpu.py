@@ -80,10 +80,33 @@ def test_result_independent_of_fusion_depth_and_tiles(n, B):
         assert np.array_equal(gpu_perm(n, 11, B, tile_bytes=tb), want), tb
 
 
+@pytest.mark.parametrize("n,B", [(1 << 20, 1024), (262147, 16), (100003, 256), (65537, 1)])
+def test_global_and_local_levels_agree(n, B):
+    """Small merge levels normally finish inside one CTA; forcing every level through the
+    global plan (chunk prefixes, hash-table tails, patches) must give the same output."""
+    want, _ = oracle.perm(n, 13, B)
+    assert np.array_equal(gpu_perm(n, 13, B, flags=ms.MS_FLAG_GLOBAL_LEVELS), want)
+    assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS), want)
+    assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0), want)
+    assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_CTA_LEVELS), want)
+
+
+@pytest.mark.parametrize("B", [2, 31, 32, 33, 100, 256, 1000, 4096])
+def test_fisher_yates_only_base_kernel(B):
+    """fuse_depth = 0: the base-block kernel only shuffles blocks (one lane per block)."""
+    for n in (B * 37 + 5, 262147):
+        want, _ = oracle.perm(n, 21, B)
+        assert np.array_equal(gpu_perm(n, 21, B, fuse_depth=0), want), n
+    rec = inputs.records16(100003)
+    want, _ = oracle.shuffle(rec, 4, B)
+    assert np.array_equal(gpu_shuffle(rec, 4, B, fuse_depth=0), want)
+
+
 @pytest.mark.parametrize("n,B", [(1 << 20, 1024), (262147, 16), (65537, 1)])
 def test_sequential_tail_path_is_identical(n, B):
     want, _ = oracle.perm(n, 3, B)
-    got = gpu_perm(n, 3, B, fuse_depth=0, flags=ms.MS_FLAG_TAIL_SEQUENTIAL)
+    got = gpu_perm(n, 3, B, fuse_depth=0,
+                   flags=ms.MS_FLAG_TAIL_SEQUENTIAL | ms.MS_FLAG_GLOBAL_LEVELS)
     assert np.array_equal(got, want)
 
 

@@ -56,5 +56,6 @@ def test_static_entry_point_rejects_sizes_beyond_its_scratch():
     assert ms.ms_perm_static(out.data_ptr(), ms.MS_STATIC_MAX_N + 1, 1, None, s) == \
         ms.MS_ERR_UNSUPPORTED
     # within the size limit but a plan whose scratch does not fit the fixed array
-    assert ms.ms_perm_static(out.data_ptr(), 1 << 20, 1, ms.params(B=1, fuse_depth=0), s) == \
-        ms.MS_ERR_UNSUPPORTED
+    big = ms.params(B=1, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS)
+    assert ms.ms_workspace_bytes(1 << 20, 4, big) > ms.MS_STATIC_SCRATCH_BYTES
+    assert ms.ms_perm_static(out.data_ptr(), 1 << 20, 1, big, s) == ms.MS_ERR_UNSUPPORTED
