@@ -67,6 +67,8 @@ typedef void *ms_stream_t;
                                         CTA-local levels; the result is identical) */
 #define MS_FLAG_CTA_LEVELS 0x8u      /* small merge levels finish per CTA rather than per warp
                                         (the result is identical) */
+#define MS_FLAG_PERM 0x10u           /* batch calls: fill every instance with its permutation of
+                                        0..n_i-1 instead of shuffling it (w must be 4) */
 
 typedef struct {
   uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B) */
@@ -148,6 +150,36 @@ ms_status ms_shuffle_host(void *h_data, uint64_t n, uint32_t w, uint64_t seed, v
                           size_t ws_bytes, const ms_params *p, ms_stream_t stream);
 ms_status ms_perm_host(uint32_t *h_out, uint64_t n, uint64_t seed, void *d_ws, size_t ws_bytes,
                        const ms_params *p, ms_stream_t stream);
+
+/*
+ * Batched form: k independent instances (the same w and B), instance i of n_i elements at device
+ * pointer h_ptrs[i] (the pointer array itself lives in host memory), with seed h_seeds[i], or
+ * base_seed + i when h_seeds is NULL. Each result equals the single call on that instance.
+ *
+ * Instances of at most 2^22 elements run in one persistent launch: every CTA takes whole
+ * instances, largest first, from an atomic queue and finishes each alone (no CTA waits for
+ * another). Larger instances run the single-instance path one after another on the stream.
+ *   ms_batch_workspace_bytes  device workspace for the batch (ping-pong buffers of the engine
+ *                             instances, per-CTA scratch, the instance table, and one
+ *                             single-instance workspace for the largest large instance).
+ *   ms_batch_prepare          writes the instance table into d_ws (a host-to-device copy from
+ *                             pageable memory; call it again whenever pointers, sizes or seeds
+ *                             change).
+ *   ms_batch_run              only enqueues kernels and memsets on the stream (so it can be
+ *                             captured into a CUDA graph once prepared); arguments as for prepare.
+ *   ms_shuffle_batch          prepare + run.
+ * flags MS_FLAG_PERM: fill each instance with its permutation of 0..n_i-1 (w = 4).
+ */
+size_t ms_batch_workspace_bytes(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *p);
+ms_status ms_batch_prepare(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                           const uint64_t *h_seeds, uint64_t base_seed, void *d_ws,
+                           size_t ws_bytes, const ms_params *p, ms_stream_t stream);
+ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                       const uint64_t *h_seeds, uint64_t base_seed, void *d_ws, size_t ws_bytes,
+                       const ms_params *p, ms_stream_t stream);
+ms_status ms_shuffle_batch(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                           const uint64_t *h_seeds, uint64_t base_seed, void *d_ws,
+                           size_t ws_bytes, const ms_params *p, ms_stream_t stream);
 
 /*
  * ms_perm_static -- ms_perm for callers that cannot allocate device memory.

@@ -14,7 +14,8 @@ import threading
 
 __all__ = [
     "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
-    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_MAX_B", "MsParams",
+    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_MAX_B", "ms_batch_workspace_bytes",
+    "ms_batch_prepare", "ms_batch_run", "ms_shuffle_batch", "batch_workspace", "shuffle_batch", "MsParams",
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
     "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
@@ -27,6 +28,7 @@ MS_FLAG_TAIL_SEQUENTIAL = 0x1
 MS_FLAG_PROFILE = 0x2
 MS_FLAG_GLOBAL_LEVELS = 0x4
 MS_FLAG_CTA_LEVELS = 0x8
+MS_FLAG_PERM = 0x10
 MS_MAX_B = 4096
 MS_STATIC_MAX_N = 1 << 21
 MS_STATIC_SCRATCH_BYTES = 16 << 20
@@ -106,6 +108,14 @@ def lib() -> ctypes.CDLL:
         L.ms_shuffle_host.restype = i32
         L.ms_perm_host.argtypes = [vp, u64, u64, vp, sz, P, vp]
         L.ms_perm_host.restype = i32
+        pu64 = ctypes.POINTER(ctypes.c_uint64)
+        pvp = ctypes.POINTER(ctypes.c_void_p)
+        L.ms_batch_workspace_bytes.argtypes = [u32, pu64, u32, P]
+        L.ms_batch_workspace_bytes.restype = sz
+        for name in ("ms_batch_prepare", "ms_batch_run", "ms_shuffle_batch"):
+            fn = getattr(L, name)
+            fn.argtypes = [u32, pvp, pu64, u32, pu64, u64, vp, sz, P, vp]
+            fn.restype = i32
         L.ms_perm_static.argtypes = [vp, u64, u64, P, vp]
         L.ms_perm_static.restype = i32
         L.ms_profile_read.argtypes = [ctypes.POINTER(MsProfile), i32]
@@ -163,6 +173,42 @@ def ms_shuffle_host(h_data: int, n: int, w: int, seed: int, d_ws: int, ws_bytes:
 def ms_perm_host(h_out: int, n: int, seed: int, d_ws: int, ws_bytes: int,
                  p: MsParams | None = None, stream: int = 0) -> int:
     return int(lib().ms_perm_host(h_out, n, seed, d_ws, ws_bytes, _p(p), stream))
+
+
+def _u64s(vals):
+    if vals is None:
+        return None
+    vals = [int(v) for v in vals]
+    return (ctypes.c_uint64 * max(len(vals), 1))(*vals)
+
+
+def _ptrs(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_void_p * max(len(vals), 1))(*vals)
+
+
+def ms_batch_workspace_bytes(ns, w: int, p: MsParams | None = None) -> int:
+    return int(lib().ms_batch_workspace_bytes(len(ns), _u64s(ns), w, _p(p)))
+
+
+def _batch_call(name, ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p, stream):
+    k = len(ns)
+    return int(getattr(lib(), name)(k, _ptrs(ptrs), _u64s(ns), w, _u64s(seeds), base_seed,
+                                     d_ws, ws_bytes, _p(p), stream))
+
+
+def ms_batch_prepare(ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p=None, stream=0) -> int:
+    return _batch_call("ms_batch_prepare", ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p,
+                       stream)
+
+
+def ms_batch_run(ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p=None, stream=0) -> int:
+    return _batch_call("ms_batch_run", ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p, stream)
+
+
+def ms_shuffle_batch(ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p=None, stream=0) -> int:
+    return _batch_call("ms_shuffle_batch", ptrs, ns, w, seeds, base_seed, d_ws, ws_bytes, p,
+                       stream)
 
 
 def ms_perm_static(d_out: int, n: int, seed: int, p: MsParams | None = None,
@@ -282,3 +328,39 @@ def perm_host(h_out, seed: int, ws, B: int = 1024, fuse_depth: int = -1, flags: 
     if st != MS_OK:
         raise MsError(st, "ms_perm_host")
     return h_out
+
+
+def batch_workspace(ns, w: int = 4, device=None, **kw):
+    import torch
+
+    nbytes = ms_batch_workspace_bytes(list(ns), w, params(**kw))
+    if nbytes == 0:
+        raise MsError(MS_ERR_INVALID, "batch workspace sizing")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def shuffle_batch(tensors, base_seed: int = 0, seeds=None, perm: bool = False, B: int = 1024,
+                  fuse_depth: int = -1, flags: int = 0, ws=None, stream=None):
+    """Shuffle (or, with perm=True, fill with permutations) a list of contiguous CUDA tensors,
+    instance i with seed seeds[i] or base_seed + i."""
+    widths = set()
+    ns, ptrs = [], []
+    for t in tensors:
+        n, w = _width(t)
+        ns.append(n)
+        ptrs.append(t.data_ptr() if n else 0)
+        if n:
+            widths.add(w)
+    if len(widths) > 1:
+        raise ValueError("all instances must have the same element width")
+    w = widths.pop() if widths else 4
+    fl = flags | (MS_FLAG_PERM if perm else 0)
+    p = params(B, fuse_depth, fl)
+    if ws is None:
+        ws = batch_workspace(ns, w, tensors[0].device if tensors else None, B=B,
+                             fuse_depth=fuse_depth, flags=fl)
+    st = ms_shuffle_batch(ptrs, ns, w, seeds, base_seed, ws.data_ptr(), ws.numel(), p,
+                          _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_shuffle_batch")
+    return tensors

@@ -233,7 +233,7 @@ namespace {
 
 const char *const kKindNames[msk::kKindNum] = {
     "leaf", "count", "scan", "kscan", "hash_clear", "tail_insert", "tail_resolve",
-    "gather", "tail_sequential", "patch_read", "patch_write", "local_level"};
+    "gather", "tail_sequential", "patch_read", "patch_write", "local_level", "batch_engine"};
 
 // Process-wide event recorder used when MS_FLAG_PROFILE is set.
 class EventProfiler final : public msk::Prof {
@@ -367,9 +367,161 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   return MS_OK;
 }
 
+// ------------------------------------------------------------------ batch layout ---------
+constexpr uint32_t kEngineGrid = 320;  // persistent CTAs (2 per SM on a 152-SM GB300, spare)
+
+struct BatchLayout {
+  size_t off_table = 0, off_queue = 0, off_scratch = 0, off_large = 0, total = 0;
+  std::vector<size_t> tmp_off;   // per instance: engine ping-pong buffer (SIZE_MAX if large)
+  std::vector<uint32_t> order;   // engine instances, largest first
+  size_t scratch_per_cta = 0;
+  size_t large_ws = 0;
+};
+
+ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *params,
+                       BatchLayout *L) {
+  const ms_params r = resolve(params);
+  if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
+  if ((r.flags & MS_FLAG_PERM) && w != 4) return MS_ERR_INVALID;
+  if (r.B == 0) return MS_ERR_INVALID;
+  if (r.B > MS_MAX_B) return MS_ERR_UNSUPPORTED;
+  if (k > 0 && h_n == nullptr) return MS_ERR_INVALID;
+  L->tmp_off.assign(k, SIZE_MAX);
+  L->order.clear();
+  size_t off = msk::round_up(static_cast<size_t>(k) * msk::engine_inst_bytes() + 1, 256);
+  L->off_table = 0;
+  L->off_queue = off;
+  off += 256;
+  for (uint32_t i = 0; i < k; ++i) {
+    if (h_n[i] > 0xFFFFFFFFull) return MS_ERR_INVALID;
+    if (h_n[i] >= 2 && h_n[i] <= msk::kEngineMaxN) {
+      L->tmp_off[i] = off;
+      off += msk::round_up(h_n[i] * w, 256);
+      L->order.push_back(i);
+    } else if (h_n[i] > msk::kEngineMaxN) {
+      const size_t ws = ms_workspace_bytes(h_n[i], w, params);
+      if (ws == 0) return MS_ERR_INVALID;
+      L->large_ws = std::max(L->large_ws, ws);
+    }
+  }
+  std::stable_sort(L->order.begin(), L->order.end(),
+                   [&](uint32_t x, uint32_t y) { return h_n[x] > h_n[y]; });
+  L->scratch_per_cta =
+      msk::round_up((2ull << msk::kEngineHbits) * 4 + 3ull * msk::kEngineKcap * 4, 256);
+  L->off_scratch = off;
+  if (!L->order.empty()) off += L->scratch_per_cta * kEngineGrid;
+  L->off_large = off;
+  off += L->large_ws;
+  L->total = off;
+  return MS_OK;
+}
+
+struct BatchInstHost {  // mirrors the device descriptor of ms_batch.cu
+  uint64_t data, tmp, n, seed;
+  uint32_t flags, pad;
+};
+
 }  // namespace
 
 extern "C" {
+
+size_t ms_batch_workspace_bytes(uint32_t k, const uint64_t *h_n, uint32_t w,
+                                const ms_params *p) {
+  BatchLayout L;
+  if (batch_layout(k, h_n, w, p, &L) != MS_OK) return 0;
+  return L.total;
+}
+
+static ms_status batch_check(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                             void *d_ws, size_t ws_bytes, const ms_params *p, BatchLayout *L) {
+  const ms_status st = batch_layout(k, h_n, w, p, L);
+  if (st != MS_OK) return st;
+  if (k > 0 && h_ptrs == nullptr) return MS_ERR_INVALID;
+  if (ws_bytes < L->total || d_ws == nullptr || reinterpret_cast<uintptr_t>(d_ws) % 256 != 0)
+    return MS_ERR_INVALID;
+  for (uint32_t i = 0; i < k; ++i)
+    if (h_n[i] > 1 && (h_ptrs[i] == nullptr || reinterpret_cast<uintptr_t>(h_ptrs[i]) % w != 0))
+      return MS_ERR_INVALID;
+  return MS_OK;
+}
+
+ms_status ms_batch_prepare(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                           const uint64_t *h_seeds, uint64_t base_seed, void *d_ws,
+                           size_t ws_bytes, const ms_params *p, ms_stream_t stream) {
+  BatchLayout L;
+  const ms_status st = batch_check(k, h_ptrs, h_n, w, d_ws, ws_bytes, p, &L);
+  if (st != MS_OK) return st;
+  if (L.order.empty()) return MS_OK;
+  if (sizeof(BatchInstHost) != msk::engine_inst_bytes()) return MS_ERR_INVALID;
+  std::vector<BatchInstHost> table(L.order.size());
+  char *base = static_cast<char *>(d_ws);
+  for (size_t q = 0; q < L.order.size(); ++q) {
+    const uint32_t i = L.order[q];
+    BatchInstHost &e = table[q];
+    e.data = reinterpret_cast<uintptr_t>(h_ptrs[i]);
+    e.tmp = reinterpret_cast<uintptr_t>(base + L.tmp_off[i]);
+    e.n = h_n[i];
+    e.seed = h_seeds ? h_seeds[i] : base_seed + i;
+    e.flags = 0;
+    e.pad = 0;
+  }
+  // pageable source: the copy has consumed it when the call returns
+  if (cudaMemcpyAsync(base + L.off_table, table.data(), table.size() * sizeof(BatchInstHost),
+                      cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return MS_ERR_CUDA;
+  return MS_OK;
+}
+
+ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                       const uint64_t *h_seeds, uint64_t base_seed, void *d_ws, size_t ws_bytes,
+                       const ms_params *p, ms_stream_t stream) {
+  BatchLayout L;
+  const ms_status st = batch_check(k, h_ptrs, h_n, w, d_ws, ws_bytes, p, &L);
+  if (st != MS_OK) return st;
+  const ms_params r = resolve(p);
+  const bool perm = (r.flags & MS_FLAG_PERM) != 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(d_ws);
+  std::unique_lock<std::mutex> prof_lock(g_prof_mu, std::defer_lock);
+  msk::Prof *prof = nullptr;
+  if (r.flags & MS_FLAG_PROFILE) {
+    prof_lock.lock();
+    prof = &profiler();
+  }
+  if (!L.order.empty()) {
+    if (msk::launch_engine(w, perm, base + L.off_table, static_cast<uint32_t>(L.order.size()),
+                           reinterpret_cast<uint32_t *>(base + L.off_queue), r.B,
+                           base + L.off_scratch, L.scratch_per_cta, msk::kEngineKcap,
+                           msk::kEngineHbits, kEngineGrid, msk::kEngineSmem, s,
+                           prof) != cudaSuccess)
+      return MS_ERR_CUDA;
+  }
+  if (prof_lock.owns_lock()) prof_lock.unlock();
+  for (uint32_t i = 0; i < k; ++i) {
+    if (h_n[i] <= 1) {
+      if (perm && h_n[i] == 1 &&
+          cudaMemsetAsync(h_ptrs[i], 0, 4, s) != cudaSuccess)
+        return MS_ERR_CUDA;
+      continue;
+    }
+    if (h_n[i] <= msk::kEngineMaxN) continue;
+    const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
+    const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large, L.large_ws,
+                             p, s);
+    if (rs != MS_OK) return rs;
+  }
+  return MS_OK;
+}
+
+ms_status ms_shuffle_batch(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uint32_t w,
+                           const uint64_t *h_seeds, uint64_t base_seed, void *d_ws,
+                           size_t ws_bytes, const ms_params *p, ms_stream_t stream) {
+  const ms_status st =
+      ms_batch_prepare(k, h_ptrs, h_n, w, h_seeds, base_seed, d_ws, ws_bytes, p, stream);
+  if (st != MS_OK) return st;
+  return ms_batch_run(k, h_ptrs, h_n, w, h_seeds, base_seed, d_ws, ws_bytes, p, stream);
+}
+
 
 void ms_default_params(ms_params *p) {
   if (!p) return;

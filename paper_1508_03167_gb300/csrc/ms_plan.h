@@ -34,6 +34,7 @@ enum KernelKind : int {
   kKindPatchRead,
   kKindPatchWrite,
   kKindLocal,
+  kKindEngine,
   kKindNum
 };
 
@@ -119,5 +120,14 @@ cudaError_t launch_level(const Plan &p, const LevelPlan &lv, const void *in, voi
                          const Buffers &b, uint64_t seed, cudaStream_t s);
 cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                                uint64_t seed, cudaStream_t s);
+// Batch engine (ms_batch.cu): one persistent launch over a device table of instances.
+cudaError_t launch_engine(uint32_t w, bool perm, const void *inst, uint32_t k, uint32_t *queue,
+                          uint32_t B, void *scratch, size_t scratch_per_cta, uint32_t kcap,
+                          uint32_t hbits, uint32_t grid, size_t smem, cudaStream_t s, Prof *prof);
+size_t engine_inst_bytes();
+constexpr uint64_t kEngineMaxN = 1ull << 22;   // largest instance the batch engine takes
+constexpr uint32_t kEngineKcap = 8192;         // tail steps per merge replayed in parallel
+constexpr uint32_t kEngineHbits = 14;          // hash slots per engine CTA
+constexpr size_t kEngineSmem = 96 * 1024;      // dynamic shared memory of an engine CTA
 
 }  // namespace msk
