@@ -44,7 +44,13 @@ def parse():
     ap.add_argument("--fuse-depth", type=int, default=0,
                     help="merge levels fused into the base-block kernel (-1: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-window", type=float, default=0.25,
+                    help="seconds of 20k/s arrivals in the serving overload run")
+    ap.add_argument("--serve-sub-rate", type=float, default=1500.0)
+    ap.add_argument("--serve-sub-window", type=float, default=2.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["scale", "batched", "batched-large", "serve"],
+                    default="scale")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: perm 2^26 + 2^24+17 records (inputs still above L2)")
     return ap.parse_args()
@@ -391,11 +397,158 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _timed_graph(torch, fn, steps, warmup):
+    """Capture fn() (stream work only) into a CUDA graph and time `steps` replays."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fn(s)  # eager run: kernel attributes are set outside the capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn(s)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched(args, large: bool):
+    """4096 perm(n_i), n_i log-uniform in [2^6, 2^20], seed_i = 1 + i (batched), or 64 shuffles
+    of uint64 arrays, n_i uniform in [10^6, 10^8] non-power-of-two (batched-large); one prepared
+    batch replayed from a CUDA graph, against one launch sequence per instance."""
+    import torch
+
+    import paper_1508_03167_gb300 as ms
+    from paper_1508_03167_gb300 import inputs
+
+    if large:
+        sizes = [int(x) for x in inputs.batch_sizes_uniform(64, 10**6, 10**8)]
+        w, B, flags = 8, args.B_rec, 0
+        bufs = [inputs.values_u64_torch(n, i).view(torch.int64) for i, n in enumerate(sizes)]
+        base_seed = 1
+    else:
+        sizes = [int(x) for x in inputs.batch_sizes_log_uniform(4096, 6, 20)]
+        w, B, flags = 4, args.B_perm, ms.MS_FLAG_PERM
+        bufs = [torch.empty(n, dtype=torch.int32, device="cuda") for n in sizes]
+        base_seed = 1
+    p = ms.params(B=B, flags=flags)
+    ptrs = [b.data_ptr() for b in bufs]
+    nbytes = ms.ms_batch_workspace_bytes(sizes, w, p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    total = sum(sizes)
+
+    def prep(s):
+        assert ms.ms_batch_prepare(ptrs, sizes, w, None, base_seed, ws.data_ptr(), nbytes, p,
+                                   s.cuda_stream) == ms.MS_OK
+
+    def run(s):
+        assert ms.ms_batch_run(ptrs, sizes, w, None, base_seed, ws.data_ptr(), nbytes, p,
+                               s.cuda_stream) == ms.MS_OK
+
+    s0 = torch.cuda.Stream()
+    with torch.cuda.stream(s0):
+        prep(s0)
+    s0.synchronize()
+    t_batch = _timed_graph(torch, run, args.steps, args.warmup)
+    # one launch sequence per instance (the same library, no batching)
+    q = ms.params(B=B)
+    wss = torch.empty(max(ms.ms_workspace_bytes(n, w, q) for n in sizes), dtype=torch.uint8,
+                      device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+
+    def per_launch():
+        for i, n in enumerate(sizes):
+            if large:
+                rc = ms.ms_shuffle(ptrs[i], n, w, base_seed + i, wss.data_ptr(), wss.numel(), q,
+                                   st)
+            else:
+                rc = ms.ms_perm(ptrs[i], n, base_seed + i, wss.data_ptr(), wss.numel(), q, st)
+            assert rc == ms.MS_OK
+
+    per_launch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    per_launch()
+    e1.record()
+    torch.cuda.synchronize()
+    t_single = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
+    line = {
+        "metric": "Gelem/s", "value": round(total / (t_batch * 1e-3) / 1e9, 4),
+        "unit": "Gelem/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_batch, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32" if not large else "u64", "data": "synthetic",
+        "config": {
+            "workload": ("batched: 4096 perm(n_i) uint32, n_i log-uniform in [2^6, 2^20], "
+                         "seed_i = 1 + i" if not large else
+                         "batched large: 64 shuffles of uint64 arrays (splitmix64 values), "
+                         "n_i uniform in [1e6, 1e8] non-power-of-two, seed_i = 1 + i"),
+            "instances": len(sizes), "elements": total, "B": B,
+            "graph": "prepared batch replayed from one CUDA graph",
+            "device_bytes": int(nbytes + sum(n * w for n in sizes)),
+        },
+        "per_launch": {"ms": round(t_single, 3),
+                       "gelem_per_s": round(total / (t_single * 1e-3) / 1e9, 4),
+                       "how": "one ms_perm / ms_shuffle launch sequence per instance"},
+        "speedup_vs_per_launch": round(t_single / t_batch, 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals of perm(n) requests, n log-uniform in [2^10, 2^26], own seeds, under a
+    40 GB device-memory cap: the offered 20k req/s (about 121 Gelem/s) overloads one GPU, so the
+    window is short; a sub-saturation rate is served too, and one-at-a-time is the baseline."""
+    import torch
+
+    from paper_1508_03167_gb300 import serve
+
+    cap = 40 * (1 << 30)
+    out = {}
+    for tag, rate, dur in (("overload_20k_per_s", 20_000, args.serve_window),
+                           ("sub_saturation", args.serve_sub_rate, args.serve_sub_window)):
+        reqs = serve.make_requests(rate, dur, 10, 26, seed_base=1)
+        srv = serve.Server(arena_bytes=cap, B=args.B_perm, max_inflight=2)
+        st = srv.run(reqs, time_limit=600)
+        del srv
+        torch.cuda.empty_cache()
+        st["offered_rate_per_s"] = rate
+        st["window_s"] = dur
+        out[tag] = st
+    reqs = serve.make_requests(args.serve_sub_rate, args.serve_sub_window, 10, 26, seed_base=1)
+    out["one_at_a_time_sub_saturation"] = serve.one_at_a_time(reqs, B=args.B_perm)
+    line = {
+        "metric": "Gelem/s", "value": round(out["overload_20k_per_s"]["gelem_per_s"], 4),
+        "unit": "Gelem/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "dtype": "u32",
+        "config": {"workload": "serving: Poisson perm(n) requests, n log-uniform in "
+                               "[2^10, 2^26], own seeds, 40 GB device-memory cap, continuous "
+                               "batching over 2 streams", "B": args.B_perm},
+        "serving": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, large=False)
+    elif args.workload == "batched-large":
+        run_batched(args, large=True)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -99,3 +99,21 @@ def poisson_arrivals(rate_hz: float, duration_s: float, stream: int = S_ARR) -> 
     u = u01(stream, np.arange(expected))
     t = np.cumsum(-np.log1p(-u) / rate_hz)
     return t[t < duration_s]
+
+
+def values_u64_torch(n: int, array_id: int = 0, device="cuda"):
+    """values_u64 computed on the device with torch int64 arithmetic (same bits)."""
+    import torch
+
+    def shr(x, k):  # logical right shift of int64 bit patterns
+        return (x >> k) & ((1 << (64 - k)) - 1)
+
+    def s64(v):  # uint64 constant as a two's-complement int64
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    base = (S_VAL << 40) + (array_id << 27)
+    j = torch.arange(n, dtype=torch.int64, device=device)
+    z = j + s64((base + 0x9E3779B97F4A7C15) % (1 << 64))
+    z = (z ^ shr(z, 30)) * s64(0xBF58476D1CE4E5B9)
+    z = (z ^ shr(z, 27)) * s64(0x94D049BB133111EB)
+    return z ^ shr(z, 31)
