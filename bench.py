@@ -517,7 +517,7 @@ def run_serve(args):
     for tag, rate, dur in (("overload_20k_per_s", 20_000, args.serve_window),
                            ("sub_saturation", args.serve_sub_rate, args.serve_sub_window)):
         reqs = serve.make_requests(rate, dur, 10, 26, seed_base=1)
-        srv = serve.Server(arena_bytes=cap, B=args.B_perm, max_inflight=2)
+        srv = serve.Server(arena_bytes=cap, B=args.B_perm, max_inflight=4)
         st = srv.run(reqs, time_limit=600)
         del srv
         torch.cuda.empty_cache()
@@ -526,13 +526,15 @@ def run_serve(args):
         out[tag] = st
     reqs = serve.make_requests(args.serve_sub_rate, args.serve_sub_window, 10, 26, seed_base=1)
     out["one_at_a_time_sub_saturation"] = serve.one_at_a_time(reqs, B=args.B_perm)
+    reqs = serve.make_requests(20_000, args.serve_window, 10, 26, seed_base=1)
+    out["one_at_a_time_overload_20k_per_s"] = serve.one_at_a_time(reqs, B=args.B_perm)
     line = {
         "metric": "Gelem/s", "value": round(out["overload_20k_per_s"]["gelem_per_s"], 4),
         "unit": "Gelem/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "dtype": "u32",
         "config": {"workload": "serving: Poisson perm(n) requests, n log-uniform in "
                                "[2^10, 2^26], own seeds, 40 GB device-memory cap, continuous "
-                               "batching over 2 streams", "B": args.B_perm},
+                               "batching over 4 streams (small requests batched, large alone)", "B": args.B_perm},
         "serving": out,
     }
     print(json.dumps(line), flush=True)

@@ -372,12 +372,19 @@ constexpr uint32_t kEngineGrid = 320;  // persistent CTAs (2 per SM on a 152-SM 
 
 struct BatchLayout {
   size_t off_table = 0, off_queue = 0, off_scratch = 0, off_large = 0, total = 0;
-  std::vector<size_t> tmp_off;   // per instance: engine ping-pong buffer (SIZE_MAX if large)
+  std::vector<size_t> tmp_off;   // per instance: engine ping-pong buffer (SIZE_MAX otherwise)
   std::vector<uint32_t> order;   // engine instances, largest first
+  std::vector<uint32_t> large;   // instances for the single-instance path
   size_t scratch_per_cta = 0;
-  size_t large_ws = 0;
+  size_t large_ws = 0;           // one single-instance workspace
+  uint32_t large_streams = 0;    // single-instance workspaces (one per side stream)
 };
 
+constexpr uint32_t kBatchSideStreams = 4;
+
+// Which instances the engine takes: at most 2^22 elements, and -- since one CTA finishes an
+// instance alone -- none much larger than the batch's average share per CTA (the rest run
+// faster on the whole GPU through the single-instance path, a few of them concurrently).
 ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *params,
                        BatchLayout *L) {
   const ms_params r = resolve(params);
@@ -388,31 +395,82 @@ ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_par
   if (k > 0 && h_n == nullptr) return MS_ERR_INVALID;
   L->tmp_off.assign(k, SIZE_MAX);
   L->order.clear();
+  L->large.clear();
+  std::vector<uint32_t> cand;
+  uint64_t cand_total = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    if (h_n[i] > 0xFFFFFFFFull) return MS_ERR_INVALID;
+    if (h_n[i] >= 2 && h_n[i] <= msk::kEngineMaxN) {
+      cand.push_back(i);
+      cand_total += h_n[i];
+    } else if (h_n[i] > msk::kEngineMaxN) {
+      L->large.push_back(i);
+    }
+  }
+  std::stable_sort(cand.begin(), cand.end(),
+                   [&](uint32_t x, uint32_t y) { return h_n[x] > h_n[y]; });
+  size_t first = 0;
+  while (first < cand.size() && h_n[cand[first]] > (1u << 16) &&
+         h_n[cand[first]] * kEngineGrid > 2 * cand_total) {
+    cand_total -= h_n[cand[first]];
+    L->large.push_back(cand[first]);
+    ++first;
+  }
+  L->order.assign(cand.begin() + first, cand.end());
+  std::sort(L->large.begin(), L->large.end());
+  for (uint32_t i : L->large) {
+    const size_t ws = ms_workspace_bytes(h_n[i], w, params);
+    if (ws == 0) return MS_ERR_INVALID;
+    L->large_ws = std::max(L->large_ws, ws);
+  }
+  L->large_streams = static_cast<uint32_t>(
+      std::min<size_t>(L->large.size(), kBatchSideStreams));
   size_t off = msk::round_up(static_cast<size_t>(k) * msk::engine_inst_bytes() + 1, 256);
   L->off_table = 0;
   L->off_queue = off;
   off += 256;
-  for (uint32_t i = 0; i < k; ++i) {
-    if (h_n[i] > 0xFFFFFFFFull) return MS_ERR_INVALID;
-    if (h_n[i] >= 2 && h_n[i] <= msk::kEngineMaxN) {
-      L->tmp_off[i] = off;
-      off += msk::round_up(h_n[i] * w, 256);
-      L->order.push_back(i);
-    } else if (h_n[i] > msk::kEngineMaxN) {
-      const size_t ws = ms_workspace_bytes(h_n[i], w, params);
-      if (ws == 0) return MS_ERR_INVALID;
-      L->large_ws = std::max(L->large_ws, ws);
-    }
+  for (uint32_t i : L->order) {
+    L->tmp_off[i] = off;
+    off += msk::round_up(h_n[i] * w, 256);
   }
-  std::stable_sort(L->order.begin(), L->order.end(),
-                   [&](uint32_t x, uint32_t y) { return h_n[x] > h_n[y]; });
   L->scratch_per_cta =
       msk::round_up((2ull << msk::kEngineHbits) * 4 + 3ull * msk::kEngineKcap * 4, 256);
   L->off_scratch = off;
   if (!L->order.empty()) off += L->scratch_per_cta * kEngineGrid;
   L->off_large = off;
-  off += L->large_ws;
+  off += L->large_ws * L->large_streams;
   L->total = off;
+  return MS_OK;
+}
+
+// Side streams of the batch form (per device, created once): large instances fork off the
+// caller's stream onto them and join back before the call's work ends.
+struct SideStreams {
+  cudaStream_t s[kBatchSideStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kBatchSideStreams] = {};
+  bool ready = false;
+};
+
+ms_status side_streams(SideStreams **out) {
+  static std::mutex mu;
+  static SideStreams per_dev[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MS_ERR_CUDA;
+  std::lock_guard<std::mutex> g(mu);
+  SideStreams &S = per_dev[dev];
+  if (!S.ready) {
+    for (uint32_t i = 0; i < kBatchSideStreams; ++i) {
+      if (cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking) != cudaSuccess)
+        return MS_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&S.join[i], cudaEventDisableTiming) != cudaSuccess)
+        return MS_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess)
+      return MS_ERR_CUDA;
+    S.ready = true;
+  }
+  *out = &S;
   return MS_OK;
 }
 
@@ -498,17 +556,36 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
   }
   if (prof_lock.owns_lock()) prof_lock.unlock();
   for (uint32_t i = 0; i < k; ++i) {
-    if (h_n[i] <= 1) {
-      if (perm && h_n[i] == 1 &&
-          cudaMemsetAsync(h_ptrs[i], 0, 4, s) != cudaSuccess)
-        return MS_ERR_CUDA;
-      continue;
+    if (perm && h_n[i] == 1 && cudaMemsetAsync(h_ptrs[i], 0, 4, s) != cudaSuccess)
+      return MS_ERR_CUDA;
+  }
+  if (L.large.empty()) return MS_OK;
+  if (L.large_streams <= 1) {
+    for (uint32_t i : L.large) {
+      const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
+      const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large, L.large_ws,
+                               p, s);
+      if (rs != MS_OK) return rs;
     }
-    if (h_n[i] <= msk::kEngineMaxN) continue;
+    return MS_OK;
+  }
+  // several large instances: fork onto side streams, one workspace each, join back
+  SideStreams *S = nullptr;
+  if (side_streams(&S) != MS_OK) return MS_ERR_CUDA;
+  if (cudaEventRecord(S->fork, s) != cudaSuccess) return MS_ERR_CUDA;
+  for (uint32_t j = 0; j < L.large_streams; ++j)
+    if (cudaStreamWaitEvent(S->s[j], S->fork, 0) != cudaSuccess) return MS_ERR_CUDA;
+  for (size_t t = 0; t < L.large.size(); ++t) {
+    const uint32_t i = L.large[t];
+    const uint32_t j = static_cast<uint32_t>(t % L.large_streams);
     const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
-    const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large, L.large_ws,
-                             p, s);
+    const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large + j * L.large_ws,
+                             L.large_ws, p, S->s[j]);
     if (rs != MS_OK) return rs;
+  }
+  for (uint32_t j = 0; j < L.large_streams; ++j) {
+    if (cudaEventRecord(S->join[j], S->s[j]) != cudaSuccess) return MS_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, S->join[j], 0) != cudaSuccess) return MS_ERR_CUDA;
   }
   return MS_OK;
 }

@@ -2,11 +2,11 @@
 
 Requests (n, seed) arrive over time. The server keeps every buffer in one fixed device arena
 (allocated once), admits a pending request only when its memory fits the arena, and keeps up to
-`max_inflight` batches on the GPU at once, one CUDA stream each: requests that arrive while
+`max_inflight` launches on the GPU at once, one CUDA stream each: requests that arrive while
 others run are admitted as soon as memory and a launch slot free up, and their kernels overlap
-with the batches already in flight. A batch is one call of the batched form (persistent
-CTA-per-instance engine; the largest requests take the single-instance path inside the same
-call). Completion times come from CUDA events on the batch's stream, so latency = completion on
+with the work already in flight. Small requests (n <= small_cap) go out together as one call of
+the batched form (persistent CTA-per-instance engine); each larger request goes out alone, so it
+never waits for a batch and no small request waits for it. Completion times come from CUDA events on the batch's stream, so latency = completion on
 the GPU timeline - arrival, both measured from the same start.
 
 The arena allocator and the admission bookkeeping are plain Python (testable without a GPU);
@@ -86,8 +86,9 @@ def percentiles(xs, ps=(50, 99)):
 class Server:
     """Continuous-batching server over the batched C entry points."""
 
-    def __init__(self, arena_bytes: int, B: int = 128, max_inflight: int = 2,
-                 max_batch: int = 4096, device=None, keep_results: bool = False):
+    def __init__(self, arena_bytes: int, B: int = 128, max_inflight: int = 4,
+                 max_batch: int = 4096, device=None, keep_results: bool = False,
+                 small_cap: int = 1 << 18):
         import torch
 
         import paper_1508_03167_gb300 as ms
@@ -98,6 +99,7 @@ class Server:
         self.max_inflight = max_inflight
         self.max_batch = max_batch
         self.keep_results = keep_results
+        self.small_cap = small_cap
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self.arena_bytes = arena_bytes
         self.mem = torch.empty(arena_bytes, dtype=torch.uint8, device=self.device)
@@ -117,6 +119,33 @@ class Server:
 
     def _large_ws(self, n):
         return self.ms.ms_workspace_bytes(n, 4, self.ms.params(B=self.B))
+
+    def _admit(self, group):
+        """Allocate outputs for a prefix of `group` and the batch workspace; returns the admitted
+        requests (possibly none). The workspace block is left in self._ws_blk."""
+        batch, ns = [], []
+        est = self.FIXED_WS
+        for r in group:
+            extra = 4 * r.n if r.n <= self.ENGINE_MAX_N else self._large_ws(r.n)
+            if self.arena.capacity - self.arena.used < est + extra + 4 * r.n:
+                break
+            out_blk = self.arena.alloc(4 * r.n)
+            if out_blk is None:
+                break
+            r.out = out_blk
+            batch.append(r)
+            ns.append(r.n)
+            est += extra
+        self._ws_blk = None
+        while batch:
+            self._ws_blk = self.arena.alloc(self._batch_ws_bytes(ns))
+            if self._ws_blk is not None:
+                break
+            r = batch.pop()
+            ns.pop()
+            self.arena.release(r.out)
+            r.out = None
+        return batch
 
     def run(self, requests, time_limit: float = 600.0) -> dict:
         """Serve `requests` (sorted by arrival). Returns latency/throughput statistics."""
@@ -154,49 +183,40 @@ class Server:
                 else:
                     still.append((evt, si, reqs, wsb))
             inflight = still
-            # admission: while a launch slot is free, take pending requests in arrival order
-            # as long as their outputs and the batch workspace fit the arena
+            # admission: small requests (n <= small_cap) go out together as one batch on a free
+            # stream; every larger request goes out alone on its own free stream. Requests are
+            # taken in arrival order as long as their buffers fit the arena.
             if free_streams and pending:
-                batch, ns = [], []
-                est = self.FIXED_WS
-                for r in pending:
-                    if len(batch) >= self.max_batch:
+                smalls = [r for r in pending if r.n <= self.small_cap]
+                groups = []
+                if smalls:
+                    groups.append(smalls[:self.max_batch])
+                groups += [[r] for r in pending if r.n > self.small_cap]
+                launched = set()
+                for group in groups:
+                    if not free_streams:
                         break
-                    extra = 4 * r.n if r.n <= self.ENGINE_MAX_N else self._large_ws(r.n)
-                    if self.arena.capacity - self.arena.used < est + extra + 4 * r.n:
-                        break
-                    out_blk = self.arena.alloc(4 * r.n)
-                    if out_blk is None:
-                        break
-                    r.out = out_blk
-                    batch.append(r)
-                    ns.append(r.n)
-                    est += extra
-                ws_blk = None
-                while batch:
-                    ws_blk = self.arena.alloc(self._batch_ws_bytes(ns))
-                    if ws_blk is not None:
-                        break
-                    r = batch.pop()
-                    ns.pop()
-                    self.arena.release(r.out)
-                    r.out = None
-                if batch:
-                    del pending[:len(batch)]
+                    batch = self._admit(group)
+                    if not batch:
+                        continue
+                    ns = [r.n for r in batch]
+                    ws_blk = self._ws_blk
                     si = free_streams.pop()
                     st = self.streams[si]
                     ptrs = [self.base + r.out[0] for r in batch]
                     seeds = [r.seed for r in batch]
                     for r in batch:
                         r.admitted = now
-                    ws_ptr = self.base + ws_blk[0]
-                    rc = ms.ms_shuffle_batch(ptrs, ns, 4, seeds, 0, ws_ptr, ws_blk[1],
-                                             self.params, st.cuda_stream)
+                        launched.add(r.rid)
+                    rc = ms.ms_shuffle_batch(ptrs, ns, 4, seeds, 0, self.base + ws_blk[0],
+                                             ws_blk[1], self.params, st.cuda_stream)
                     if rc != ms.MS_OK:
                         raise ms.MsError(rc, "ms_shuffle_batch")
                     evt = torch.cuda.Event(enable_timing=True)
                     evt.record(st)
                     inflight.append((evt, si, batch, ws_blk))
+                if launched:
+                    pending = [r for r in pending if r.rid not in launched]
             if nxt >= len(requests) and not pending and not inflight:
                 break
             if time.perf_counter() - t0 > time_limit:
