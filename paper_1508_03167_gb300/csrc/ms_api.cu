@@ -163,19 +163,19 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     lv.warp_local = false;
     lv.warp_bytes = 0;
     lv.mlog = 0;
-    if (Nmax * w <= kWarpSpanBytes && !(flags & (MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS))) {
+    if (Nmax <= kWarpMergeMax && !(flags & (MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS))) {
+      // one warp per span of up to 16 merges (at most kWarpSpanMax elements), global to global
       uint32_t m = 0;
-      while (m < kLocalMaxMergesLog && (Nmax << (m + 1)) * w <= kWarpSpanBytes &&
-             (M >> (m + 1)) >= 1)
+      while (m < kLocalMaxMergesLog && (Nmax << (m + 1)) <= kWarpSpanMax && (M >> (m + 1)) >= 1)
         ++m;
       lv.local = true;
       lv.warp_local = true;
       lv.mlog = m;
       lv.span_max = static_cast<uint32_t>(ceil_scaled(n, lv.level + 1 + m, c));
       lv.ucap = level_units(n, c, lv.level + 1 + m, lv.level);
-      lv.tcap = static_cast<uint32_t>((lv.span_max / 4 + 16) & ~1u);
-      lv.warp_bytes = static_cast<uint32_t>(round_up(
-          static_cast<size_t>(lv.span_max) * w + 2ull * lv.ucap * 4 + 2ull * lv.tcap, 16));
+      const double per = std::sqrt(2.0 * static_cast<double>(Nmax) / 3.14159265358979) + 2.0;
+      lv.tcap = static_cast<uint32_t>((4.0 * per * (1u << m) + 64.0)) & ~1u;
+      lv.warp_bytes = static_cast<uint32_t>(round_up(2ull * lv.ucap * 4 + 6ull * lv.tcap, 16));
       lv.smem = 0;
       lv.kcap = 0;
       lv.hbits = 10;
@@ -359,8 +359,9 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     void *dst = (cur == data) ? b.other : data;
     const msk::LevelPlan &lv = p.levels[i];
-    const cudaError_t e = lv.local ? msk::launch_local_level(p, lv, cur, dst, seed, s)
-                                   : msk::launch_level(p, lv, cur, dst, b, seed, s);
+    const cudaError_t e = lv.warp_local ? msk::launch_warp_level(p, lv, cur, dst, seed, s)
+                          : lv.local    ? msk::launch_local_level(p, lv, cur, dst, seed, s)
+                                        : msk::launch_level(p, lv, cur, dst, b, seed, s);
     if (e != cudaSuccess) return MS_ERR_CUDA;
     cur = dst;
   }

@@ -64,7 +64,8 @@ __device__ __forceinline__ uint32_t draw_uniform(uint2 key, uint32_t tag, uint32
                                                  DrawMemo &memo) {
   if (R <= 1u) return 0u;
   const uint32_t b = 32u - __clz(R - 1u);
-  const uint32_t slices = 32u / b;
+  // floor(32 / b), exact: see the note in draw_from_word
+  const uint32_t slices = static_cast<uint32_t>(__fdividef(32.0f, static_cast<float>(b)));
   const uint32_t mask = (b == 32u) ? 0xFFFFFFFFu : ((1u << b) - 1u);
   const uint32_t c2 = (tag << 16) | level;
   for (uint32_t j = 0; j < (1u << 20); ++j) {

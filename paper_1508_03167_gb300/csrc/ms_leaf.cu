@@ -195,21 +195,29 @@ __global__ void __launch_bounds__(32) fy_kernel(LeafArgs a, uint32_t per_cta) {
                                                boundary(a.n, a.c, leaf));
       E *blk = blocks + lane * P;
       if (L >= 2u) {
+        // positions L-1 .. 1 in quads of four (one Philox block each), the block of the next
+        // quad computed while the current one is applied
         uint32_t quad = (L - 1u) >> 2;
         uint4 cur = philox10(make_uint4(quad, id, (kTagLeaf << 16), 0u), a.key);
-        uint4 nxt = cur;
-        for (uint32_t i = L - 1u; i >= 1u; --i) {
-          if ((i & 3u) == 3u || i == L - 1u) {
-            // entering quad i/4: start the Philox block of the quad below it
-            if (quad > 0) nxt = philox10(make_uint4(quad - 1u, id, (kTagLeaf << 16), 0u), a.key);
+        uint32_t i = L - 1u;
+        for (;;) {
+          const uint4 nxt = quad > 0
+                                ? philox10(make_uint4(quad - 1u, id, (kTagLeaf << 16), 0u), a.key)
+                                : cur;
+          const uint32_t lo = quad << 2;  // first position of this quad
+#pragma unroll
+          for (uint32_t v = 4; v-- > 0;) {
+            const uint32_t pos = lo + v;
+            if (pos <= i && pos >= 1u) {
+              const uint32_t j =
+                  draw_with_word0(a.key, kTagLeaf, 0u, id, pos, pos + 1u, pick_word(cur, v));
+              swap_smem(blk, pos, j);
+            }
           }
-          const uint32_t j = draw_with_word0(a.key, kTagLeaf, 0u, id, i, i + 1u,
-                                             pick_word(cur, i & 3u));
-          swap_smem(blk, i, j);
-          if ((i & 3u) == 0u) {
-            cur = nxt;
-            --quad;
-          }
+          if (quad == 0) break;
+          --quad;
+          i = lo - 1u;
+          cur = nxt;
         }
       }
     }

@@ -47,7 +47,9 @@ __device__ __forceinline__ bool draw_from_word(uint32_t word, uint32_t R, uint32
     x = first;
     return true;
   }
-  const uint32_t slices = 32u / b;
+  // floor(32 / b): 32 / b is either exact (b a power of two) or at least 1/32 away from an
+  // integer, far beyond the error of the fast reciprocal, so the truncation is exact
+  const uint32_t slices = static_cast<uint32_t>(__fdividef(32.0f, static_cast<float>(b)));
   for (uint32_t u = 1; u < slices; ++u) {
     const uint32_t v = (word >> (u * b)) & mask;
     if (v < R) {

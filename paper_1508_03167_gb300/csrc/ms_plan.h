@@ -16,7 +16,8 @@ constexpr uint32_t kChunk = 4096u;            // coin steps per HBM chunk (32 Ph
 constexpr uint32_t kDefaultTileBytes = 48u * 1024u;
 constexpr uint32_t kLocalSpanBytes = 32u * 1024u;  // staging of a local-mode merge level
 constexpr uint32_t kLocalMaxMergesLog = 4u;        // at most 16 merges per local CTA
-constexpr uint32_t kWarpSpanBytes = 8u * 1024u;    // staging of a warp-local merge span
+constexpr uint32_t kWarpMergeMax = 4096u;           // largest merge a single warp finishes
+constexpr uint32_t kWarpSpanMax = 8192u;            // elements of a warp's span of merges
 constexpr uint32_t kSmemLimit = 200u * 1024u; // dynamic shared memory budget of one CTA
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
@@ -120,6 +121,8 @@ cudaError_t launch_level(const Plan &p, const LevelPlan &lv, const void *in, voi
                          const Buffers &b, uint64_t seed, cudaStream_t s);
 cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                                uint64_t seed, cudaStream_t s);
+cudaError_t launch_warp_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                              uint64_t seed, cudaStream_t s);
 // Batch engine (ms_batch.cu): one persistent launch over a device table of instances.
 cudaError_t launch_engine(uint32_t w, bool perm, const void *inst, uint32_t k, uint32_t *queue,
                           uint32_t B, void *scratch, size_t scratch_per_cta, uint32_t kcap,
