@@ -71,7 +71,8 @@ typedef void *ms_stream_t;
                                         0..n_i-1 instead of shuffling it (w must be 4) */
 
 typedef struct {
-  uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B) */
+  uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B);
+                          0 = autotuned: taken from the tuning table (ms_resolve_params) */
   int32_t fuse_depth;  /* merge levels done in shared memory per tile; -1 = automatic */
   uint32_t flags;      /* MS_FLAG_* */
   uint32_t tile_bytes; /* shared-memory bytes per tile buffer for the automatic fusion depth;
@@ -103,6 +104,41 @@ typedef struct {
   uint64_t launches[MS_PROFILE_KINDS];   /* launches recorded */
   double ms[MS_PROFILE_KINDS];           /* summed event-to-event milliseconds */
 } ms_profile;
+
+/*
+ * Autotuner lookup. B = 0 in ms_params asks for the cutoff (and, where fuse_depth is -1 or the
+ * level-mode flags are unset, the fusion depth and level mode) measured fastest for the call's
+ * element width and size on a GB300. The paper leaves the cutoff open (Algorithm 3 only asks for
+ * "blocks of roughly the same size"; its listing takes it as a parameter); B changes the result
+ * (the block split depends on it), so the resolved value is a pure function of (n, w, installed
+ * table) and a caller who needs to reproduce a result records it.
+ *   ms_tune_entry            one row: applies to calls of width w, single (batch = 0) or batched
+ *                            (batch = 1), with ceil(log2 n) <= log2n_max (the smallest such
+ *                            bucket wins; beyond every bucket the largest applies). For batched
+ *                            calls n is the median instance size. flags may hold
+ *                            MS_FLAG_CTA_LEVELS / MS_FLAG_GLOBAL_LEVELS only.
+ *   ms_resolve_params        replaces B = 0 in *inout by the table's choice for (n, w); other
+ *                            fields are kept (fuse_depth only if it is not -1). MS_ERR_INVALID
+ *                            for a bad w or a NULL pointer.
+ *   ms_resolve_batch_params  the same for a batch of k sizes h_n (host array).
+ *   ms_tune_install          replaces the process-wide table by a copy of count rows (count = 0:
+ *                            back to the built-in table); MS_ERR_INVALID if a row is malformed.
+ *                            Thread-safe; calls already resolved keep their parameters.
+ *   ms_tune_table            copies up to cap rows of the current table to out (may be NULL) and
+ *                            returns the number of rows.
+ */
+typedef struct {
+  uint32_t w;
+  uint32_t batch;
+  uint32_t log2n_max;
+  uint32_t B;
+  int32_t fuse_depth;
+  uint32_t flags;
+} ms_tune_entry;
+ms_status ms_resolve_params(uint64_t n, uint32_t w, ms_params *inout);
+ms_status ms_resolve_batch_params(uint32_t k, const uint64_t *h_n, uint32_t w, ms_params *inout);
+ms_status ms_tune_install(const ms_tune_entry *entries, uint32_t count);
+uint32_t ms_tune_table(ms_tune_entry *out, uint32_t cap);
 
 /* Default parameters: B = 1024, automatic fusion depth, no flags. */
 void ms_default_params(ms_params *p);

@@ -20,7 +20,8 @@ __all__ = [
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
     "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
     "ms_status_string", "ms_version", "ms_perm_static", "MS_STATIC_MAX_N", "MS_STATIC_SCRATCH_BYTES", "params", "plan", "shuffle_", "perm", "shuffle_host",
-    "perm_host", "workspace",
+    "perm_host", "workspace", "MsTuneEntry", "ms_resolve_params", "ms_resolve_batch_params",
+    "ms_tune_install", "ms_tune_table", "resolve", "resolve_batch",
 ]
 
 MS_OK, MS_ERR_INVALID, MS_ERR_UNSUPPORTED, MS_ERR_NOMEM, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
@@ -59,6 +60,15 @@ class MsProfile(ctypes.Structure):
         return {self.names[k].value.decode(): {"launches": int(self.launches[k]),
                                               "ms": float(self.ms[k])}
                 for k in range(self.kinds)}
+
+
+class MsTuneEntry(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("log2n_max", ctypes.c_uint32), ("B", ctypes.c_uint32),
+                ("fuse_depth", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class MsError(RuntimeError):
@@ -116,6 +126,14 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = [u32, pvp, pu64, u32, pu64, u64, vp, sz, P, vp]
             fn.restype = i32
+        L.ms_resolve_params.argtypes = [u64, u32, P]
+        L.ms_resolve_params.restype = i32
+        L.ms_resolve_batch_params.argtypes = [u32, pu64, u32, P]
+        L.ms_resolve_batch_params.restype = i32
+        L.ms_tune_install.argtypes = [ctypes.POINTER(MsTuneEntry), u32]
+        L.ms_tune_install.restype = i32
+        L.ms_tune_table.argtypes = [ctypes.POINTER(MsTuneEntry), u32]
+        L.ms_tune_table.restype = u32
         L.ms_perm_static.argtypes = [vp, u64, u64, P, vp]
         L.ms_perm_static.restype = i32
         L.ms_profile_read.argtypes = [ctypes.POINTER(MsProfile), i32]
@@ -217,6 +235,40 @@ def ms_perm_static(d_out: int, n: int, seed: int, p: MsParams | None = None,
     return int(lib().ms_perm_static(d_out, n, seed, _p(p), stream))
 
 
+def ms_resolve_params(n: int, w: int, p: MsParams) -> MsParams:
+    """Copy of p with B = 0 replaced by the autotuner table's choice for (n, w)."""
+    out = MsParams(p.B, p.fuse_depth, p.flags, p.tile_bytes)
+    st = lib().ms_resolve_params(n, w, ctypes.byref(out))
+    if st != MS_OK:
+        raise MsError(st, "ms_resolve_params")
+    return out
+
+
+def ms_resolve_batch_params(ns, w: int, p: MsParams) -> MsParams:
+    out = MsParams(p.B, p.fuse_depth, p.flags, p.tile_bytes)
+    st = lib().ms_resolve_batch_params(len(ns), _u64s(ns), w, ctypes.byref(out))
+    if st != MS_OK:
+        raise MsError(st, "ms_resolve_batch_params")
+    return out
+
+
+def ms_tune_install(entries) -> None:
+    """Install a tuning table (a list of MsTuneEntry or dicts); an empty list restores the
+    built-in table."""
+    rows = [e if isinstance(e, MsTuneEntry) else MsTuneEntry(**e) for e in entries]
+    arr = (MsTuneEntry * max(len(rows), 1))(*rows)
+    st = lib().ms_tune_install(arr, len(rows))
+    if st != MS_OK:
+        raise MsError(st, "ms_tune_install")
+
+
+def ms_tune_table() -> list[dict]:
+    k = int(lib().ms_tune_table(None, 0))
+    arr = (MsTuneEntry * max(k, 1))()
+    k = int(lib().ms_tune_table(arr, k))
+    return [arr[i].as_dict() for i in range(k)]
+
+
 def ms_profile_read(reset: bool = True) -> MsProfile:
     out = MsProfile()
     st = lib().ms_profile_read(ctypes.byref(out), 1 if reset else 0)
@@ -245,6 +297,15 @@ def params(B: int = 1024, fuse_depth: int = -1, flags: int = 0, tile_bytes: int 
 
 def plan(n: int, w: int = 4, **kw) -> dict:
     return ms_plan_info(n, w, params(**kw)).as_dict()
+
+
+def resolve(n: int, w: int = 4, **kw) -> MsParams:
+    """Parameters a call on (n, w) runs with: B = 0 (autotuned) resolved by the tuning table."""
+    return ms_resolve_params(n, w, params(**kw))
+
+
+def resolve_batch(ns, w: int = 4, **kw) -> MsParams:
+    return ms_resolve_batch_params(list(ns), w, params(**kw))
 
 
 def _stream_handle(stream) -> int:

@@ -20,7 +20,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libmergeshuffle.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ms_api.cu", "ms_leaf.cu", "ms_level.cu", "ms_static.cu", "ms_batch.cu", "ms_wlevel.cu"]
+SOURCES = ["ms_api.cu", "ms_leaf.cu", "ms_level.cu", "ms_static.cu", "ms_batch.cu", "ms_wlevel.cu",
+           "ms_tune.cu"]
 
 _lock = threading.Lock()
 

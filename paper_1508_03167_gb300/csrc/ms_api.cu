@@ -229,6 +229,12 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
 
 using msk::Plan;
 
+namespace msk {
+// autotuner lookup (ms_tune.cu): B = 0 resolved from the tuning table
+ms_params resolve_single(uint64_t n, uint32_t w, const ms_params *p);
+ms_params resolve_batch(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *p);
+}  // namespace msk
+
 namespace {
 
 const char *const kKindNames[msk::kKindNum] = {
@@ -296,15 +302,8 @@ EventProfiler &profiler() {
 }
 std::mutex g_prof_mu;
 
-ms_params resolve(const ms_params *p) {
-  ms_params r;
-  ms_default_params(&r);
-  if (p) r = *p;
-  return r;
-}
-
 ms_status plan_for(uint64_t n, uint32_t w, const ms_params *p, Plan *plan) {
-  const ms_params r = resolve(p);
+  const ms_params r = msk::resolve_single(n, w, p);
   const int rc = msk::make_plan(n, w, r.B, r.fuse_depth, r.tile_bytes, r.flags, plan);
   if (rc == 1) return MS_ERR_INVALID;
   if (rc == 2) return MS_ERR_UNSUPPORTED;
@@ -388,7 +387,7 @@ constexpr uint32_t kBatchSideStreams = 4;
 // faster on the whole GPU through the single-instance path, a few of them concurrently).
 ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *params,
                        BatchLayout *L) {
-  const ms_params r = resolve(params);
+  const ms_params r = msk::resolve_batch(k, h_n, w, params);
   if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
   if ((r.flags & MS_FLAG_PERM) && w != 4) return MS_ERR_INVALID;
   if (r.B == 0) return MS_ERR_INVALID;
@@ -420,7 +419,7 @@ ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_par
   L->order.assign(cand.begin() + first, cand.end());
   std::sort(L->large.begin(), L->large.end());
   for (uint32_t i : L->large) {
-    const size_t ws = ms_workspace_bytes(h_n[i], w, params);
+    const size_t ws = ms_workspace_bytes(h_n[i], w, &r);
     if (ws == 0) return MS_ERR_INVALID;
     L->large_ws = std::max(L->large_ws, ws);
   }
@@ -537,7 +536,8 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
   BatchLayout L;
   const ms_status st = batch_check(k, h_ptrs, h_n, w, d_ws, ws_bytes, p, &L);
   if (st != MS_OK) return st;
-  const ms_params r = resolve(p);
+  // one B for the whole batch (large instances included)
+  const ms_params r = msk::resolve_batch(k, h_n, w, p);
   const bool perm = (r.flags & MS_FLAG_PERM) != 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_ws);
@@ -565,7 +565,7 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
     for (uint32_t i : L.large) {
       const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
       const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large, L.large_ws,
-                               p, s);
+                               &r, s);
       if (rs != MS_OK) return rs;
     }
     return MS_OK;
@@ -581,7 +581,7 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
     const uint32_t j = static_cast<uint32_t>(t % L.large_streams);
     const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
     const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large + j * L.large_ws,
-                             L.large_ws, p, S->s[j]);
+                             L.large_ws, &r, S->s[j]);
     if (rs != MS_OK) return rs;
   }
   for (uint32_t j = 0; j < L.large_streams; ++j) {

@@ -76,7 +76,7 @@ def test_plan_records():
 
 
 @pytest.mark.parametrize("n,w,B,status", [(100, 3, 16, ms.MS_ERR_INVALID),
-                                          (100, 4, 0, ms.MS_ERR_INVALID),
+                                          (100, 3, 0, ms.MS_ERR_INVALID),
                                           (2**32, 4, 16, ms.MS_ERR_INVALID),
                                           (100, 4, 5000, ms.MS_ERR_UNSUPPORTED)])
 def test_invalid_arguments_are_rejected_synchronously(n, w, B, status):

@@ -106,3 +106,17 @@ def test_prepared_batch_replays_from_a_cuda_graph():
         for i, n in enumerate(sizes):
             want, _ = oracle.perm(n, 3 + i, B)
             assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), want), i
+
+
+def test_autotuned_batch_runs_every_instance_at_the_batch_B():
+    """B = 0 in a batch resolves one B from the median size (the tuning table's batch row); every
+    instance, the large ones on the single-instance path included, uses it."""
+    import torch
+
+    sizes = [100, 3000, 65537, 1 << 20, (1 << 22) + 5]
+    B = ms.resolve_batch(sizes, 4, B=0).B
+    outs = [torch.full((n,), -1, dtype=torch.int32, device="cuda") for n in sizes]
+    _run_batch(outs, 4, 40, 0, perm=True)
+    for i, n in enumerate(sizes):
+        want, _ = oracle.perm(n, 40 + i, B)
+        assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), want), (i, n)

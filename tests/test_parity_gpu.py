@@ -139,3 +139,13 @@ def test_edge_sizes():
     for n in (64, 65, 128, 129):
         want, _ = oracle.perm(n, 2, 64)
         assert np.array_equal(gpu_perm(n, 2, 64), want)
+
+
+@pytest.mark.parametrize("n", [1000, 100003, 1 << 20])
+def test_autotuned_B_matches_oracle_at_the_resolved_B(n):
+    """B = 0 runs with the tuning table's B; the oracle with that B gives the same result."""
+    r = ms.resolve(n, 4, B=0)
+    assert r.B >= 1
+    got = gpu_perm(n, 11, 0)
+    want, _ = oracle.perm(n, 11, r.B)
+    assert np.array_equal(got, want)
