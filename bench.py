@@ -29,7 +29,7 @@ if ROOT not in sys.path:
 N_PERM = 1 << 30
 N_REC = 300_000_017
 SEED = 7
-DEFAULT_B = {"perm": 128, "rec": 128}
+DEFAULT_B = {"perm": 0, "rec": 0}  # 0: the autotuner's table chooses (reported as resolved)
 
 
 def parse():
@@ -41,8 +41,8 @@ def parse():
     ap.add_argument("--B-perm", type=int, default=DEFAULT_B["perm"])
     ap.add_argument("--B-rec", type=int, default=DEFAULT_B["rec"])
     ap.add_argument("--tile-bytes", type=int, default=0)
-    ap.add_argument("--fuse-depth", type=int, default=0,
-                    help="merge levels fused into the base-block kernel (-1: automatic)")
+    ap.add_argument("--fuse-depth", type=int, default=-1,
+                    help="merge levels fused into the base-block kernel (-1: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-window", type=float, default=0.25,
                     help="seconds of 20k/s arrivals in the serving overload run")
@@ -176,10 +176,11 @@ def run_ours(args, world, rank, local):
     n_rec = (1 << 24) + 17 if args.small else N_REC
     seed = SEED + rank
     flags = ms.MS_FLAG_PROFILE
-    p_perm = ms.params(B=args.B_perm, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes,
-                       flags=flags)
-    p_rec = ms.params(B=args.B_rec, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes,
-                      flags=flags)
+    # B = 0 resolves through the autotuner's table; the resolved parameters define the result
+    p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=args.fuse_depth,
+                        tile_bytes=args.tile_bytes, flags=flags)
+    p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=args.fuse_depth,
+                       tile_bytes=args.tile_bytes, flags=flags)
     plan_perm = ms.ms_plan_info(n_perm, 4, p_perm)
     plan_rec = ms.ms_plan_info(n_rec, 16, p_rec)
 
@@ -261,8 +262,10 @@ def run_ours(args, world, rank, local):
         hp = torch.empty(n_perm, dtype=torch.int32, pin_memory=True)
         hr = torch.empty((n_rec, 4), dtype=torch.int32, pin_memory=True)
         hr.copy_(rec_host)
-        q_perm = ms.params(B=args.B_perm, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes)
-        q_rec = ms.params(B=args.B_rec, fuse_depth=args.fuse_depth, tile_bytes=args.tile_bytes)
+        q_perm = ms.params(B=p_perm.B, fuse_depth=p_perm.fuse_depth, tile_bytes=args.tile_bytes,
+                           flags=p_perm.flags & ~ms.MS_FLAG_PROFILE)
+        q_rec = ms.params(B=p_rec.B, fuse_depth=p_rec.fuse_depth, tile_bytes=args.tile_bytes,
+                          flags=p_rec.flags & ~ms.MS_FLAG_PROFILE)
         wsh_perm = torch.empty(ms.ms_host_workspace_bytes(n_perm, 4, q_perm), dtype=torch.uint8,
                                device=dev)
         wsh_rec = torch.empty(ms.ms_host_workspace_bytes(n_rec, 16, q_rec), dtype=torch.uint8,
@@ -292,7 +295,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args)
+        cpu = cpu_baseline(p_perm.B, p_rec.B)
 
     line = {
         "metric": "Gelem/s",
@@ -312,7 +315,8 @@ def run_ours(args, world, rank, local):
                          "n=300000017 16-byte records {u32 key, 12-byte splitmix64 payload}, seed 7"
                          if not args.small else "small profiling case: perm 2^26 + 2^24+17 records"),
             "n_perm": n_perm, "n_rec": n_rec, "seed": SEED,
-            "B_perm": args.B_perm, "B_rec": args.B_rec,
+            "B_perm": p_perm.B, "B_rec": p_rec.B,
+            "B_source": "autotuner table" if args.B_perm == 0 else "command line",
             "fuse_depth_perm": plan_perm.fuse_depth, "fuse_depth_rec": plan_rec.fuse_depth,
             "passes_perm": plan_perm.passes, "passes_rec": plan_rec.passes,
             "l2": "inputs larger than L2 (4.3 GB and 4.8 GB arrays), no flush",
@@ -331,22 +335,23 @@ def run_ours(args, world, rank, local):
 
 
 # ------------------------------------------------------------------ CPU oracle --------------
-def cpu_baseline(args) -> dict:
-    """The oracle as it stands on one host core, on a bounded sample of the workload."""
+def cpu_baseline(B_perm: int, B_rec: int) -> dict:
+    """The oracle as it stands on one host core, on a bounded sample of the workload (the same
+    element mix as the GPU step, 1/32 of its perm and 1/36 of its records: about 10-20 s)."""
     import oracle
     from paper_1508_03167_gb300 import inputs
 
-    n1 = 1 << 23
-    n2 = 1 << 21
+    n1 = 1 << 25
+    n2 = 1 << 23
     rec = inputs.records16(n2)
     t0 = time.perf_counter()
-    oracle.perm(n1, SEED, args.B_perm)
-    oracle.shuffle(rec, SEED, args.B_rec)
+    oracle.perm(n1, SEED, B_perm)
+    oracle.shuffle(rec, SEED, B_rec)
     dt = time.perf_counter() - t0
     return {"value": round((n1 + n2) / dt / 1e9, 6), "unit": "Gelem/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"perm(2^23) u32 + shuffle(2^21) 16-byte records, B={args.B_perm}/"
-                      f"{args.B_rec}, single-threaded C oracle, {dt:.1f} s"}
+            "sample": f"perm(2^25) u32 + shuffle(2^23) 16-byte records, B={B_perm}/{B_rec}, "
+                      f"single-threaded C oracle, {dt:.1f} s"}
 
 
 def run_reference(args, world, rank):
@@ -354,15 +359,19 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
+    import paper_1508_03167_gb300 as ms
     from paper_1508_03167_gb300 import inputs
 
     n1 = 1 << 21
     n2 = 1 << 19
     rec = inputs.records16(n2)
+    # the B the GPU arm runs the full-size workload with (host-side table lookup, no GPU)
+    B_perm = ms.resolve(N_PERM, 4, B=args.B_perm).B
+    B_rec = ms.resolve(N_REC, 16, B=args.B_rec).B
 
     def step():
-        oracle.perm(n1, SEED, args.B_perm)
-        oracle.shuffle(rec, SEED, args.B_rec)
+        oracle.perm(n1, SEED, B_perm)
+        oracle.shuffle(rec, SEED, B_rec)
 
     for _ in range(args.warmup):
         step()
@@ -372,7 +381,7 @@ def run_reference(args, world, rank):
     dt = (time.perf_counter() - t0) / args.steps
     value = (n1 + n2) / dt / 1e9
     sample = (f"per step: perm(2^21) u32 + shuffle(2^19) 16-byte records of the same workload, "
-              f"B={args.B_perm}/{args.B_rec}, single-threaded C oracle")
+              f"B={B_perm}/{B_rec}, single-threaded C oracle")
     line = {
         "impl": "reference",
         "metric": "Gelem/s",
@@ -438,6 +447,9 @@ def run_batched(args, large: bool):
         w, B, flags = 4, args.B_perm, ms.MS_FLAG_PERM
         bufs = [torch.empty(n, dtype=torch.int32, device="cuda") for n in sizes]
         base_seed = 1
+    # one B for the batch (B = 0: the autotuner's batch row); the per-launch baseline uses the
+    # same B, so both produce the same permutations
+    B = ms.resolve_batch(sizes, w, B=B, flags=flags).B
     p = ms.params(B=B, flags=flags)
     ptrs = [b.data_ptr() for b in bufs]
     nbytes = ms.ms_batch_workspace_bytes(sizes, w, p)
@@ -512,12 +524,19 @@ def run_serve(args):
 
     from paper_1508_03167_gb300 import serve
 
+    import paper_1508_03167_gb300 as ms
+
     cap = 40 * (1 << 30)
     out = {}
+    # one B for every request (results must not depend on which batch a request joins): the
+    # autotuner's batch row for the request-size distribution
+    B = ms.resolve_batch(
+        [r.n for r in serve.make_requests(args.serve_sub_rate, args.serve_sub_window, 10, 26)],
+        4, B=args.B_perm, flags=ms.MS_FLAG_PERM).B
     for tag, rate, dur in (("overload_20k_per_s", 20_000, args.serve_window),
                            ("sub_saturation", args.serve_sub_rate, args.serve_sub_window)):
         reqs = serve.make_requests(rate, dur, 10, 26, seed_base=1)
-        srv = serve.Server(arena_bytes=cap, B=args.B_perm, max_inflight=4)
+        srv = serve.Server(arena_bytes=cap, B=B, max_inflight=4)
         st = srv.run(reqs, time_limit=600)
         del srv
         torch.cuda.empty_cache()
@@ -525,16 +544,16 @@ def run_serve(args):
         st["window_s"] = dur
         out[tag] = st
     reqs = serve.make_requests(args.serve_sub_rate, args.serve_sub_window, 10, 26, seed_base=1)
-    out["one_at_a_time_sub_saturation"] = serve.one_at_a_time(reqs, B=args.B_perm)
+    out["one_at_a_time_sub_saturation"] = serve.one_at_a_time(reqs, B=B)
     reqs = serve.make_requests(20_000, args.serve_window, 10, 26, seed_base=1)
-    out["one_at_a_time_overload_20k_per_s"] = serve.one_at_a_time(reqs, B=args.B_perm)
+    out["one_at_a_time_overload_20k_per_s"] = serve.one_at_a_time(reqs, B=B)
     line = {
         "metric": "Gelem/s", "value": round(out["overload_20k_per_s"]["gelem_per_s"], 4),
         "unit": "Gelem/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "dtype": "u32",
         "config": {"workload": "serving: Poisson perm(n) requests, n log-uniform in "
                                "[2^10, 2^26], own seeds, 40 GB device-memory cap, continuous "
-                               "batching over 4 streams (small requests batched, large alone)", "B": args.B_perm},
+                               "batching over 4 streams (small requests batched, large alone)", "B": B},
         "serving": out,
     }
     print(json.dumps(line), flush=True)

@@ -93,6 +93,10 @@ class Server:
 
         import paper_1508_03167_gb300 as ms
 
+        if B < 1:
+            # B = 0 would resolve per batch (by its median size), so a request's result would
+            # depend on which requests it was batched with; resolve one B up front instead
+            raise ValueError("the server needs an explicit cutoff B (see ms.resolve_batch)")
         self.ms = ms
         self.torch = torch
         self.B = B
