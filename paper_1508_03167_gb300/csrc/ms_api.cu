@@ -56,19 +56,20 @@ LeafSmem leaf_smem(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
   L.tile_max = static_cast<uint32_t>(tile_max);
   const uint64_t padded = (1ull << d) * L.stride;
   L.buf0 = static_cast<uint32_t>(std::max<uint64_t>(padded, tile_max));
-  L.ucap_w = 1;
+  // coin-word capacities in multiples of four words: the arrays start 16-byte aligned
+  L.ucap_w = 4;
   for (uint32_t lam = 0; lam < L.dw; ++lam)
-    L.ucap_w = std::max(L.ucap_w, level_units(n, c, L.dw, lam));
-  L.ucap_c = 1;
+    L.ucap_w = std::max(L.ucap_w, (level_units(n, c, L.dw, lam) + 3u) & ~3u);
+  L.ucap_c = 4;
   for (uint32_t lam = L.dw; lam < d; ++lam)
-    L.ucap_c = std::max(L.ucap_c, level_units(n, c, d, lam));
+    L.ucap_c = std::max(L.ucap_c, (level_units(n, c, d, lam) + 3u) & ~3u);
   const uint64_t wtile = ceil_scaled(n, L.dw, c);
   L.tcap_w = static_cast<uint32_t>((wtile / 4 + 16) & ~1ull);
   L.tcap_c = static_cast<uint32_t>((tile_max / 4 + 16) & ~1ull);
   L.aux_w = static_cast<uint32_t>(round_up(2ull * L.ucap_w * 4 + 2ull * L.tcap_w, 16));
   const size_t aux_c = round_up(2ull * L.ucap_c * 4 + 2ull * L.tcap_c, 16);
   const size_t aux = std::max<size_t>(8ull * L.aux_w, aux_c);
-  L.bytes = round_up(static_cast<size_t>(L.buf0) * w + tile_max * w + aux, 16);
+  L.bytes = round_up(static_cast<size_t>(L.buf0) * w + tile_max * w, 16) + round_up(aux, 16);
   return L;
 }
 
@@ -187,10 +188,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       lv.local = true;
       lv.mlog = m;
       lv.span_max = static_cast<uint32_t>(ceil_scaled(n, lv.level + 1 + m, c));
-      lv.ucap = level_units(n, c, lv.level + 1 + m, lv.level);
+      lv.ucap = (level_units(n, c, lv.level + 1 + m, lv.level) + 3u) & ~3u;
       lv.tcap = static_cast<uint32_t>((lv.span_max / 4 + 16) & ~1u);
-      lv.smem = round_up(static_cast<size_t>(lv.span_max) * w + 2ull * lv.ucap * 4 +
-                             2ull * lv.tcap, 16);
+      lv.smem = round_up(static_cast<size_t>(lv.span_max) * w, 16) +
+                round_up(2ull * lv.ucap * 4 + 2ull * lv.tcap, 16);
       lv.kcap = 0;
       lv.hbits = 10;
     }

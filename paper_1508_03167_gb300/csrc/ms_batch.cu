@@ -61,9 +61,9 @@ __device__ __forceinline__ uint64_t span_bytes_needed(const LeafArgs &a, uint32_
   const uint32_t gl = m + lvl + 1u;
   const uint64_t span_max = ((a.n << gl) + a.q - 1u) >> a.c;
   const uint64_t Nmax = ((a.n << (lvl + 1u)) + a.q - 1u) >> a.c;
-  const uint64_t units = (1ull << m) * ((Nmax + 31u) >> 5);
+  const uint64_t units = ((1ull << m) * ((Nmax + 31u) >> 5) + 3u) & ~3ull;
   const uint64_t tcap = (span_max / 4u + 16u) & ~1ull;
-  return span_max * sizeof(E) + units * 8u + tcap * 2u + 64u;
+  return span_max * sizeof(E) + 16u + units * 8u + tcap * 2u + 64u;
 }
 
 // per-CTA scratch layout (global memory): hash keys, hash values, draws, destinations
@@ -432,19 +432,7 @@ __global__ void __launch_bounds__(kEngThreads, 2) engine_kernel(EngineArgs g) {
           const uint64_t leaf = lb + tid;
           const uint32_t L = static_cast<uint32_t>(boundary(a.n, c, leaf + 1) -
                                                    boundary(a.n, c, leaf));
-          E *blk = blocks + tid * a.stride;
-          uint4 qw = make_uint4(0, 0, 0, 0);
-          uint32_t quad = 0xFFFFFFFFu;
-          for (uint32_t i = L; i-- > 1u;) {
-            if ((i >> 2) != quad) {
-              quad = i >> 2;
-              qw = philox10(make_uint4(quad, static_cast<uint32_t>(leaf), (kTagLeaf << 16), 0u),
-                            a.key);
-            }
-            const uint32_t j = draw_with_word0(a.key, kTagLeaf, 0u, static_cast<uint32_t>(leaf),
-                                               i, i + 1u, pick_word(qw, i & 3u));
-            swap_smem(blk, i, j);
-          }
+          fisher_yates_block(blocks + tid * a.stride, L, static_cast<uint32_t>(leaf), a.key);
         }
         __syncthreads();
         for (uint32_t k = warp; k < cnt; k += kEngWarps) {
@@ -473,11 +461,11 @@ __global__ void __launch_bounds__(kEngThreads, 2) engine_kernel(EngineArgs g) {
         const uint32_t Mt = 1u << m;
         const uint32_t Wm = static_cast<uint32_t>((Nmax + 31u) >> 5);
         a.tile_max = static_cast<uint32_t>(span_max);
-        a.ucap_c = Mt * Wm;
+        a.ucap_c = (Mt * Wm + 3u) & ~3u;  // the prefixes start 16-byte aligned too
         a.tcap_c = static_cast<uint32_t>((span_max / 4u + 16u) & ~1ull);
         GroupSmem S;
         E *stage = reinterpret_cast<E *>(smem_raw);
-        S.cw = reinterpret_cast<uint32_t *>(stage + span_max);
+        S.cw = reinterpret_cast<uint32_t *>(align16(stage + span_max));
         S.zp = S.cw + a.ucap_c;
         S.mv = reinterpret_cast<uint16_t *>(S.zp + a.ucap_c);
         S.ucap = a.ucap_c;
@@ -490,7 +478,8 @@ __global__ void __launch_bounds__(kEngThreads, 2) engine_kernel(EngineArgs g) {
           const uint64_t lb = sp << gl;
           const uint64_t g0 = boundary(a.n, c, lb);
           const uint32_t len = static_cast<uint32_t>(boundary(a.n, c, lb + (1ull << gl)) - g0);
-          merge_level<kEngWarps, E>(a, S, lb, lb, g0, lvl, gl, cur + g0, len, false, stage);
+          merge_level<kEngWarps, E>(a, S, lb, lb, g0, lvl, gl, cur + g0, len, false, stage,
+                                    cur + g0, len);
           for (uint32_t i = tid; i < len; i += kEngThreads) other[g0 + i] = stage[i];
           __syncthreads();
         }

@@ -14,9 +14,10 @@
 // Base blocks sit at an odd stride in buffer 0, so the lanes of a warp (all at the same
 // Fisher-Yates step i) hit 32 different banks; merge level 0 reads that layout and writes
 // buffer 1 contiguously; later levels ping-pong between the buffers.
-// Every gather issues a batch of independent shared-memory loads before its stores; every merge
-// tail (the random insertions) has its draws computed in parallel, then one thread per merge
-// applies its swaps in order, eight at a time whenever those eight provably commute.
+// Every gather takes one lane per output position (conflict-free stores, loads in two runs) and
+// issues several words' loads before their stores; every merge tail (the random insertions) has
+// its draws and the final positions of the elements it moves computed in parallel, then the
+// moved values are read into the level's dead input buffer and written back.
 #include "ms_merge.cuh"
 
 namespace msk {
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
 
   E *const buf0 = reinterpret_cast<E *>(smem_raw);
   E *const buf1 = buf0 + a.buf0;
-  unsigned char *const aux = reinterpret_cast<unsigned char *>(buf1 + a.tile_max);
+  unsigned char *const aux = align16(buf1 + a.tile_max);
 
   const E *in = static_cast<const E *>(a.in);
   E *out = static_cast<E *>(a.out);
@@ -76,48 +77,33 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
     const uint64_t g1 = boundary(a.n, a.c, leaf0 + (1ull << a.d));
     const uint32_t len = static_cast<uint32_t>(g1 - g0);
 
+    // ---------------- load: one warp per base block (perm: the identity is generated) -------
+    const uint32_t nleaves = 1u << a.d;
+    for (uint32_t k = warp; k < nleaves; k += kLeafWarps) {
+      const uint64_t bs = boundary(a.n, a.c, leaf0 + k);
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf0 + k + 1) - bs);
+      E *blk = buf0 + k * P;
+      if constexpr (kPerm) {
+        for (uint32_t i = lane; i < L; i += 32u) blk[i] = static_cast<E>(bs + i);
+      } else {
+        for (uint32_t i = lane; i < L; i += 32u) blk[i] = in[bs + i];
+      }
+    }
+    __syncthreads();
+    // ---------------- Algorithm 1: one thread per base block (odd stride: distinct banks) ----
+    for (uint32_t k = tid; k < nleaves; k += kLeafThreads) {
+      const uint64_t leaf = leaf0 + k;
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
+                                               boundary(a.n, a.c, leaf));
+      fisher_yates_block(buf0 + k * P, L, static_cast<uint32_t>(leaf), a.key);
+    }
+    __syncthreads();
     if (warp < nwt) {
       // ---------------- warp phase: base blocks [lb, lb + 2^dw) ----------------
       const uint64_t lb = leaf0 + static_cast<uint64_t>(warp) * wleaves;
-      // load (perm: the identity is generated in place, one lane per block)
-      if constexpr (kPerm) {
-        for (uint32_t k = lane; k < wleaves; k += 32u) {
-          const uint64_t bs = boundary(a.n, a.c, lb + k);
-          const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
-          E *blk = buf0 + (warp * wleaves + k) * P;
-          for (uint32_t i = 0; i < L; ++i) blk[i] = static_cast<E>(bs + i);
-        }
-      } else {
-        for (uint32_t k = 0; k < wleaves; ++k) {
-          const uint64_t bs = boundary(a.n, a.c, lb + k);
-          const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
-          E *blk = buf0 + (warp * wleaves + k) * P;
-          for (uint32_t i = lane; i < L; i += 32u) blk[i] = in[bs + i];
-        }
-      }
-      __syncwarp();
-      // Algorithm 1, one lane per base block; one Philox block serves four positions
-      for (uint32_t k = lane; k < wleaves; k += 32u) {
-        const uint64_t leaf = lb + k;
-        const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
-                                                 boundary(a.n, a.c, leaf));
-        E *blk = buf0 + (warp * wleaves + k) * P;
-        uint4 qw = make_uint4(0, 0, 0, 0);
-        uint32_t quad = 0xFFFFFFFFu;
-        for (uint32_t i = L; i-- > 1u;) {
-          if ((i >> 2) != quad) {
-            quad = i >> 2;
-            qw = philox10(make_uint4(quad, static_cast<uint32_t>(leaf), (kTagLeaf << 16), 0u),
-                          a.key);
-          }
-          const uint32_t j = draw_with_word0(a.key, kTagLeaf, 0u, static_cast<uint32_t>(leaf),
-                                             i, i + 1u, pick_word(qw, i & 3u));
-          swap_smem(blk, i, j);
-        }
-      }
-      __syncwarp();
       if (a.dw > 0)
-        merge_level<1, E>(a, Sw, lb, leaf0, g0, 0u, a.dw, buf0, a.buf0, true, buf1);
+        merge_level<1, E>(a, Sw, lb, leaf0, g0, 0u, a.dw, buf0, a.buf0, true, buf1,
+                          buf0 + warp * wleaves * P, wleaves * P);
     }
     // buffer 0 switches from the padded layout to the contiguous one
     __syncthreads();
@@ -125,8 +111,11 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
     E *Y = (a.dw > 0) ? buf0 : buf1;
     if (warp < nwt) {
       const uint64_t lb = leaf0 + static_cast<uint64_t>(warp) * wleaves;
+      // this warp's range of the tile (its tail scratch on every warp level)
+      const uint32_t w0 = static_cast<uint32_t>(boundary(a.n, a.c, lb) - g0);
+      const uint32_t wn = static_cast<uint32_t>(boundary(a.n, a.c, lb + wleaves) - g0) - w0;
       for (uint32_t lam = 1; lam < a.dw; ++lam) {
-        merge_level<1, E>(a, Sw, lb, leaf0, g0, lam, a.dw, X, a.tile_max, false, Y);
+        merge_level<1, E>(a, Sw, lb, leaf0, g0, lam, a.dw, X, a.tile_max, false, Y, X + w0, wn);
         E *t = X;
         X = Y;
         Y = t;
@@ -143,7 +132,8 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
     for (uint32_t lam = a.dw; lam < a.d; ++lam) {
       const bool padded = (lam == 0);  // only when the warp phase is empty
       merge_level<kLeafWarps, E>(a, Sc, leaf0, leaf0, g0, lam, a.d, X,
-                                 padded ? a.buf0 : a.tile_max, padded, Y);
+                                 padded ? a.buf0 : a.tile_max, padded, Y, X,
+                                 padded ? a.buf0 : a.tile_max);
       E *t = X;
       X = Y;
       Y = t;
@@ -159,7 +149,6 @@ __global__ void __launch_bounds__(kLeafThreads, 2) leaf_kernel(LeafArgs a) {
 // Fisher-Yates only (d = 0): one warp per CTA, one lane per base block. The blocks of a CTA sit
 // at an odd stride in shared memory, so the lanes (all at the same step) hit distinct banks.
 // Loads and stores go block by block with all 32 lanes, so global accesses stay coalesced.
-// The Philox block of the next quad of positions is computed one quad ahead.
 template <typename E, bool kPerm>
 __global__ void __launch_bounds__(32) fy_kernel(LeafArgs a, uint32_t per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -190,36 +179,9 @@ __global__ void __launch_bounds__(32) fy_kernel(LeafArgs a, uint32_t per_cta) {
     __syncwarp();
     if (lane < cnt) {
       const uint64_t leaf = lb + lane;
-      const uint32_t id = static_cast<uint32_t>(leaf);
       const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
                                                boundary(a.n, a.c, leaf));
-      E *blk = blocks + lane * P;
-      if (L >= 2u) {
-        // positions L-1 .. 1 in quads of four (one Philox block each), the block of the next
-        // quad computed while the current one is applied
-        uint32_t quad = (L - 1u) >> 2;
-        uint4 cur = philox10(make_uint4(quad, id, (kTagLeaf << 16), 0u), a.key);
-        uint32_t i = L - 1u;
-        for (;;) {
-          const uint4 nxt = quad > 0
-                                ? philox10(make_uint4(quad - 1u, id, (kTagLeaf << 16), 0u), a.key)
-                                : cur;
-          const uint32_t lo = quad << 2;  // first position of this quad
-#pragma unroll
-          for (uint32_t v = 4; v-- > 0;) {
-            const uint32_t pos = lo + v;
-            if (pos <= i && pos >= 1u) {
-              const uint32_t j =
-                  draw_with_word0(a.key, kTagLeaf, 0u, id, pos, pos + 1u, pick_word(cur, v));
-              swap_smem(blk, pos, j);
-            }
-          }
-          if (quad == 0) break;
-          --quad;
-          i = lo - 1u;
-          cur = nxt;
-        }
-      }
+      fisher_yates_block(blocks + lane * P, L, static_cast<uint32_t>(leaf), a.key);
     }
     __syncwarp();
     for (uint32_t k = 0; k < cnt; ++k) {
@@ -289,7 +251,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) local_level_kernel(LeafArgs a
   __shared__ uint32_t merges[8][kGroupMerges];
   E *const stage = reinterpret_cast<E *>(smem_raw);
   GroupSmem S;
-  S.cw = reinterpret_cast<uint32_t *>(stage + a.tile_max);
+  S.cw = reinterpret_cast<uint32_t *>(align16(stage + a.tile_max));
   S.zp = S.cw + a.ucap_c;
   S.mv = reinterpret_cast<uint16_t *>(S.zp + a.ucap_c);
   S.ucap = a.ucap_c;
@@ -305,48 +267,11 @@ __global__ void __launch_bounds__(kLeafThreads, 2) local_level_kernel(LeafArgs a
     const uint64_t lb = sp << gl;
     const uint64_t g0 = boundary(a.n, a.c, lb);
     const uint32_t len = static_cast<uint32_t>(boundary(a.n, a.c, lb + (1ull << gl)) - g0);
-    merge_level<kLeafWarps, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage);
+    // the input span is dead once gathered: it holds the tail patches
+    merge_level<kLeafWarps, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage,
+                               const_cast<E *>(in) + g0, len);
     for (uint32_t i = threadIdx.x; i < len; i += kLeafThreads) out[g0 + i] = stage[i];
     __syncthreads();
-  }
-}
-
-// The same with one warp per span: each warp finishes its own 2^m small merges (warp barriers
-// only), so the SM interleaves many independent warps. 4 warps per CTA share nothing but the
-// CTA's shared memory allocation.
-constexpr uint32_t kWarpLocalWarps = 4;
-template <typename E>
-__global__ void __launch_bounds__(kWarpLocalWarps * 32, 8)
-    warp_local_level_kernel(LeafArgs a, uint32_t lam, uint32_t m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint32_t merges[kWarpLocalWarps][8][kGroupMerges];
-  const uint32_t warp = threadIdx.x >> 5;
-  unsigned char *base = smem_raw + warp * a.aux_w;
-  E *const stage = reinterpret_cast<E *>(base);
-  GroupSmem S;
-  S.cw = reinterpret_cast<uint32_t *>(stage + a.tile_max);
-  S.zp = S.cw + a.ucap_c;
-  S.mv = reinterpret_cast<uint16_t *>(S.zp + a.ucap_c);
-  S.ucap = a.ucap_c;
-  S.tcap = a.tcap_c;
-  S.m_a = merges[warp][0]; S.m_b = merges[warp][1]; S.m_s = merges[warp][2];
-  S.m_n1 = merges[warp][3]; S.m_N = merges[warp][4]; S.m_T = merges[warp][5];
-  S.m_off = merges[warp][6]; S.m_lb = merges[warp][7];
-  S.scratch = nullptr;
-  const E *in = static_cast<const E *>(a.in);
-  E *out = static_cast<E *>(a.out);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t gl = m + lam + 1u;
-  const uint64_t spans = a.q >> gl;
-  const uint64_t nwarps = static_cast<uint64_t>(gridDim.x) * kWarpLocalWarps;
-  for (uint64_t sp = static_cast<uint64_t>(blockIdx.x) * kWarpLocalWarps + warp; sp < spans;
-       sp += nwarps) {
-    const uint64_t lb = sp << gl;
-    const uint64_t g0 = boundary(a.n, a.c, lb);
-    const uint32_t len = static_cast<uint32_t>(boundary(a.n, a.c, lb + (1ull << gl)) - g0);
-    merge_level<1, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage);
-    for (uint32_t i = lane; i < len; i += 32u) out[g0 + i] = stage[i];
-    __syncwarp();
   }
 }
 
@@ -370,20 +295,6 @@ cudaError_t launch_local_t(const Plan &p, const LevelPlan &lv, const void *in, v
   a.ucap_c = lv.ucap;
   a.tcap_c = lv.tcap;
   a.aux_w = lv.warp_bytes;
-  if (lv.warp_local) {
-    auto wk = warp_local_level_kernel<E>;
-    const size_t smem = static_cast<size_t>(lv.warp_bytes) * kWarpLocalWarps;
-    cudaError_t e2 = cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(smem));
-    if (e2 != cudaSuccess) return e2;
-    const uint64_t spans = p.q >> (lv.mlog + lv.level + 1u);
-    const uint64_t blocks = (spans + kWarpLocalWarps - 1) / kWarpLocalWarps;
-    const uint64_t grid = blocks < 1048576ull ? blocks : 1048576ull;
-    if (p.prof) p.prof->begin(kKindLocal, s);
-    wk<<<static_cast<unsigned>(grid), kWarpLocalWarps * 32, smem, s>>>(a, lv.level, lv.mlog);
-    if (p.prof) p.prof->end(s);
-    return cudaGetLastError();
-  }
   auto kern = local_level_kernel<E>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(lv.smem));

@@ -31,6 +31,13 @@ struct LeafArgs {
   uint32_t aux_w;      // bytes of one warp's auxiliary region
 };
 
+// first 16-byte boundary at or after p
+template <typename T>
+__device__ __forceinline__ unsigned char *align16(T *p) {
+  return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15u) &
+                                           ~static_cast<uintptr_t>(15u));
+}
+
 template <typename E>
 __device__ __forceinline__ void swap_smem(E *a, uint32_t i, uint32_t j) {
   const E t = a[i];
@@ -81,6 +88,35 @@ __device__ __forceinline__ uint32_t draw_with_word0(uint2 key, uint32_t tag, uin
   return draw_continue(key, tag, level, id, pos, R);
 }
 
+// Algorithm 1 (descending Fisher-Yates) on one base block of L elements in shared memory:
+// for i = L-1 .. 1, swap blk[i] with blk[j], j uniform in {0..i} from the LEAF stream of block
+// `id` at position i. Positions go in quads (one Philox block serves four of them), and the
+// block of the next quad is computed while the current one is applied.
+template <typename E>
+__device__ __forceinline__ void fisher_yates_block(E *blk, uint32_t L, uint32_t id, uint2 key) {
+  if (L < 2u) return;
+  uint32_t quad = (L - 1u) >> 2;
+  uint4 cur = philox10(make_uint4(quad, id, (kTagLeaf << 16), 0u), key);
+  uint32_t i = L - 1u;
+  for (;;) {
+    const uint4 nxt =
+        quad > 0 ? philox10(make_uint4(quad - 1u, id, (kTagLeaf << 16), 0u), key) : cur;
+    const uint32_t lo = quad << 2;  // first position of this quad
+#pragma unroll
+    for (uint32_t v = 4; v-- > 0;) {
+      const uint32_t pos = lo + v;
+      if (pos <= i && pos >= 1u) {
+        const uint32_t j = draw_with_word0(key, kTagLeaf, 0u, id, pos, pos + 1u, pick_word(cur, v));
+        swap_smem(blk, pos, j);
+      }
+    }
+    if (quad == 0) break;
+    --quad;
+    i = lo - 1u;
+    cur = nxt;
+  }
+}
+
 // ---------------------------------------------------------------------------- groups ------
 // A group is one warp (G = 1) or the whole CTA (G = kLeafWarps).
 template <int G>
@@ -125,17 +161,15 @@ struct GroupSmem {
 // blocks become 2^(gl-lam-1) runs. lb = global index of the region's first base block; the
 // tile-relative positions are relative to g0 (global position of the tile's first element).
 // X is read as base blocks at stride P (padded) on level 0 of the warp phase, contiguous
-// otherwise (X may also be global memory); Y is written contiguously.
+// otherwise (X may also be global memory); Y is written contiguously. V (vcap elements, this
+// group's own) is scratch for the tail patches: the level's input, dead once the gather is done.
 template <int G, typename E>
 __device__ __forceinline__ void merge_level(const LeafArgs &a, const GroupSmem &S, uint64_t lb,
                                             uint64_t leaf0, uint64_t g0, uint32_t lam,
                                             uint32_t gl, const E *X, uint32_t xcap, bool padded,
-                                            E *Y) {
+                                            E *Y, E *V, uint32_t vcap) {
   using Gp = Group<G>;
   constexpr uint32_t kT = Gp::kThreads;
-  // consecutive positions per lane in the gather, kLpw lanes per coin word
-  constexpr uint32_t kPos = sizeof(E) >= 16 ? 4u : 8u;
-  constexpr uint32_t kLpw = 32u / kPos;
   const uint32_t gt = Gp::tid();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t Mt = 1u << (gl - lam - 1u);
@@ -257,42 +291,70 @@ __device__ __forceinline__ void merge_level(const LeafArgs &a, const GroupSmem &
   }
   Gp::sync();
 
-  // ---- stable interleave and leftover copy: kLpw lanes per coin word, kPos positions per lane;
-  // all loads of a lane are issued before its stores
-  for (uint32_t u = gt / kLpw; u < U; u += kT / kLpw) {
-    const uint32_t r = merge_of(u);
-    const uint32_t j = u - r * Wm;
-    const uint32_t N = S.m_N[r];
-    const uint32_t sub = (gt % kLpw) * kPos;
-    const uint32_t t0 = 32u * j + sub;
-    if (t0 >= N) continue;
-    const uint32_t word = S.cw[u];
-    const uint32_t Zu = S.zp[u];
-    const uint32_t aa = S.m_a[r], bb = S.m_b[r], T = S.m_T[r], lbase = S.m_lb[r];
-    const uint32_t dst = S.m_s[r] + t0;
-    const uint32_t cnt = min(kPos, N - t0);
-    uint32_t z = Zu + __popc(~word & low_mask(sub));  // Z + zbase at position t0
-    E v[kPos];
+  // ---- stable interleave and leftover copy: one lane per position, so a warp covers one coin
+  // word (32 consecutive outputs: conflict-free stores; the loads are two runs, one per half).
+  // A warp takes four consecutive words at a time (one vector load of their coin words and one
+  // of their prefixes; the merge's bases loaded once when all four lie in one merge) and issues
+  // the four loads of its lanes before their stores.
+  {
+    constexpr uint32_t kWords = 4;
+    const uint32_t wg = gt >> 5;
+    const uint32_t lt = low_mask(lane);  // lanes below this one
+    const bool vec =
+        ((reinterpret_cast<uintptr_t>(S.cw) | reinterpret_cast<uintptr_t>(S.zp)) & 15u) == 0;
+    for (uint32_t u0 = wg * kWords; u0 < U; u0 += G * kWords) {
+      uint32_t cwv[kWords], zpv[kWords];
+      if (vec && u0 + kWords <= U) {
+        const uint4 c4 = *reinterpret_cast<const uint4 *>(S.cw + u0);
+        const uint4 z4 = *reinterpret_cast<const uint4 *>(S.zp + u0);
+        cwv[0] = c4.x; cwv[1] = c4.y; cwv[2] = c4.z; cwv[3] = c4.w;
+        zpv[0] = z4.x; zpv[1] = z4.y; zpv[2] = z4.z; zpv[3] = z4.w;
+      } else {
 #pragma unroll
-    for (uint32_t k = 0; k < kPos; ++k) {
-      if (k < cnt) {
-        const uint32_t t = t0 + k;
-        const uint32_t bit = (word >> (sub + k)) & 1u;
-        const uint32_t src = (t < T) ? (bit ? bb + t - z : aa + z) : lbase + t;
-        z += bit ^ 1u;
-        v[k] = X[min(src, xcap - 1u)];  // clamp keeps the read inside the buffer
+        for (uint32_t k = 0; k < kWords; ++k) {
+          cwv[k] = u0 + k < U ? S.cw[u0 + k] : 0u;
+          zpv[k] = u0 + k < U ? S.zp[u0 + k] : 0u;
+        }
       }
-    }
+      const uint32_t r0 = merge_of(u0);
+      const bool one_merge = merge_of(min(u0 + kWords - 1u, U - 1u)) == r0;
+      const uint32_t N0 = S.m_N[r0], T0 = S.m_T[r0], A0 = S.m_a[r0], B0 = S.m_b[r0],
+                     L0 = S.m_lb[r0], s0 = S.m_s[r0];
+      E v[kWords];
+      uint32_t dst[kWords];
 #pragma unroll
-    for (uint32_t k = 0; k < kPos; ++k)
-      if (k < cnt) Y[dst + k] = v[k];
+      for (uint32_t k = 0; k < kWords; ++k) {
+        dst[k] = kNone;
+        const uint32_t u = u0 + k;
+        if (u < U) {
+          uint32_t r = r0, N = N0, T = T0, aa = A0, bb = B0, lbase = L0, sb = s0;
+          if (!one_merge) {
+            r = merge_of(u);
+            N = S.m_N[r]; T = S.m_T[r]; aa = S.m_a[r]; bb = S.m_b[r];
+            lbase = S.m_lb[r]; sb = S.m_s[r];
+          }
+          const uint32_t t = 32u * (u - r * Wm) + lane;
+          if (t < N) {
+            const uint32_t word = cwv[k];
+            const uint32_t z = zpv[k] + __popc(~word & lt);  // Z + zbase at t
+            const uint32_t src =
+                (t < T) ? (((word >> lane) & 1u) ? bb + t - z : aa + z) : lbase + t;
+            v[k] = X[min(src, xcap - 1u)];  // clamp keeps the read inside the buffer
+            dst[k] = sb + t;
+          }
+        }
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < kWords; ++k)
+        if (dst[k] != kNone) Y[dst[k]] = v[k];
+    }
   }
 
   // ---- tail draws, one Philox block per four consecutive positions
   const uint32_t Q = total >> 16;
   const uint32_t K = total & 0xFFFFu;
-  const bool precomputed = K <= S.tcap;
-  if (precomputed) {
+  const bool drawn = K <= S.tcap;
+  if (drawn) {
     for (uint32_t gq = gt; gq < Q; gq += kT) {
       uint32_t lo = 0, hi = Mt;  // largest r with quad offset <= gq
       while (hi - lo > 1u) {
@@ -317,51 +379,129 @@ __device__ __forceinline__ void merge_level(const LeafArgs &a, const GroupSmem &
   }
   Gp::sync();
 
-  // ---- random insertion of positions T..N-1, in order (Algorithm 2's second loop)
-  constexpr uint32_t kBatch = sizeof(E) >= 16 ? 4u : 8u;
-  for (uint32_t r = gt; r < Mt; r += kT) {
-    const uint32_t T = S.m_T[r], N = S.m_N[r], s = S.m_s[r];
-    E *C = Y + s;
-    uint32_t i = T;
-    if (precomputed) {
-      const uint16_t *mk = S.mv + (S.m_off[r] & 0xFFFFu);  // mk[i - T] = draw of position i
-      while (i < N) {
-        if (i + kBatch <= N) {
-          // swaps (i+k, m_k) for k < kBatch commute when every m_k lies before the window and
-          // all m_k differ: then they touch 2*kBatch distinct positions
-          uint32_t m[kBatch];
-          bool ok = true;
-#pragma unroll
-          for (uint32_t k = 0; k < kBatch; ++k) {
-            m[k] = mk[i - T + k];
-            ok &= m[k] < i;
-          }
-#pragma unroll
-          for (uint32_t k = 0; k < kBatch; ++k)
-#pragma unroll
-            for (uint32_t l = k + 1; l < kBatch; ++l) ok &= m[k] != m[l];
-          if (ok) {
-            E lo[kBatch], hi[kBatch];
-#pragma unroll
-            for (uint32_t k = 0; k < kBatch; ++k) {
-              lo[k] = C[i + k];
-              hi[k] = C[m[k]];
-            }
-#pragma unroll
-            for (uint32_t k = 0; k < kBatch; ++k) {
-              C[i + k] = hi[k];
-              C[m[k]] = lo[k];
-            }
-            i += kBatch;
-            continue;
-          }
-        }
-        swap_smem(C, i, static_cast<uint32_t>(mk[i - T]));
-        ++i;
+  // ---- random insertion of positions T..N-1 (Algorithm 2's second loop), resolved in parallel:
+  // the element at tail position i lands on m_i at step i and moves on to T + s at every later
+  // step s whose draw hits its position; the element a first hit displaces from m < T follows
+  // the same rule from position i. Final positions are found for every tail step at once, then
+  // all moved values are read (into the dead input buffer V) before any is written back.
+  const bool parallel = drawn && (2ull * K * sizeof(E) + 4ull * K <= 1ull * vcap * sizeof(E));
+  if (parallel) {
+    uint32_t *const fin = reinterpret_cast<uint32_t *>(V + 2u * K);  // d1 | d2 << 16 per step
+    auto merge_of_step = [&](uint32_t g) {
+      uint32_t lo = 0, hi = Mt;  // largest r with tail offset <= g
+      while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((S.m_off[mid] & 0xFFFFu) <= g) lo = mid;
+        else hi = mid;
       }
-    } else {
-      const uint32_t id = static_cast<uint32_t>(rbase + r);
-      for (; i < N; ++i) swap_smem(C, i, draw_uniform(a.key, kTagTail, lam, id, i, i + 1u));
+      return lo;
+    };
+    for (uint32_t g = gt; g < K; g += kT) {
+      const uint32_t r = merge_of_step(g);
+      const uint32_t koff = S.m_off[r] & 0xFFFFu;
+      const uint32_t T = S.m_T[r];
+      const uint32_t k_r = S.m_N[r] - T;
+      const uint16_t *mr = S.mv + koff;  // mr[st] = draw of position T + st
+      const uint32_t st = g - koff;
+      const uint32_t m = mr[st];
+      // follow an element from position pos after step `from - 1` (eight draws loaded at a
+      // time, then compared in order)
+      auto follow = [&](uint32_t pos, uint32_t from) {
+        uint32_t s2 = from;
+        for (; s2 + 8u <= k_r; s2 += 8u) {
+          uint32_t d[8];
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k) d[k] = mr[s2 + k];
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k)
+            if (d[k] == pos) pos = T + s2 + k;
+        }
+        for (; s2 < k_r; ++s2)
+          if (mr[s2] == pos) pos = T + s2;
+        return pos;
+      };
+      const uint32_t d1 = follow(m, st + 1u);
+      uint32_t d2 = 0xFFFFu;
+      if (m < T) {
+        uint32_t hits = 0;
+        uint32_t s2 = 0;
+        for (; s2 + 8u <= st; s2 += 8u) {
+#pragma unroll
+          for (uint32_t k = 0; k < 8u; ++k) hits += (mr[s2 + k] == m);
+        }
+        for (; s2 < st; ++s2) hits += (mr[s2] == m);
+        if (hits == 0) d2 = follow(T + st, st + 1u);
+      }
+      fin[g] = d1 | (d2 << 16);
+    }
+    Gp::sync();
+    for (uint32_t g = gt; g < K; g += kT) {
+      const uint32_t r = merge_of_step(g);
+      const uint32_t koff = S.m_off[r] & 0xFFFFu;
+      const uint32_t C = S.m_s[r];
+      const uint32_t i = S.m_T[r] + (g - koff);
+      V[g] = Y[C + i];
+      if ((fin[g] >> 16) != 0xFFFFu) V[K + g] = Y[C + S.mv[g]];
+    }
+    Gp::sync();
+    for (uint32_t g = gt; g < K; g += kT) {
+      const uint32_t r = merge_of_step(g);
+      const uint32_t koff = S.m_off[r] & 0xFFFFu;
+      const uint32_t C = S.m_s[r];
+      const uint32_t i = S.m_T[r] + (g - koff);
+      const uint32_t f = fin[g];
+      const uint32_t d1 = f & 0xFFFFu, d2 = f >> 16;
+      if (d1 != i) Y[C + d1] = V[g];
+      if (d2 != 0xFFFFu) Y[C + d2] = V[K + g];
+    }
+  } else {
+    // sequential fallback (more tail steps than the scratch holds): one thread per merge
+    // applies the swaps in order, eight at a time whenever those eight provably commute
+    constexpr uint32_t kBatch = sizeof(E) >= 16 ? 4u : 8u;
+    for (uint32_t r = gt; r < Mt; r += kT) {
+      const uint32_t T = S.m_T[r], N = S.m_N[r], s = S.m_s[r];
+      E *C = Y + s;
+      uint32_t i = T;
+      if (drawn) {
+        const uint16_t *mk = S.mv + (S.m_off[r] & 0xFFFFu);  // mk[i - T] = draw of position i
+        while (i < N) {
+          if (i + kBatch <= N) {
+            // swaps (i+k, m_k) for k < kBatch commute when every m_k lies before the window and
+            // all m_k differ: then they touch 2*kBatch distinct positions
+            uint32_t m[kBatch];
+            bool ok = true;
+#pragma unroll
+            for (uint32_t k = 0; k < kBatch; ++k) {
+              m[k] = mk[i - T + k];
+              ok &= m[k] < i;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < kBatch; ++k)
+#pragma unroll
+              for (uint32_t l = k + 1; l < kBatch; ++l) ok &= m[k] != m[l];
+            if (ok) {
+              E lo[kBatch], hi[kBatch];
+#pragma unroll
+              for (uint32_t k = 0; k < kBatch; ++k) {
+                lo[k] = C[i + k];
+                hi[k] = C[m[k]];
+              }
+#pragma unroll
+              for (uint32_t k = 0; k < kBatch; ++k) {
+                C[i + k] = hi[k];
+                C[m[k]] = lo[k];
+              }
+              i += kBatch;
+              continue;
+            }
+          }
+          swap_smem(C, i, static_cast<uint32_t>(mk[i - T]));
+          ++i;
+        }
+      } else {
+        const uint32_t id = static_cast<uint32_t>(rbase + r);
+        for (; i < N; ++i) swap_smem(C, i, draw_uniform(a.key, kTagTail, lam, id, i, i + 1u));
+      }
     }
   }
   Gp::sync();
