@@ -3,8 +3,8 @@
  *
  * MergeShuffle (Bacher, Bodini, Hollender, Lumbroso, arXiv 1508.03167) permutes an array
  * uniformly at random: split it into q = 2^c base blocks, shuffle each block with Fisher-Yates
- * (Algorithm 1), then merge adjacent blocks level by level (Algorithm 3) with the random merge
- * of Algorithm 2 -- coins interleave the two halves until one runs out, and the leftovers are
+ * (Algorithm 1), then merge adjacent blocks level by level (Algorithm 2) with the random merge
+ * of Algorithm 3 -- coins interleave the two halves until one runs out, and the leftovers are
  * placed by random insertion.
  *
  * Result definition ("MS-Philox v1"). The output is a pure function of (input, n, seed, B):
@@ -14,7 +14,7 @@
  *   - the merge interleaves the halves stably (coin t = 0: next unused element of the first half,
  *     1: of the second half) until a coin asks for an exhausted half at step T; the other half's
  *     remaining elements follow in order; then for i = T..N-1, swap positions i and m_i,
- *     m_i uniform in {0..i} (Algorithm 2's second loop);
+ *     m_i uniform in {0..i} (Algorithm 3's second loop);
  *   - coin t of merge (l, r) is bit t%32 of word (t/32)%4 of Philox4x32-10(counter =
  *     (t/128, r, 0x10000|l, 0), key = (lo32(seed), hi32(seed)));
  *   - a uniform draw in [0, R) for stream (tag, level, id, pos) takes b = ceil(log2 R) bits
@@ -108,7 +108,7 @@ typedef struct {
 /*
  * Autotuner lookup. B = 0 in ms_params asks for the cutoff (and, where fuse_depth is -1 or the
  * level-mode flags are unset, the fusion depth and level mode) measured fastest for the call's
- * element width and size on a GB300. The paper leaves the cutoff open (Algorithm 3 only asks for
+ * element width and size on a GB300. The paper leaves the cutoff open (Algorithm 2 only asks for
  * "blocks of roughly the same size"; its listing takes it as a parameter); B changes the result
  * (the block split depends on it), so the resolved value is a pure function of (n, w, installed
  * table) and a caller who needs to reproduce a result records it.
@@ -150,7 +150,7 @@ ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *p, ms_plan *out)
 size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *p);
 
 /*
- * Permute d_data[0..n) in place, uniformly at random (Algorithm 3 of the paper), stream-ordered.
+ * Permute d_data[0..n) in place, uniformly at random (Algorithm 2 of the paper), stream-ordered.
  *   d_data  device pointer to n elements of w bytes (w in {4, 8, 16}); w-byte aligned
  *           (16-byte aligned for w = 16). Elements are moved as opaque w-byte records.
  *   n       0 <= n <= 2^32 - 1 (the paper's 32-bit n); n <= 1 returns MS_OK and launches

@@ -213,7 +213,7 @@ static void fisher_yates(ms_src *src, unsigned char *a, uint64_t len, uint32_t w
   }
 }
 
-/* ------------------------------------------------------------------ Algorithm 2 --------- */
+/* ------------------------------------------------------------------ Algorithm 3 --------- */
 /* Random insertion that finishes every merge ("one list is depleted; use Fisher-Yates to finish
  * merging"): for i = T .. N-1, m uniform in {0..i}, swap C[i] and C[m]. */
 static void merge_tail(ms_src *src, unsigned char *c, uint64_t T, uint64_t N, uint32_t w,
@@ -260,7 +260,7 @@ static uint64_t merge_stable(ms_src *src, const unsigned char *A, uint64_t n1,
   return T;
 }
 
-/* Algorithm 2 as printed (in place): i walks the output, j the second half; a 1-coin swaps
+/* Algorithm 3 as printed (in place): i walks the output, j the second half; a 1-coin swaps
  * T[i] with T[j] and advances j; either way i advances unless the requested half is empty. */
 static uint64_t merge_literal(ms_src *src, unsigned char *a, uint64_t n1, uint64_t n2,
                               uint32_t w, uint32_t level, uint32_t id, ms_oracle_stats *st) {
@@ -285,7 +285,7 @@ static uint64_t merge_literal(ms_src *src, unsigned char *a, uint64_t n1, uint64
   return T;
 }
 
-/* ------------------------------------------------------------------ Algorithm 3 --------- */
+/* ------------------------------------------------------------------ Algorithm 2 --------- */
 /* Split into q = 2^c blocks, Fisher-Yates each block, then merge adjacent blocks level by level:
  * on level l (p = 2^l) merge r joins [b(2pr), b(2pr+p)) and [b(2pr+p), b(2pr+2p)). */
 static int run_mergeshuffle(ms_src *src, unsigned char *data, uint64_t n, uint32_t w, uint32_t B,

@@ -9,10 +9,10 @@
  *
  * The oracle is a plain, single-threaded restatement of the paper:
  *   - Algorithm 1 (Fisher-Yates, descending form) on each base block,
- *   - Algorithm 3 (MergeShuffle driver) with the block split of the appendix listing
+ *   - Algorithm 2 (MergeShuffle driver) with the block split of the appendix listing
  *     (q = 2^c blocks, c the smallest integer with floor(n / 2^c) <= cutoff, boundaries
  *     floor(n * i / q)),
- *   - Algorithm 2 (Merge): coin loop until one side is exhausted, then random insertion
+ *   - Algorithm 3 (Merge): coin loop until one side is exhausted, then random insertion
  *     of every remaining position (the "Fisher-Yates to finish merging" loop).
  *
  * Two merge placements are provided:
@@ -23,7 +23,7 @@
  *                        the BalancedShuffle correctness lemma (Section 3.2) and by the Merge
  *                        lemma's conditioning argument (Section 2.1). This is the definition the
  *                        GPU path reproduces bit for bit.
- *   MS_ORACLE_LITERAL -- Algorithm 2 exactly as printed: in-place swaps, which rotate the
+ *   MS_ORACLE_LITERAL -- Algorithm 3 exactly as printed: in-place swaps, which rotate the
  *                        unconsumed part of the first half. Same coins, same break step, same
  *                        tail draws, so the same number of random bits; different output.
  *

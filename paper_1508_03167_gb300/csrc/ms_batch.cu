@@ -1,7 +1,7 @@
 // ms_batch.cu -- batched MergeShuffle (arXiv 1508.03167) for many independent instances.
 //
 // One persistent launch: every CTA repeatedly takes the next instance from an atomic queue
-// (instances are queued largest first) and runs the whole of Algorithm 3 on it alone, so no CTA
+// (instances are queued largest first) and runs the whole of Algorithm 2 on it alone, so no CTA
 // ever waits for another:
 //   * Fisher-Yates on the base blocks (Algorithm 1), one thread per block, blocks staged in
 //     shared memory at an odd stride;
@@ -10,7 +10,7 @@
 //     kernels), tails included;
 //   * larger merges: zero counts of the coins per 4096-step chunk, their prefix and the break
 //     step, then a chunk-by-chunk streaming gather from one buffer to the other, then the merge
-//     tail (Algorithm 2's random insertions) replayed on indices through a hash table in the
+//     tail (Algorithm 3's random insertions) replayed on indices through a hash table in the
 //     CTA's own scratch and applied as patches.
 // Instances too large for one CTA are run by the single-instance path (same result).
 #include "ms_merge.cuh"

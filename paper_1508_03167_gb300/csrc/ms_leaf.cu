@@ -2,7 +2,7 @@
 //
 // A tile is loaded into shared memory (or generated as the identity for perm), every base block
 // is shuffled by Fisher-Yates (Algorithm 1 of arXiv 1508.03167, descending form), and merge
-// levels 0..d-1 of Algorithm 3 run inside shared memory with the stable random merge (Algorithm 2:
+// levels 0..d-1 of Algorithm 2 run inside shared memory with the stable random merge (Algorithm 3:
 // coin interleave until one half is exhausted, leftovers in order, then random insertion).
 // The tile is written back once, so this kernel is the first of the 1 + (c - d) HBM passes.
 //

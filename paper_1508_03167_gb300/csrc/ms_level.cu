@@ -1,14 +1,14 @@
-// ms_level.cu -- one merge level of Algorithm 3 (arXiv 1508.03167) streamed through HBM.
+// ms_level.cu -- one merge level of Algorithm 2 (arXiv 1508.03167) streamed through HBM.
 //
 // Every merge r of level l joins two shuffled halves [s, mid) and [mid, e). The merge is split
 // into data-oblivious planning and one streaming pass:
 //   count    zero coins per 4096-step chunk of every merge (Philox only, no array traffic);
 //   scan     per merge: exclusive prefix of the chunk counts and the break step T, where a coin
-//            first asks for an exhausted half (Algorithm 2's first loop);
+//            first asks for an exhausted half (Algorithm 3's first loop);
 //   kscan    prefix of the tail lengths N - T over the level's merges;
 //   insert   tail draws m_i (i = T..N-1, uniform in {0..i}) into a hash table keyed by
 //            (merge, target position);
-//   resolve  replays the random insertions (Algorithm 2's second loop) on indices only: every
+//   resolve  replays the random insertions (Algorithm 3's second loop) on indices only: every
 //            displaced element's trajectory gives one (destination, source) patch;
 //   gather   the streaming pass: out[s+t] = coin t ? B[t - Z_t] : A[Z_t] for t < T, the
 //            remainder of the non-exhausted half for t >= T (coalesced reads of both halves);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) patch_write_kernel(LevelArgs a) {
   }
 }
 
-// fallback: Algorithm 2's second loop as printed, one thread per merge, in place
+// fallback: Algorithm 3's second loop as printed, one thread per merge, in place
 template <typename E>
 __global__ void __launch_bounds__(kThreads) tail_sequential_kernel(LevelArgs a) {
   if (!a.ctrl[1]) return;

@@ -1,7 +1,7 @@
 // ms_merge.cuh -- device building blocks shared by the base-block, local-level and batch
 // kernels: rejection draws from a given Philox word, warp / CTA groups, and one merge level of
-// Algorithm 3 (arXiv 1508.03167) executed by a group over a region held in (or read from)
-// memory, with the stable interleave of Algorithm 2 and its random-insertion tail.
+// Algorithm 2 (arXiv 1508.03167) executed by a group over a region held in (or read from)
+// memory, with the stable interleave of Algorithm 3 and its random-insertion tail.
 #pragma once
 
 #include "ms_common.cuh"
@@ -157,7 +157,7 @@ struct GroupSmem {
   uint32_t *scratch;  // 33 words for CTA-wide scans
 };
 
-// One merge level of Algorithm 3 over the group's region: 2^(gl-lam) merged runs of 2^lam base
+// One merge level of Algorithm 2 over the group's region: 2^(gl-lam) merged runs of 2^lam base
 // blocks become 2^(gl-lam-1) runs. lb = global index of the region's first base block; the
 // tile-relative positions are relative to g0 (global position of the tile's first element).
 // X is read as base blocks at stride P (padded) on level 0 of the warp phase, contiguous
@@ -379,7 +379,7 @@ __device__ __forceinline__ void merge_level(const LeafArgs &a, const GroupSmem &
   }
   Gp::sync();
 
-  // ---- random insertion of positions T..N-1 (Algorithm 2's second loop), resolved in parallel:
+  // ---- random insertion of positions T..N-1 (Algorithm 3's second loop), resolved in parallel:
   // the element at tail position i lands on m_i at step i and moves on to T + s at every later
   // step s whose draw hits its position; the element a first hit displaces from m < T follows
   // the same rule from position i. Final positions are found for every tail step at once, then

@@ -1,11 +1,11 @@
 // ms_wlevel.cu -- one HBM merge level of small merges, one warp per span of merges.
 //
-// Each warp takes 2^m consecutive merges of level l (Algorithm 3 of arXiv 1508.03167) and
+// Each warp takes 2^m consecutive merges of level l (Algorithm 2 of arXiv 1508.03167) and
 // finishes them alone, with warp barriers only, straight from one global buffer to the other:
-//   coins, zero prefix and break step T of every merge in shared memory (Algorithm 2's first
+//   coins, zero prefix and break step T of every merge in shared memory (Algorithm 3's first
 //   loop); the stable interleave written directly to the output with one lane per position, so
 //   every store instruction covers 32 consecutive elements and every load instruction two short
-//   runs of the halves; then the merge tails (Algorithm 2's second loop) resolved in parallel:
+//   runs of the halves; then the merge tails (Algorithm 3's second loop) resolved in parallel:
 //   every draw is computed, every displaced element's final position is found by following the
 //   later insertions that target it, and the moves are applied as patches (all values read
 //   first, through the merge's input range, which the level no longer needs, then written).
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kWlWarps * 32, 8) warp_stream_level_kernel(WlA
     }
     __syncwarp();
 
-    // ---- merge tails (Algorithm 2's second loop)
+    // ---- merge tails (Algorithm 3's second loop)
     if (K <= a.tcap) {
       // draws: tail step st of merge r is position i = T_r + st, uniform in {0..i}
       for (uint32_t g = lane; g < K; g += 32u) {
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kWlWarps * 32, 8) warp_stream_level_kernel(WlA
       }
       __syncwarp();
     } else if (lane < Mt) {
-      // more tail steps than the parallel replay holds: Algorithm 2's loop as printed
+      // more tail steps than the parallel replay holds: Algorithm 3's loop as printed
       const uint32_t r = lane;
       const uint32_t T = m_T[r], N = m_N[r];
       E *C = Y + m_s[r];

@@ -3,7 +3,7 @@ size bucket by timing the CUDA library on the GPU, and writes the table the libr
 lookup uses (``csrc/ms_tune_table.h``, built in) plus a JSON copy that can be installed at run
 time with ``ms_tune_install``.
 
-The paper leaves the cutoff open (Algorithm 3 splits into "blocks of roughly the same size"; the
+The paper leaves the cutoff open (Algorithm 2 splits into "blocks of roughly the same size"; the
 appendix listing takes the cutoff as a parameter). B is part of the result's definition, so the
 tuner only changes which B a call with B = 0 resolves to; every tuned choice is recorded in the
 table. The fusion depth and the level mode never change the result.

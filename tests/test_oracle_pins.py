@@ -71,7 +71,7 @@ def test_philox_matches_curand_host_generator(seed):
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
 def test_exact_uniformity_all_cutoffs(n, mode):
     """Every one of the n! outputs has probability exactly 1/n!, for every cutoff B in 1..n
-    (Merge lemma, Section 2.1; induction over Algorithm 3)."""
+    (Merge lemma, Section 2.1; induction over Algorithm 2)."""
     for B in range(1, n + 1):
         num, den, paths = oracle.enumerate_perm(n, B, mode)
         assert den % math.factorial(n) == 0
@@ -312,7 +312,7 @@ def test_single_block_is_textbook_fisher_yates(n):
 
 
 def test_two_elements_one_merge():
-    """n = 2, B = 1: two one-element blocks and one Merge, worked by hand from Algorithm 2:
+    """n = 2, B = 1: two one-element blocks and one Merge, worked by hand from Algorithm 3:
     the first coin picks which element leads; the second either takes the other element
     (no tail) or breaks, leaving one element for the random insertion at position 1."""
     for seed in range(200):
