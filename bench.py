@@ -337,12 +337,12 @@ def run_ours(args, world, rank, local):
 # ------------------------------------------------------------------ CPU oracle --------------
 def cpu_baseline(B_perm: int, B_rec: int) -> dict:
     """The oracle as it stands on one host core, on a bounded sample of the workload (the same
-    element mix as the GPU step, 1/32 of its perm and 1/36 of its records: about 10-20 s)."""
+    element mix as the GPU step, 1/16 of its perm and 1/18 of its records: about 10-30 s)."""
     import oracle
     from paper_1508_03167_gb300 import inputs
 
-    n1 = 1 << 25
-    n2 = 1 << 23
+    n1 = 1 << 26
+    n2 = 1 << 24
     rec = inputs.records16(n2)
     t0 = time.perf_counter()
     oracle.perm(n1, SEED, B_perm)
@@ -350,7 +350,7 @@ def cpu_baseline(B_perm: int, B_rec: int) -> dict:
     dt = time.perf_counter() - t0
     return {"value": round((n1 + n2) / dt / 1e9, 6), "unit": "Gelem/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"perm(2^25) u32 + shuffle(2^23) 16-byte records, B={B_perm}/{B_rec}, "
+            "sample": f"perm(2^26) u32 + shuffle(2^24) 16-byte records, B={B_perm}/{B_rec}, "
                       f"single-threaded C oracle, {dt:.1f} s"}
 
 

@@ -69,6 +69,15 @@ typedef void *ms_stream_t;
                                         (the result is identical) */
 #define MS_FLAG_PERM 0x10u           /* batch calls: fill every instance with its permutation of
                                         0..n_i-1 instead of shuffling it (w must be 4) */
+#define MS_FLAG_WARP_LEVELS 0x40u    /* small merge levels run one warp per group of merges,
+                                        global to global, instead of streamed spans (the
+                                        result is identical) */
+#define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
+                                        stream beside it (the result is identical). By default
+                                        the data-independent plan of each global merge level
+                                        runs on a second, high-priority stream paired with the
+                                        caller's, one or two levels ahead; make the first call
+                                        on a stream before capturing it into a CUDA graph */
 
 typedef struct {
   uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B);

@@ -162,9 +162,37 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     // local mode when a merge (and up to 16 of them) fits one CTA's staging buffer
     lv.local = false;
     lv.warp_local = false;
+    lv.span = false;
     lv.warp_bytes = 0;
     lv.mlog = 0;
-    if (Nmax <= kWarpMergeMax && !(flags & (MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS))) {
+    // span buffers of 16 KiB (four CTAs per SM) when the merges fit, else 32 KiB (two)
+    const uint32_t S = ceil_scaled(n, lv.level + 1, c) <= kSpanBytes / 2 / w ? kSpanBytes / 2 / w
+                                                                            : kSpanBytes / w;
+    const uint32_t mode_flags = MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS | MS_FLAG_WARP_LEVELS;
+    // (16-byte records: a span holds too few of them to amortise the per-span work; their
+    // small levels stream per warp instead)
+    if (!(flags & mode_flags) && w <= 8 && ceil_scaled(n, lv.level + 1, c) <= S) {
+      // streamed spans of up to 64 merges
+      uint32_t m = 0;
+      while ((1u << (m + 1)) <= kSpanMaxMerges && (M >> (m + 1)) >= 1 &&
+             ceil_scaled(n, lv.level + 2 + m, c) <= S)
+        ++m;
+      lv.local = true;
+      lv.span = true;
+      lv.mlog = m;
+      lv.span_max = S;
+      lv.ucap = (level_units(n, c, lv.level + 1 + m, lv.level) + 3u) & ~3u;
+      const double Mt = static_cast<double>(1u << m);
+      const double per = std::sqrt(2.0 * static_cast<double>(Nmax) / 3.14159265358979) + 2.0;
+      double tc = Mt * per + 4.8 * std::sqrt(Mt * static_cast<double>(Nmax)) + 64.0;
+      const double span_el = static_cast<double>(ceil_scaled(n, lv.level + 1 + m, c));
+      if (tc > span_el) tc = span_el;
+      lv.tcap = static_cast<uint32_t>(tc);
+      lv.smem = span_smem_bytes(S, w, lv.ucap, lv.tcap);
+      lv.kcap = 0;
+      lv.hbits = 10;
+    } else if (Nmax <= kWarpMergeMax &&
+               !(flags & (MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS))) {
       // one warp per span of up to 16 merges (at most kWarpSpanMax elements), global to global
       uint32_t m = 0;
       while (m < kLocalMaxMergesLog && (Nmax << (m + 1)) <= kWarpSpanMax && (M >> (m + 1)) >= 1)
@@ -210,7 +238,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   size_t off = 0;
   p.off_buf = off;
   if (p.nlevels > 0) off += round_up(n * w, 256);
+  uint32_t nglobal = 0;
+  for (uint32_t i = 0; i < p.nlevels; ++i) nglobal += p.levels[i].local ? 0u : 1u;
   if (p.nlevels > 0 && kcap_max > 0) {
+    const size_t base = off;
     p.off_zc = off;     off += round_up(zc_cap * 4, 256);
     p.off_minfo = off;  off += round_up(minfo_cap * 16, 256);
     p.off_ctrl = off;   off += 256;
@@ -220,6 +251,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     p.off_pdst = off;   off += round_up(2 * kcap_max * 4, 256);
     p.off_psrc = off;   off += round_up(2 * kcap_max * 4, 256);
     p.off_ptmp = off;   off += round_up(2 * kcap_max * w, 256);
+    p.plan_set_bytes = off - base;
+    // two plan sets when there is a next global level to plan during a level's data pass
+    p.plan_sets = nglobal >= 2 ? 2u : 1u;
+    off += (p.plan_sets - 1) * p.plan_set_bytes;
   }
   p.ws_bytes = off > 256 ? off : 256;
   *out = p;
@@ -311,21 +346,71 @@ ms_status plan_for(uint64_t n, uint32_t w, const ms_params *p, Plan *plan) {
   return MS_OK;
 }
 
-msk::Buffers buffers_for(const Plan &p, void *data, void *ws) {
+msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   char *base = static_cast<char *>(ws);
+  char *ps = base + static_cast<size_t>(set) * p.plan_set_bytes;  // this plan set
   msk::Buffers b;
   b.data = data;
   b.other = base + p.off_buf;
-  b.zc = reinterpret_cast<uint32_t *>(base + p.off_zc);
-  b.minfo = reinterpret_cast<uint4 *>(base + p.off_minfo);
-  b.ctrl = reinterpret_cast<uint32_t *>(base + p.off_ctrl);
-  b.mv = reinterpret_cast<uint32_t *>(base + p.off_mv);
-  b.hkeys = reinterpret_cast<unsigned long long *>(base + p.off_hkeys);
-  b.hvals = reinterpret_cast<uint32_t *>(base + p.off_hvals);
-  b.pdst = reinterpret_cast<uint32_t *>(base + p.off_pdst);
-  b.psrc = reinterpret_cast<uint32_t *>(base + p.off_psrc);
-  b.ptmp = base + p.off_ptmp;
+  b.zc = reinterpret_cast<uint32_t *>(ps + p.off_zc);
+  b.minfo = reinterpret_cast<uint4 *>(ps + p.off_minfo);
+  b.ctrl = reinterpret_cast<uint32_t *>(ps + p.off_ctrl);
+  b.mv = reinterpret_cast<uint32_t *>(ps + p.off_mv);
+  b.hkeys = reinterpret_cast<unsigned long long *>(ps + p.off_hkeys);
+  b.hvals = reinterpret_cast<uint32_t *>(ps + p.off_hvals);
+  b.pdst = reinterpret_cast<uint32_t *>(ps + p.off_pdst);
+  b.psrc = reinterpret_cast<uint32_t *>(ps + p.off_psrc);
+  b.ptmp = ps + p.off_ptmp;
   return b;
+}
+
+// The plan stream paired with a caller's stream (per device, created on first use, highest
+// priority so that its short kernels are dispatched between the blocks of a running gather),
+// with the events of the two-set pipeline. A mutex serialises the enqueue of one call's
+// pipeline per caller stream.
+struct PlanStream {
+  int dev = -1;
+  cudaStream_t caller = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t planned[2] = {};
+  cudaEvent_t released[2] = {};
+  std::mutex mu;
+};
+
+ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
+  static std::mutex mu;
+  static PlanStream pool[64];
+  static uint32_t used = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MS_ERR_CUDA;
+  std::lock_guard<std::mutex> g(mu);
+  for (uint32_t i = 0; i < used; ++i)
+    if (pool[i].dev == dev && pool[i].caller == caller) {
+      *out = &pool[i];
+      return MS_OK;
+    }
+  if (used == 64) {
+    *out = nullptr;  // too many distinct caller streams: the call runs without the side stream
+    return MS_OK;
+  }
+  PlanStream &S = pool[used];
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return MS_ERR_CUDA;
+  if (cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, hi) != cudaSuccess)
+    return MS_ERR_CUDA;
+  for (int k = 0; k < 2; ++k) {
+    if (cudaEventCreateWithFlags(&S.planned[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S.released[k], cudaEventDisableTiming) != cudaSuccess)
+      return MS_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess)
+    return MS_ERR_CUDA;
+  S.dev = dev;
+  S.caller = caller;
+  ++used;
+  *out = &S;
+  return MS_OK;
 }
 
 ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
@@ -348,20 +433,65 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   if (ws_bytes < p.ws_bytes) return MS_ERR_INVALID;
   if (p.ws_bytes > 256 && (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
     return MS_ERR_INVALID;
-  const msk::Buffers b = buffers_for(p, data, ws);
+  const msk::Buffers b0 = buffers_for(p, data, ws, 0);
   std::unique_lock<std::mutex> prof_lock(g_prof_mu, std::defer_lock);
   if (p.flags & MS_FLAG_PROFILE) {
     prof_lock.lock();
     p.prof = &profiler();
   }
-  void *cur = (p.nlevels % 2 == 0) ? data : b.other;
+  // global levels, in order; level j uses plan set j % 2 and its plan runs on the side stream,
+  // two levels ahead at most (set j % 2 is released when level j - 2's patches are done)
+  uint32_t glob[33];
+  uint32_t ng = 0;
+  for (uint32_t i = 0; i < p.nlevels; ++i)
+    if (!p.levels[i].local) glob[ng++] = i;
+  PlanStream *P = nullptr;
+  if (p.plan_sets == 2 && !(p.flags & MS_FLAG_SINGLE_STREAM) && plan_stream(s, &P) != MS_OK)
+    return MS_ERR_CUDA;
+  std::unique_lock<std::mutex> pipe_lock;
+  auto plan_on_side = [&](uint32_t j) -> bool {
+    const msk::Buffers bj = buffers_for(p, data, ws, j % 2);
+    if (j >= 2 && cudaStreamWaitEvent(P->side, P->released[j % 2], 0) != cudaSuccess) return false;
+    if (msk::launch_level_plan(p, p.levels[glob[j]], bj, seed, P->side) != cudaSuccess)
+      return false;
+    return cudaEventRecord(P->planned[j % 2], P->side) == cudaSuccess;
+  };
+  if (P) {
+    pipe_lock = std::unique_lock<std::mutex>(P->mu);
+    // the side stream starts after everything already on the caller's stream (earlier calls
+    // may still be reading the plan sets)
+    if (cudaEventRecord(P->fork, s) != cudaSuccess) return MS_ERR_CUDA;
+    if (cudaStreamWaitEvent(P->side, P->fork, 0) != cudaSuccess) return MS_ERR_CUDA;
+    for (uint32_t j = 0; j < ng && j < 2; ++j)
+      if (!plan_on_side(j)) return MS_ERR_CUDA;
+  }
+  void *cur = (p.nlevels % 2 == 0) ? data : b0.other;
   if (msk::launch_leaf(p, data, cur, perm, seed, s) != cudaSuccess) return MS_ERR_CUDA;
+  uint32_t j = 0;  // next global level
   for (uint32_t i = 0; i < p.nlevels; ++i) {
-    void *dst = (cur == data) ? b.other : data;
+    void *dst = (cur == data) ? b0.other : data;
     const msk::LevelPlan &lv = p.levels[i];
-    const cudaError_t e = lv.warp_local ? msk::launch_warp_level(p, lv, cur, dst, seed, s)
-                          : lv.local    ? msk::launch_local_level(p, lv, cur, dst, seed, s)
-                                        : msk::launch_level(p, lv, cur, dst, b, seed, s);
+    cudaError_t e = cudaSuccess;
+    if (lv.span) {
+      e = msk::launch_span_level(p, lv, cur, dst, seed, s);
+    } else if (lv.warp_local) {
+      e = msk::launch_warp_level(p, lv, cur, dst, seed, s);
+    } else if (lv.local) {
+      e = msk::launch_local_level(p, lv, cur, dst, seed, s);
+    } else {
+      const msk::Buffers bj = buffers_for(p, data, ws, P ? j % 2 : 0);
+      if (P) {
+        if (cudaStreamWaitEvent(s, P->planned[j % 2], 0) != cudaSuccess) return MS_ERR_CUDA;
+      } else if (msk::launch_level_plan(p, lv, bj, seed, s) != cudaSuccess) {
+        return MS_ERR_CUDA;
+      }
+      e = msk::launch_level_data(p, lv, cur, dst, bj, seed, s);
+      if (e == cudaSuccess && P) {
+        if (cudaEventRecord(P->released[j % 2], s) != cudaSuccess) return MS_ERR_CUDA;
+        if (j + 2 < ng && !plan_on_side(j + 2)) return MS_ERR_CUDA;
+      }
+      ++j;
+    }
     if (e != cudaSuccess) return MS_ERR_CUDA;
     cur = dst;
   }

@@ -478,8 +478,9 @@ __global__ void __launch_bounds__(kEngThreads, 2) engine_kernel(EngineArgs g) {
           const uint64_t lb = sp << gl;
           const uint64_t g0 = boundary(a.n, c, lb);
           const uint32_t len = static_cast<uint32_t>(boundary(a.n, c, lb + (1ull << gl)) - g0);
+          // X is global here: the tails run in shared memory, in order (no patch scratch)
           merge_level<kEngWarps, E>(a, S, lb, lb, g0, lvl, gl, cur + g0, len, false, stage,
-                                    cur + g0, len);
+                                    nullptr, 0u);
           for (uint32_t i = tid; i < len; i += kEngThreads) other[g0 + i] = stage[i];
           __syncthreads();
         }

@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(kLeafThreads, 2) local_level_kernel(LeafArgs a
     const uint64_t lb = sp << gl;
     const uint64_t g0 = boundary(a.n, a.c, lb);
     const uint32_t len = static_cast<uint32_t>(boundary(a.n, a.c, lb + (1ull << gl)) - g0);
-    // the input span is dead once gathered: it holds the tail patches
-    merge_level<kLeafWarps, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage,
-                               const_cast<E *>(in) + g0, len);
+    // X is global here: the tails run in shared memory, in order (no patch scratch)
+    merge_level<kLeafWarps, E>(a, S, lb, lb, g0, lam, gl, in + g0, len, false, stage, nullptr,
+                               0u);
     for (uint32_t i = threadIdx.x; i < len; i += kLeafThreads) out[g0 + i] = stage[i];
     __syncthreads();
   }

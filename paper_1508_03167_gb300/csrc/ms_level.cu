@@ -475,9 +475,8 @@ unsigned grid_for(uint64_t items, uint64_t per_block, uint64_t cap) {
   return static_cast<unsigned>(g);
 }
 
-template <typename E>
-cudaError_t launch_level_t(const Plan &p, const LevelPlan &lv, const void *in, void *out,
-                           const Buffers &b, uint64_t seed, cudaStream_t s) {
+LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                     const Buffers &b, uint64_t seed) {
   LevelArgs a;
   a.in = in;
   a.out = out;
@@ -499,45 +498,64 @@ cudaError_t launch_level_t(const Plan &p, const LevelPlan &lv, const void *in, v
   a.pdst = b.pdst;
   a.psrc = b.psrc;
   a.ptmp = b.ptmp;
+  return a;
+}
+
+constexpr unsigned kResident = 152u * 8u;
+
+template <typename F>
+void timed(Prof *pf, int kind, cudaStream_t s, F &&launch) {
+  if (pf) pf->begin(kind, s);
+  launch();
+  if (pf) pf->end(s);
+}
+
+template <typename E>
+cudaError_t launch_data_t(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                          const Buffers &b, uint64_t seed, cudaStream_t s) {
+  const LevelArgs a = level_args(p, lv, in, out, b, seed);
   const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
-  const unsigned resident = 152u * 8u;
-  Prof *pf = p.prof;
-  auto timed = [&](int kind, auto &&launch) {
-    if (pf) pf->begin(kind, s);
-    launch();
-    if (pf) pf->end(s);
-  };
-  timed(kKindCount, [&] {
-    count_kernel<<<grid_for(nchunks, kThreads / 32, 1u << 20), kThreads, 0, s>>>(a);
-  });
-  timed(kKindScan, [&] { scan_kernel<<<grid_for(lv.M, 1, 1u << 20), kThreads, 0, s>>>(a); });
-  timed(kKindKscan, [&] { kscan_kernel<<<1, 1024, 0, s>>>(a); });
-  cudaError_t err = cudaSuccess;
-  timed(kKindHashClear, [&] {
-    err = cudaMemsetAsync(b.hkeys, 0xFF, sizeof(unsigned long long) << lv.hbits, s);
-  });
-  if (err != cudaSuccess) return err;
-  timed(kKindInsert, [&] { tail_insert_kernel<<<resident, kThreads, 0, s>>>(a); });
-  timed(kKindResolve, [&] { tail_resolve_kernel<<<resident, kThreads, 0, s>>>(a); });
-  timed(kKindGather, [&] {
+  timed(p.prof, kKindGather, s, [&] {
     gather_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(a);
   });
-  timed(kKindTailSeq, [&] {
+  timed(p.prof, kKindTailSeq, s, [&] {
     tail_sequential_kernel<E><<<grid_for(lv.M, kThreads, 1u << 16), kThreads, 0, s>>>(a);
   });
-  timed(kKindPatchRead, [&] { patch_read_kernel<E><<<resident, kThreads, 0, s>>>(a); });
-  timed(kKindPatchWrite, [&] { patch_write_kernel<E><<<resident, kThreads, 0, s>>>(a); });
+  timed(p.prof, kKindPatchRead, s,
+        [&] { patch_read_kernel<E><<<kResident, kThreads, 0, s>>>(a); });
+  timed(p.prof, kKindPatchWrite, s,
+        [&] { patch_write_kernel<E><<<kResident, kThreads, 0, s>>>(a); });
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
-                         const Buffers &b, uint64_t seed, cudaStream_t s) {
+cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers &b, uint64_t seed,
+                              cudaStream_t s) {
+  const LevelArgs a = level_args(p, lv, nullptr, nullptr, b, seed);
+  const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
+  timed(p.prof, kKindCount, s, [&] {
+    count_kernel<<<grid_for(nchunks, kThreads / 32, 1u << 20), kThreads, 0, s>>>(a);
+  });
+  timed(p.prof, kKindScan, s,
+        [&] { scan_kernel<<<grid_for(lv.M, 1, 1u << 20), kThreads, 0, s>>>(a); });
+  timed(p.prof, kKindKscan, s, [&] { kscan_kernel<<<1, 1024, 0, s>>>(a); });
+  cudaError_t err = cudaSuccess;
+  timed(p.prof, kKindHashClear, s, [&] {
+    err = cudaMemsetAsync(b.hkeys, 0xFF, sizeof(unsigned long long) << lv.hbits, s);
+  });
+  if (err != cudaSuccess) return err;
+  timed(p.prof, kKindInsert, s, [&] { tail_insert_kernel<<<kResident, kThreads, 0, s>>>(a); });
+  timed(p.prof, kKindResolve, s, [&] { tail_resolve_kernel<<<kResident, kThreads, 0, s>>>(a); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                              const Buffers &b, uint64_t seed, cudaStream_t s) {
   switch (p.w) {
-    case 4: return launch_level_t<uint32_t>(p, lv, in, out, b, seed, s);
-    case 8: return launch_level_t<uint2>(p, lv, in, out, b, seed, s);
-    case 16: return launch_level_t<uint4>(p, lv, in, out, b, seed, s);
+    case 4: return launch_data_t<uint32_t>(p, lv, in, out, b, seed, s);
+    case 8: return launch_data_t<uint2>(p, lv, in, out, b, seed, s);
+    case 16: return launch_data_t<uint4>(p, lv, in, out, b, seed, s);
     default: return cudaErrorInvalidValue;
   }
 }

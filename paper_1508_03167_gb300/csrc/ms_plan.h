@@ -19,6 +19,8 @@ constexpr uint32_t kLocalMaxMergesLog = 4u;        // at most 16 merges per loca
 constexpr uint32_t kWarpMergeMax = 4096u;           // largest merge a single warp finishes
 constexpr uint32_t kWarpSpanMax = 8192u;            // elements of a warp's span of merges
 constexpr uint32_t kSmemLimit = 200u * 1024u; // dynamic shared memory budget of one CTA
+constexpr uint32_t kSpanBytes = 32u * 1024u;  // span buffer of the streamed small-merge levels
+constexpr uint32_t kSpanMaxMerges = 64u;      // merges per span at most
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // Kernel classes timed by the optional profiler (MS_FLAG_PROFILE).
@@ -57,6 +59,7 @@ struct LevelPlan {
   // local mode: every merge finishes inside one CTA (2^mlog merges per CTA)
   bool local;
   bool warp_local;      // one warp per span (no CTA barriers)
+  bool span;            // streamed spans with asynchronous prefetch (ms_span.cu)
   uint32_t warp_bytes;  // shared memory of one warp's span (warp-local mode)
   uint32_t mlog;
   uint32_t span_max;  // elements of the largest CTA span
@@ -88,9 +91,13 @@ struct Plan {
   LevelPlan levels[33];
   uint32_t flags = 0;
   Prof *prof = nullptr;
-  // workspace layout (byte offsets from the workspace base)
+  // workspace layout (byte offsets from the workspace base). The plan scratch of the global
+  // levels comes in plan_sets copies, plan_set_bytes apart: level j of the global levels uses
+  // set j % plan_sets, so the plan of the next level can be built while this one streams.
   size_t off_buf = 0, off_zc = 0, off_minfo = 0, off_ctrl = 0, off_mv = 0, off_hkeys = 0,
          off_hvals = 0, off_pdst = 0, off_psrc = 0, off_ptmp = 0, ws_bytes = 0;
+  size_t plan_set_bytes = 0;
+  uint32_t plan_sets = 0;
   uint32_t zc_cap = 0, minfo_cap = 0, kcap_max = 0, hbits_max = 0;
   bool buffer_in_ws = true;  // false for the host form, where both buffers live in ws
 };
@@ -117,12 +124,19 @@ struct Buffers {
 // Kernel launchers (ms_leaf.cu, ms_level.cu). Return the launch error (cudaSuccess if none).
 cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s);
-cudaError_t launch_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
-                         const Buffers &b, uint64_t seed, cudaStream_t s);
+// A global level in two parts: the data-independent plan (coin counts, prefixes, break steps,
+// tail draws and their replay on indices) and the data pass (streaming gather, tail patches).
+cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers &b, uint64_t seed,
+                              cudaStream_t s);
+cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                              const Buffers &b, uint64_t seed, cudaStream_t s);
 cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                                uint64_t seed, cudaStream_t s);
 cudaError_t launch_warp_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                               uint64_t seed, cudaStream_t s);
+cudaError_t launch_span_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
+                              uint64_t seed, cudaStream_t s);
+size_t span_smem_bytes(uint32_t S, uint32_t w, uint32_t ucap, uint32_t tcap);
 // Batch engine (ms_batch.cu): one persistent launch over a device table of instances.
 cudaError_t launch_engine(uint32_t w, bool perm, const void *inst, uint32_t k, uint32_t *queue,
                           uint32_t B, void *scratch, size_t scratch_per_cta, uint32_t kcap,

@@ -173,12 +173,17 @@ class Server:
             for evt, si, reqs, wsb in inflight:
                 if evt.query():
                     t_done = start_evt.elapsed_time(evt) * 1e-3
+                    if self.keep_results:
+                        # copy the results out on the batch's own stream and wait for the copy:
+                        # the arena blocks are reused by later batches on other streams
+                        with torch.cuda.stream(self.streams[si]):
+                            for r in reqs:
+                                off = r.out[0]
+                                self.results[r.rid] = self.mem[off:off + 4 * r.n].view(
+                                    torch.int32).clone()
+                        self.streams[si].synchronize()
                     for r in reqs:
                         r.done = t_done
-                        if self.keep_results:
-                            off = r.out[0]
-                            self.results[r.rid] = self.mem[off:off + 4 * r.n].view(
-                                torch.int32).clone()
                         self.arena.release(r.out)
                         done.append(r)
                         elems += r.n

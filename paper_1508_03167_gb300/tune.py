@@ -26,9 +26,12 @@ B_CANDIDATES = (32, 64, 128, 256, 512, 1024)
 # (fuse_depth, flags) alternatives per B: the planner's fusion depth or none; per-warp or
 # per-CTA small levels
 MODE_CANDIDATES = ((-1, 0), (0, 0), (0, 0x8))
-# size points per width: log2 n (the largest fits a 2 x n x w footprint comfortably)
+# size points per width: log2 n (the largest fits a 2 x n x w footprint comfortably); sizes are
+# 2^k for w = 4 and 2^k + 17 otherwise (uneven halves), except that the last 16-byte point is
+# the 300,000,017-record workload itself
 SINGLE_POINTS = {4: (10, 14, 18, 22, 26, 30), 8: (10, 14, 18, 22, 26, 29),
-                 16: (10, 14, 18, 22, 26, 28)}
+                 16: (10, 14, 18, 22, 26, 29)}
+EXACT_N = {(16, 29): 300_000_017}
 QUICK_POINTS = {4: (14, 22, 26), 8: (22,), 16: (22,)}
 
 
@@ -168,7 +171,7 @@ def tune(quick: bool = False, reps: int = 5, log=print) -> list[dict]:
     points = QUICK_POINTS if quick else SINGLE_POINTS
     for w, pts in points.items():
         for lg, lmax in zip(sorted(pts), buckets(pts)):
-            n = (1 << lg) + (0 if w == 4 else 17)  # records: uneven halves as in the workloads
+            n = EXACT_N.get((w, lg), (1 << lg) + (0 if w == 4 else 17))
             timings = {}
             for B in B_CANDIDATES:
                 if B >= n:

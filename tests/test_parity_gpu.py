@@ -89,6 +89,8 @@ def test_global_and_local_levels_agree(n, B):
     assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS), want)
     assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0), want)
     assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_CTA_LEVELS), want)
+    assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_WARP_LEVELS), want)
+    assert np.array_equal(gpu_perm(n, 13, B, fuse_depth=0, flags=ms.MS_FLAG_SINGLE_STREAM), want)
 
 
 @pytest.mark.parametrize("B", [2, 31, 32, 33, 100, 256, 1000, 4096])
@@ -107,6 +109,9 @@ def test_sequential_tail_path_is_identical(n, B):
     want, _ = oracle.perm(n, 3, B)
     got = gpu_perm(n, 3, B, fuse_depth=0,
                    flags=ms.MS_FLAG_TAIL_SEQUENTIAL | ms.MS_FLAG_GLOBAL_LEVELS)
+    assert np.array_equal(got, want)
+    # the streamed small-merge levels' own sequential fallback
+    got = gpu_perm(n, 3, B, fuse_depth=0, flags=ms.MS_FLAG_TAIL_SEQUENTIAL)
     assert np.array_equal(got, want)
 
 
