@@ -194,6 +194,57 @@ __global__ void __launch_bounds__(32) fy_kernel(LeafArgs a, uint32_t per_cta) {
   }
 }
 
+// Fisher-Yates only, on indices (d = 0, elements of 8 or 16 bytes, base blocks of at most
+// kIdxMaxLeaf elements): the lane of each base block shuffles the 32-bit indices 0..L-1 in shared
+// memory (the draws and swaps of Algorithm 1, so the block ends up as in[perm]), then the warp
+// gathers the block's elements through them: out[b + i] = in[b + idx[i]]. Shared memory per
+// block is 4 bytes an element instead of w, so more warps fit an SM. When out and in are the
+// same array a block is read whole into registers before any of it is written.
+constexpr uint32_t kIdxMaxLeaf = 256;
+template <typename E>
+__global__ void __launch_bounds__(32) fy_index_kernel(LeafArgs a, uint32_t per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *const idx = reinterpret_cast<uint32_t *>(smem_raw);
+  const E *in = static_cast<const E *>(a.in);
+  E *out = static_cast<E *>(a.out);
+  const bool in_place = static_cast<const void *>(in) == static_cast<const void *>(out);
+  const uint32_t lane = threadIdx.x;
+  const uint32_t P = a.stride;
+  const uint64_t groups = (a.q + per_cta - 1) / per_cta;
+  for (uint64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
+    const uint64_t lb = gidx * per_cta;
+    const uint32_t cnt = static_cast<uint32_t>(a.q - lb < per_cta ? a.q - lb : per_cta);
+    if (lane < cnt) {
+      const uint64_t leaf = lb + lane;
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
+                                               boundary(a.n, a.c, leaf));
+      uint32_t *blk = idx + lane * P;
+      for (uint32_t i = 0; i < L; ++i) blk[i] = i;
+      fisher_yates_block(blk, L, static_cast<uint32_t>(leaf), a.key);
+    }
+    __syncwarp();
+    constexpr uint32_t kPer = kIdxMaxLeaf / 32;
+    for (uint32_t k = 0; k < cnt; ++k) {
+      const uint64_t bs = boundary(a.n, a.c, lb + k);
+      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
+      const uint32_t *blk = idx + k * P;
+      E v[kPer];
+#pragma unroll
+      for (uint32_t j = 0; j < kPer; ++j) {
+        const uint32_t i = lane + 32u * j;
+        if (i < L) v[j] = in[bs + blk[i]];
+      }
+      if (in_place) __syncwarp();  // the whole block is read before any of it is written
+#pragma unroll
+      for (uint32_t j = 0; j < kPer; ++j) {
+        const uint32_t i = lane + 32u * j;
+        if (i < L) out[bs + i] = v[j];
+      }
+      __syncwarp();
+    }
+  }
+}
+
 template <typename E, bool kPerm>
 cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t seed,
                           cudaStream_t s) {
@@ -214,6 +265,20 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
   a.ucap_c = p.ucap_c;
   a.tcap_c = p.tcap_c;
   a.aux_w = p.aux_w;
+  if (p.d == 0 && p.fy_per_cta > 0 && !kPerm && sizeof(E) >= 8 && p.leaf_max <= kIdxMaxLeaf) {
+    auto fk = fy_index_kernel<E>;
+    const uint32_t per = 32;
+    const size_t smem = static_cast<size_t>(per) * p.leaf_stride * sizeof(uint32_t);
+    cudaError_t e2 = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem));
+    if (e2 != cudaSuccess) return e2;
+    const uint64_t groups = (p.q + per - 1) / per;
+    const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
+    if (p.prof) p.prof->begin(kKindLeaf, s);
+    fk<<<static_cast<unsigned>(grid), 32, smem, s>>>(a, per);
+    if (p.prof) p.prof->end(s);
+    return cudaGetLastError();
+  }
   if (p.d == 0 && p.fy_per_cta > 0) {
     auto fk = fy_kernel<E, kPerm>;
     const size_t smem = static_cast<size_t>(p.fy_per_cta) * p.leaf_stride * sizeof(E);
