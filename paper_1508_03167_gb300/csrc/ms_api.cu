@@ -165,9 +165,13 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     lv.span = false;
     lv.warp_bytes = 0;
     lv.mlog = 0;
-    // span buffers of 16 KiB (four CTAs per SM) when the merges fit, else 32 KiB (two)
-    const uint32_t S = ceil_scaled(n, lv.level + 1, c) <= kSpanBytes / 2 / w ? kSpanBytes / 2 / w
-                                                                            : kSpanBytes / w;
+    // span buffers of 8 KiB (128-thread CTAs, eight an SM) when the merges fit, else 16 KiB
+    // (256 threads, four an SM), else 32 KiB (two)
+    const uint64_t nm = ceil_scaled(n, lv.level + 1, c);
+    const uint32_t S = nm <= kSpanBytes / 4 / w   ? kSpanBytes / 4 / w
+                       : nm <= kSpanBytes / 2 / w ? kSpanBytes / 2 / w
+                                                  : kSpanBytes / w;
+    lv.span_threads = S == kSpanBytes / 4 / w ? 128u : 256u;
     const uint32_t mode_flags = MS_FLAG_GLOBAL_LEVELS | MS_FLAG_CTA_LEVELS | MS_FLAG_WARP_LEVELS;
     // (16-byte records: a span holds too few of them to amortise the per-span work; their
     // small levels stream per warp instead)

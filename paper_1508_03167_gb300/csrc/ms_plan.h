@@ -60,6 +60,7 @@ struct LevelPlan {
   bool local;
   bool warp_local;      // one warp per span (no CTA barriers)
   bool span;            // streamed spans with asynchronous prefetch (ms_span.cu)
+  uint32_t span_threads;  // 128 or 256 threads a CTA
   uint32_t warp_bytes;  // shared memory of one warp's span (warp-local mode)
   uint32_t mlog;
   uint32_t span_max;  // elements of the largest CTA span

@@ -17,8 +17,6 @@
 namespace msk {
 namespace {
 
-constexpr int kSpanThreads = 256;
-constexpr uint32_t kSpanWarps = kSpanThreads / 32;
 
 struct SpanArgs {
   const void *in;
@@ -55,8 +53,11 @@ __device__ __forceinline__ void cp_async_wait() {
 
 __host__ __device__ __forceinline__ size_t r16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename E>
-__global__ void __launch_bounds__(kSpanThreads, 4) span_level_kernel(SpanArgs a) {
+// kThreads = 128 or 256; the register budget (64 a thread) lets 1024 / kThreads CTAs share an SM
+template <typename E, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) span_level_kernel(SpanArgs a) {
+  constexpr uint32_t kSpanThreads = kThreads;
+  constexpr uint32_t kSpanWarps = kThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t mg[8][kSpanMaxMerges];
   __shared__ uint32_t scratch[33];
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kSpanThreads, 4) span_level_kernel(SpanArgs a)
   cp_async_wait<0>();  // nothing in flight at exit
 }
 
-template <typename E>
+template <typename E, int kThreads>
 cudaError_t launch_t(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                      uint64_t seed, cudaStream_t s) {
   SpanArgs a;
@@ -433,12 +434,12 @@ cudaError_t launch_t(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.ucap = lv.ucap;
   a.tcap = lv.tcap;
   a.flags = p.flags;
-  auto kern = span_level_kernel<E>;
+  auto kern = span_level_kernel<E, kThreads>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(lv.smem));
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSpanThreads, lv.smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, lv.smem);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -447,7 +448,7 @@ cudaError_t launch_t(const Plan &p, const LevelPlan &lv, const void *in, void *o
   const uint64_t resident = static_cast<uint64_t>(per_sm > 0 ? per_sm : 1) * sms;
   const uint64_t grid = a.spans < resident ? a.spans : resident;
   if (p.prof) p.prof->begin(kKindLocal, s);
-  kern<<<static_cast<unsigned>(grid), kSpanThreads, lv.smem, s>>>(a);
+  kern<<<static_cast<unsigned>(grid), kThreads, lv.smem, s>>>(a);
   if (p.prof) p.prof->end(s);
   return cudaGetLastError();
 }
@@ -460,10 +461,14 @@ size_t span_smem_bytes(uint32_t S, uint32_t w, uint32_t ucap, uint32_t tcap) {
 
 cudaError_t launch_span_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                               uint64_t seed, cudaStream_t s) {
+  const bool small = lv.span_threads == 128;
   switch (p.w) {
-    case 4: return launch_t<uint32_t>(p, lv, in, out, seed, s);
-    case 8: return launch_t<uint2>(p, lv, in, out, seed, s);
-    case 16: return launch_t<uint4>(p, lv, in, out, seed, s);
+    case 4: return small ? launch_t<uint32_t, 128>(p, lv, in, out, seed, s)
+                         : launch_t<uint32_t, 256>(p, lv, in, out, seed, s);
+    case 8: return small ? launch_t<uint2, 128>(p, lv, in, out, seed, s)
+                         : launch_t<uint2, 256>(p, lv, in, out, seed, s);
+    case 16: return small ? launch_t<uint4, 128>(p, lv, in, out, seed, s)
+                          : launch_t<uint4, 256>(p, lv, in, out, seed, s);
     default: return cudaErrorInvalidValue;
   }
 }
