@@ -155,6 +155,12 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+# DRAM bytes (read + written) per element of one gather launch, from an ncu capture of the
+# gather kernel on a smaller case with inputs above L2 (perm 2^26, records 2^24 + 17), scaled to
+# a full launch by the elements it processes
+GATHER_TRAFFIC_PER_ELEM = {4: 7.311, 16: 28.71}
+
+
 def g_levels(ms, n, w, p) -> int:
     """Merge levels of the plan that run through the global streaming gather."""
     plan = ms.ms_plan_info(n, w, p)
@@ -235,6 +241,9 @@ def run_ours(args, world, rank, local):
     gather_bytes = args.steps * (nglob_perm * 2 * n_perm * 4 + nglob_rec * 2 * n_rec * 16)
     peaks = measured_peaks()
     achieved = gather_bytes / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else 0.0
+    nlaunch = nglob_perm + nglob_rec
+    traffic = ((nglob_perm * GATHER_TRAFFIC_PER_ELEM[4] * n_perm +
+                nglob_rec * GATHER_TRAFFIC_PER_ELEM[16] * n_rec) / nlaunch) if nlaunch else None
     roofline = {
         "bound": "hbm",
         "kernel": "gather (HBM merge level)",
@@ -243,7 +252,9 @@ def run_ours(args, world, rank, local):
         "peak_source": peaks["source"],
         "unit": "GB/s",
         "frac": round(achieved / peaks["hbm_gbs"], 4),
-        "traffic": None,
+        "traffic": round(traffic) if traffic else None,
+        "traffic_note": "bytes per gather launch (dram read+write), ncu on a smaller case "
+                        "scaled by elements; the small case leaves ~50 MB of writes in L2",
         "algorithmic_bytes_per_launch": {"perm": 2 * n_perm * 4, "rec": 2 * n_rec * 16},
         "avg_launch_ms": round(g["ms"] / max(g["launches"], 1), 4),
         "whole_path_frac": round(
