@@ -72,6 +72,13 @@ typedef void *ms_stream_t;
 #define MS_FLAG_WARP_LEVELS 0x40u    /* small merge levels run one warp per group of merges,
                                         global to global, instead of streamed spans (the
                                         result is identical) */
+#define MS_FLAG_SINGLE_LEVELS 0x80u  /* one data pass per global merge level: no fusing of
+                                        consecutive levels into one pass (the result is
+                                        identical) */
+#define MS_FLAG_PAIR_LEVELS 0x100u   /* fuse consecutive global levels into one data pass for
+                                        every element width (by default only 16-byte elements,
+                                        where the pass is bound by memory rather than by its
+                                        instructions; the result is identical) */
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level
@@ -103,6 +110,8 @@ typedef struct {
   uint32_t kernel_launches; /* kernels this library launches for one call */
   uint32_t global_levels;   /* HBM levels that use the global plan and streaming gather; the
                                other hbm_levels - global_levels finish inside a CTA or a warp */
+  uint32_t fused_pairs;     /* pairs of consecutive global levels sharing one data pass:
+                               passes = 1 + hbm_levels - fused_pairs */
 } ms_plan;
 
 /* Per-kernel-class timing accumulated over calls made with MS_FLAG_PROFILE. */
@@ -125,7 +134,8 @@ typedef struct {
  *                            (batch = 1), with ceil(log2 n) <= log2n_max (the smallest such
  *                            bucket wins; beyond every bucket the largest applies). For batched
  *                            calls n is the median instance size. flags may hold
- *                            MS_FLAG_CTA_LEVELS / MS_FLAG_GLOBAL_LEVELS only.
+ *                            MS_FLAG_CTA_LEVELS, MS_FLAG_GLOBAL_LEVELS,
+ *                            MS_FLAG_SINGLE_LEVELS and MS_FLAG_PAIR_LEVELS only.
  *   ms_resolve_params        replaces B = 0 in *inout by the table's choice for (n, w); other
  *                            fields are kept (fuse_depth only if it is not -1). MS_ERR_INVALID
  *                            for a bad w or a NULL pointer.

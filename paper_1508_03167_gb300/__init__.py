@@ -14,7 +14,7 @@ import threading
 
 __all__ = [
     "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
-    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_MAX_B", "ms_batch_workspace_bytes",
+    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_FLAG_SINGLE_LEVELS", "MS_FLAG_PAIR_LEVELS", "MS_MAX_B", "ms_batch_workspace_bytes",
     "ms_batch_prepare", "ms_batch_run", "ms_shuffle_batch", "batch_workspace", "shuffle_batch", "MsParams",
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
@@ -32,6 +32,8 @@ MS_FLAG_CTA_LEVELS = 0x8
 MS_FLAG_PERM = 0x10
 MS_FLAG_SINGLE_STREAM = 0x20
 MS_FLAG_WARP_LEVELS = 0x40
+MS_FLAG_SINGLE_LEVELS = 0x80
+MS_FLAG_PAIR_LEVELS = 0x100
 MS_MAX_B = 4096
 MS_STATIC_MAX_N = 1 << 21
 MS_STATIC_SCRATCH_BYTES = 16 << 20
@@ -48,7 +50,7 @@ class MsPlan(ctypes.Structure):
                 ("hbm_levels", ctypes.c_uint32), ("passes", ctypes.c_uint32),
                 ("tiles", ctypes.c_uint64), ("tile_max", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_uint32),
-                ("global_levels", ctypes.c_uint32)]
+                ("global_levels", ctypes.c_uint32), ("fused_pairs", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

@@ -239,11 +239,41 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   p.kcap_max = static_cast<uint32_t>(kcap_max);
   p.hbits_max = hbits_max;
 
+  // consecutive global levels fuse in pairs (one data pass for two levels)
+  uint32_t nlocal = 0, units = 0;
+  uint32_t xhbits_max = 0;
+  for (uint32_t i = 0; i < p.nlevels; ++i) {
+    p.levels[i].pair = 0;
+    p.levels[i].xhbits = 0;
+  }
+  for (uint32_t i = 0; i < p.nlevels; ++i) {
+    LevelPlan &lv = p.levels[i];
+    if (lv.local) {
+      ++nlocal;
+      continue;
+    }
+    if (lv.pair == 2) continue;  // second level of the pair before it
+    ++units;
+    // (the fused pass evaluates two interleaves and an exception test per element: worth it
+    // where the pass is bound by memory, i.e. for 16-byte elements, or on request)
+    const bool want_pairs = !(flags & MS_FLAG_SINGLE_LEVELS) &&
+                            (w >= 16 || (flags & MS_FLAG_PAIR_LEVELS));
+    if (want_pairs && i + 1 < p.nlevels && !p.levels[i + 1].local) {
+      lv.pair = 1;
+      p.levels[i + 1].pair = 2;
+      uint32_t xb = 10;
+      while ((1ull << xb) < 4ull * lv.kcap) ++xb;
+      lv.xhbits = xb;
+      xhbits_max = std::max(xhbits_max, xb);
+    }
+  }
+  p.units = units;
+  p.hbm_passes = nlocal + units;
+  const bool pairs = xhbits_max > 0;
+
   size_t off = 0;
   p.off_buf = off;
   if (p.nlevels > 0) off += round_up(n * w, 256);
-  uint32_t nglobal = 0;
-  for (uint32_t i = 0; i < p.nlevels; ++i) nglobal += p.levels[i].local ? 0u : 1u;
   if (p.nlevels > 0 && kcap_max > 0) {
     const size_t base = off;
     p.off_zc = off;     off += round_up(zc_cap * 4, 256);
@@ -256,9 +286,21 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     p.off_psrc = off;   off += round_up(2 * kcap_max * 4, 256);
     p.off_ptmp = off;   off += round_up(2 * kcap_max * w, 256);
     p.plan_set_bytes = off - base;
-    // two plan sets when there is a next global level to plan during a level's data pass
-    p.plan_sets = nglobal >= 2 ? 2u : 1u;
+    // a unit (a level or a fused pair) uses two plan sets; two units' sets, so that the next
+    // unit's plan can be built during a unit's data pass
+    p.plan_sets = units >= 2 ? 4u : 2u;
     off += (p.plan_sets - 1) * p.plan_set_bytes;
+    // exception structures of a pair's first level, one copy per live unit (after the sets)
+    if (pairs) {
+      const size_t ebase = off;
+      p.off_zb = off - ebase;     off += round_up(zc_cap * 32ull, 256);
+      p.off_xbits = off - ebase;  off += round_up((n + 31) / 32 * 4, 256);
+      p.off_xkeys = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+      p.off_xvals = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+      p.exc_base = ebase;
+      p.exc_bytes = off - ebase;
+      off += (p.plan_sets / 2 - 1) * p.exc_bytes;
+    }
   }
   p.ws_bytes = off > 256 ? off : 256;
   *out = p;
@@ -279,7 +321,8 @@ namespace {
 
 const char *const kKindNames[msk::kKindNum] = {
     "leaf", "count", "scan", "kscan", "hash_clear", "tail_insert", "tail_resolve",
-    "gather", "tail_sequential", "patch_read", "patch_write", "local_level", "batch_engine"};
+    "gather", "tail_sequential", "patch_read", "patch_write", "local_level", "batch_engine",
+    "pair_gather", "exceptions"};
 
 // Process-wide event recorder used when MS_FLAG_PROFILE is set.
 class EventProfiler final : public msk::Prof {
@@ -356,6 +399,11 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   msk::Buffers b;
   b.data = data;
   b.other = base + p.off_buf;
+  char *es = base + p.exc_base + static_cast<size_t>(set / 2) * p.exc_bytes;  // unit's copy
+  b.zb = reinterpret_cast<uint8_t *>(es + p.off_zb);
+  b.xbits = reinterpret_cast<uint32_t *>(es + p.off_xbits);
+  b.xkeys = reinterpret_cast<uint32_t *>(es + p.off_xkeys);
+  b.xvals = reinterpret_cast<uint32_t *>(es + p.off_xvals);
   b.zc = reinterpret_cast<uint32_t *>(ps + p.off_zc);
   b.minfo = reinterpret_cast<uint4 *>(ps + p.off_minfo);
   b.ctrl = reinterpret_cast<uint32_t *>(ps + p.off_ctrl);
@@ -443,38 +491,57 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
     prof_lock.lock();
     p.prof = &profiler();
   }
-  // global levels, in order; level j uses plan set j % 2 and its plan runs on the side stream,
-  // two levels ahead at most (set j % 2 is released when level j - 2's patches are done)
-  uint32_t glob[33];
-  uint32_t ng = 0;
+  // global units (a single level or a fused pair of levels), in order. Unit u uses plan sets
+  // 2(u % 2) and 2(u % 2) + 1 (the pair's second level takes the second); its plan runs on the
+  // side stream, two units ahead at most (the sets of unit u are released when unit u - 2's
+  // data pass is done).
+  uint32_t unit_level[33];
+  uint32_t nu = 0;
   for (uint32_t i = 0; i < p.nlevels; ++i)
-    if (!p.levels[i].local) glob[ng++] = i;
+    if (!p.levels[i].local && p.levels[i].pair != 2) unit_level[nu++] = i;
   PlanStream *P = nullptr;
-  if (p.plan_sets == 2 && !(p.flags & MS_FLAG_SINGLE_STREAM) && plan_stream(s, &P) != MS_OK)
+  if (nu >= 1 && p.plan_sets >= 2 && !(p.flags & MS_FLAG_SINGLE_STREAM) &&
+      plan_stream(s, &P) != MS_OK)
     return MS_ERR_CUDA;
-  std::unique_lock<std::mutex> pipe_lock;
-  auto plan_on_side = [&](uint32_t j) -> bool {
-    const msk::Buffers bj = buffers_for(p, data, ws, j % 2);
-    if (j >= 2 && cudaStreamWaitEvent(P->side, P->released[j % 2], 0) != cudaSuccess) return false;
-    if (msk::launch_level_plan(p, p.levels[glob[j]], bj, seed, P->side) != cudaSuccess)
-      return false;
-    return cudaEventRecord(P->planned[j % 2], P->side) == cudaSuccess;
+  const uint32_t slots = p.plan_sets >= 4 ? 2u : 1u;  // units whose sets can be live at once
+  auto unit_sets = [&](uint32_t u, msk::Buffers *b1, msk::Buffers *b2) {
+    const uint32_t base = 2u * (u % slots);
+    *b1 = buffers_for(p, data, ws, base);
+    *b2 = buffers_for(p, data, ws, base + 1u);
   };
+  auto launch_unit_plan = [&](uint32_t u, cudaStream_t st) -> bool {
+    msk::Buffers b1, b2;
+    unit_sets(u, &b1, &b2);
+    const msk::LevelPlan &lv = p.levels[unit_level[u]];
+    if (lv.pair == 1)
+      return msk::launch_pair_plan(p, lv, p.levels[unit_level[u] + 1], b1, b2, seed, st) ==
+             cudaSuccess;
+    return msk::launch_level_plan(p, lv, b1, seed, st) == cudaSuccess;
+  };
+  auto plan_on_side = [&](uint32_t u) -> bool {
+    const uint32_t k = u % 2;
+    if (u >= slots && cudaStreamWaitEvent(P->side, P->released[k], 0) != cudaSuccess)
+      return false;
+    if (!launch_unit_plan(u, P->side)) return false;
+    return cudaEventRecord(P->planned[k], P->side) == cudaSuccess;
+  };
+  std::unique_lock<std::mutex> pipe_lock;
   if (P) {
     pipe_lock = std::unique_lock<std::mutex>(P->mu);
     // the side stream starts after everything already on the caller's stream (earlier calls
     // may still be reading the plan sets)
     if (cudaEventRecord(P->fork, s) != cudaSuccess) return MS_ERR_CUDA;
     if (cudaStreamWaitEvent(P->side, P->fork, 0) != cudaSuccess) return MS_ERR_CUDA;
-    for (uint32_t j = 0; j < ng && j < 2; ++j)
-      if (!plan_on_side(j)) return MS_ERR_CUDA;
+    for (uint32_t u = 0; u < nu && u < slots; ++u)
+      if (!plan_on_side(u)) return MS_ERR_CUDA;
   }
-  void *cur = (p.nlevels % 2 == 0) ? data : b0.other;
+  void *cur = (p.hbm_passes % 2 == 0) ? data : b0.other;
   if (msk::launch_leaf(p, data, cur, perm, seed, s) != cudaSuccess) return MS_ERR_CUDA;
-  uint32_t j = 0;  // next global level
+  uint32_t u = 0;  // next global unit
   for (uint32_t i = 0; i < p.nlevels; ++i) {
-    void *dst = (cur == data) ? b0.other : data;
     const msk::LevelPlan &lv = p.levels[i];
+    if (lv.pair == 2) continue;  // done with the pair's first level
+    void *dst = (cur == data) ? b0.other : data;
     cudaError_t e = cudaSuccess;
     if (lv.span) {
       e = msk::launch_span_level(p, lv, cur, dst, seed, s);
@@ -483,18 +550,20 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
     } else if (lv.local) {
       e = msk::launch_local_level(p, lv, cur, dst, seed, s);
     } else {
-      const msk::Buffers bj = buffers_for(p, data, ws, P ? j % 2 : 0);
+      msk::Buffers b1, b2;
+      unit_sets(u, &b1, &b2);
       if (P) {
-        if (cudaStreamWaitEvent(s, P->planned[j % 2], 0) != cudaSuccess) return MS_ERR_CUDA;
-      } else if (msk::launch_level_plan(p, lv, bj, seed, s) != cudaSuccess) {
+        if (cudaStreamWaitEvent(s, P->planned[u % 2], 0) != cudaSuccess) return MS_ERR_CUDA;
+      } else if (!launch_unit_plan(u, s)) {
         return MS_ERR_CUDA;
       }
-      e = msk::launch_level_data(p, lv, cur, dst, bj, seed, s);
+      e = lv.pair == 1 ? msk::launch_pair_data(p, lv, p.levels[i + 1], cur, dst, b1, b2, seed, s)
+                       : msk::launch_level_data(p, lv, cur, dst, b1, seed, s);
       if (e == cudaSuccess && P) {
-        if (cudaEventRecord(P->released[j % 2], s) != cudaSuccess) return MS_ERR_CUDA;
-        if (j + 2 < ng && !plan_on_side(j + 2)) return MS_ERR_CUDA;
+        if (cudaEventRecord(P->released[u % 2], s) != cudaSuccess) return MS_ERR_CUDA;
+        if (u + slots < nu && !plan_on_side(u + slots)) return MS_ERR_CUDA;
       }
-      ++j;
+      ++u;
     }
     if (e != cudaSuccess) return MS_ERR_CUDA;
     cur = dst;
@@ -757,18 +826,24 @@ ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *params, ms_plan 
   out->c = p.c;
   out->fuse_depth = p.d;
   out->hbm_levels = p.nlevels;
-  out->passes = n <= 1 ? 0u : 1u + p.nlevels;
+  out->passes = n <= 1 ? 0u : 1u + p.hbm_passes;
   out->tiles = n <= 1 ? 0u : p.tiles;
   out->tile_max = n <= 1 ? n : p.tile_max;
   out->workspace_bytes = p.ws_bytes;
   uint32_t launches = n <= 1 ? 0u : 1u;
   uint32_t global = 0;
   for (uint32_t i = 0; i < p.nlevels && n > 1; ++i) {
-    launches += p.levels[i].local ? 1u : 9u;
-    global += p.levels[i].local ? 0u : 1u;
+    const msk::LevelPlan &lv = p.levels[i];
+    // global single level: 6 plan + 4 data launches (a memset among them); fused pair: 6 + 6
+    // plan, 3 exception-map steps, 7 data launches (4 of them idle unless the fallback runs)
+    launches += lv.local ? 1u : lv.pair == 1 ? 22u : lv.pair == 2 ? 0u : 10u;
+    global += lv.local ? 0u : 1u;
   }
   out->kernel_launches = launches;
   out->global_levels = global;
+  uint32_t pairs = 0;
+  for (uint32_t i = 0; i < p.nlevels && n > 1; ++i) pairs += p.levels[i].pair == 1 ? 1u : 0u;
+  out->fused_pairs = pairs;
   return MS_OK;
 }
 

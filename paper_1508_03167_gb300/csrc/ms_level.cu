@@ -46,7 +46,20 @@ struct LevelArgs {
   uint32_t *pdst;
   uint32_t *psrc;
   void *ptmp;
+  uint8_t *zb;             // optional: zero coins per 128-step block (count_kernel)
+  const uint32_t *gate;    // optional: the kernel runs only if (*gate != 0) == gate_on
+  uint32_t gate_on;
+  void *out_alt;           // optional: tails and patches act on out_alt when *alt_sel != 0
+  const uint32_t *alt_sel;
 };
+
+__device__ __forceinline__ bool gated_off(const LevelArgs &a) {
+  return a.gate != nullptr && ((*a.gate != 0u) != (a.gate_on != 0u));
+}
+template <typename E>
+__device__ __forceinline__ E *target_of(const LevelArgs &a) {
+  return static_cast<E *>((a.alt_sel != nullptr && *a.alt_sel != 0u) ? a.out_alt : a.out);
+}
 
 struct MergeBounds {
   uint64_t s, mid, e;
@@ -88,6 +101,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(LevelArgs a) {
     const uint32_t blk = j * (kChunk / 128u) + lane;
     uint32_t z = 0;
     if (128ull * blk < N) z = block_zero_count(coin_block(a.key, a.level, r, blk), blk, N);
+    if (a.zb) a.zb[cid * 32u + lane] = static_cast<uint8_t>(z);  // z <= 128
     z = warp_sum(z);
     if (lane == 0) a.zc[cid] = z;
   }
@@ -340,7 +354,7 @@ template <typename E>
 __global__ void __launch_bounds__(kThreads) patch_read_kernel(LevelArgs a) {
   if (a.ctrl[1]) return;
   const uint32_t K = a.ctrl[0];
-  const E *out = static_cast<const E *>(a.out);
+  const E *out = target_of<E>(a);
   E *tmp = static_cast<E *>(a.ptmp);
   for (uint32_t g = blockIdx.x * kThreads + threadIdx.x; g < 2u * K; g += gridDim.x * kThreads) {
     const uint32_t p = g < K ? g : a.kcap + (g - K);
@@ -352,7 +366,7 @@ template <typename E>
 __global__ void __launch_bounds__(kThreads) patch_write_kernel(LevelArgs a) {
   if (a.ctrl[1]) return;
   const uint32_t K = a.ctrl[0];
-  E *out = static_cast<E *>(a.out);
+  E *out = target_of<E>(a);
   const E *tmp = static_cast<const E *>(a.ptmp);
   for (uint32_t g = blockIdx.x * kThreads + threadIdx.x; g < 2u * K; g += gridDim.x * kThreads) {
     const uint32_t p = g < K ? g : a.kcap + (g - K);
@@ -365,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) patch_write_kernel(LevelArgs a) {
 template <typename E>
 __global__ void __launch_bounds__(kThreads) tail_sequential_kernel(LevelArgs a) {
   if (!a.ctrl[1]) return;
-  E *out = static_cast<E *>(a.out);
+  E *out = target_of<E>(a);
   for (uint32_t r = blockIdx.x * kThreads + threadIdx.x; r < a.M; r += gridDim.x * kThreads) {
     const uint4 mi = a.minfo[r];
     const MergeBounds mb = merge_bounds(a, r);
@@ -387,6 +401,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(LevelArgs a) {
   __shared__ uint32_t cw[kChunk / 32u];
   __shared__ uint32_t zw[kChunk / 32u];
   __shared__ uint32_t scratch[33];
+  if (gated_off(a)) return;
   const E *__restrict__ in = static_cast<const E *>(a.in);
   E *__restrict__ out = static_cast<E *>(a.out);
   const uint32_t lane = threadIdx.x & 31u;
@@ -468,6 +483,354 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(LevelArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------- fused pairs --
+// Two consecutive levels l, l+1 in one data pass. Level l's output (never written) is the
+// stable interleave of its halves with the tail moves applied; a tail move is an exception:
+// output position q holds the interleave element of merge position F(q) != q. The plan stores,
+// for every exception, the input index that element comes from (a bitmap marks the exception
+// positions, an open-addressing hash maps position -> input index). The data pass then gathers
+// level l+1's interleave straight from level l's input.
+
+struct ExcArgs {
+  uint32_t *bits;   // one bit per element of level l's output
+  uint32_t *keys;   // hash keys (output position), ~0 = empty
+  uint32_t *vals;   // input index of the element at that position
+  uint32_t hbits;
+};
+
+__device__ __forceinline__ uint32_t xhash_slot(uint32_t key, uint32_t hbits) {
+  return (key * 0x9E3779B1u) >> (32u - hbits);
+}
+
+// Input index (into level l's input) of the interleave element at merge position p of merge r.
+__device__ uint32_t interleave_source(const LevelArgs &a, uint32_t r, uint32_t p) {
+  const MergeBounds mb = merge_bounds(a, r);
+  const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+  const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+  const uint4 mi = a.minfo[r];
+  const uint32_t s = static_cast<uint32_t>(mb.s);
+  if (p >= mi.x) return s + ((mi.y == n1) ? p : p - (N - n1));  // leftover, in order
+  const uint32_t blk = p >> 7;
+  const uint32_t chunk = p >> 12;  // kChunk = 4096 steps = 32 blocks
+  const uint64_t cid = static_cast<uint64_t>(r) * a.J + chunk;
+  uint32_t Z = a.zc[cid];  // zeros before the chunk (exclusive prefix after the scan)
+  {
+    // plus the zero counts of the chunk's blocks before blk: 32 bytes read as two vectors
+    const uint4 *zb4 = reinterpret_cast<const uint4 *>(a.zb + cid * 32u);
+    const uint32_t nb = blk - chunk * 32u;  // bytes to add, < 32
+    const uint4 lo = zb4[0], hi = zb4[1];
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) {
+      const uint32_t keep = nb >= 4u * k + 4u ? 4u : (nb > 4u * k ? nb - 4u * k : 0u);
+      const uint32_t m = keep >= 4u ? 0xFFFFFFFFu : ((1u << (8u * keep)) - 1u);
+      Z += __vsadu4(w[k] & m, 0u);  // sum of the kept bytes
+    }
+  }
+  const uint4 c = coin_block(a.key, a.level, r, blk);
+  const uint32_t q = p & 127u;
+  const uint32_t words[4] = {c.x, c.y, c.z, c.w};
+  for (uint32_t wi = 0; wi < (q >> 5); ++wi) Z += __popc(~words[wi]);
+  const uint32_t word = words[q >> 5];
+  Z += __popc(~word & low_mask(q & 31u));
+  return s + (((word >> (q & 31u)) & 1u) ? n1 + p - Z : Z);
+}
+
+__global__ void __launch_bounds__(kThreads) exceptions_kernel(LevelArgs a, ExcArgs x) {
+  if (a.ctrl[1]) return;  // the unfused fallback runs instead
+  const uint32_t K = a.ctrl[0];
+  const uint32_t hmask = (1u << x.hbits) - 1u;
+  for (uint32_t g = blockIdx.x * kThreads + threadIdx.x; g < 2u * K; g += gridDim.x * kThreads) {
+    const uint32_t pi = g < K ? g : a.kcap + (g - K);
+    const uint32_t dst = a.pdst[pi];
+    if (dst == kNone || dst >= a.n) continue;
+    const uint32_t r = owner_merge(a, g < K ? g : g - K);
+    const uint32_t s = static_cast<uint32_t>(merge_bounds(a, r).s);
+    const uint32_t xs = interleave_source(a, r, a.psrc[pi] - s);
+    atomicOr(&x.bits[dst >> 5], 1u << (dst & 31u));
+    uint32_t h = xhash_slot(dst, x.hbits);
+    for (uint32_t probe = 0; probe <= hmask; ++probe) {
+      const uint32_t old = atomicCAS(&x.keys[h], 0xFFFFFFFFu, dst);
+      if (old == 0xFFFFFFFFu) {
+        x.vals[h] = xs;
+        break;
+      }
+      h = (h + 1u) & hmask;
+    }
+  }
+}
+
+struct PairArgs {
+  const void *in;
+  void *out;
+  LevelArgs l1, l2;  // the two levels' plans (l1.J, zc, zb, minfo; l2.M, J, zc, minfo)
+  ExcArgs x;
+};
+
+// half h of level l+1's merge R is merge 2R+h of level l; its used position range in the chunk
+// is [lo, lo+cnt); the coin words of level l covering it start at block blo.
+constexpr uint32_t kPairW = 136;  // words per half: <= 4096 positions + block alignment
+
+template <typename E>
+__global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
+  __shared__ uint32_t cw2[kChunk / 32u];
+  __shared__ uint32_t zw2[kChunk / 32u];
+  __shared__ uint32_t cw1[2][kPairW];
+  __shared__ uint32_t zw1[2][kPairW];
+  __shared__ uint32_t xb1[2][kPairW];  // exception bits of each half's range (word-aligned)
+  __shared__ uint32_t xval[2][kChunk];  // input index of each exception, by position in range
+  __shared__ uint32_t scratch[33];
+  __shared__ uint32_t hs[2][12];
+  const LevelArgs &a1 = pa.l1;
+  const LevelArgs &a2 = pa.l2;
+  if (a1.ctrl[1]) return;  // level l's tails overflowed: the unfused fallback runs instead
+  const E *__restrict__ in = static_cast<const E *>(pa.in);
+  E *__restrict__ out = static_cast<E *>(pa.out);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint64_t nchunks = static_cast<uint64_t>(a2.M) * a2.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t R = static_cast<uint32_t>(cid / a2.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(R) * a2.J);
+    const MergeBounds mb2 = merge_bounds(a2, R);
+    const uint32_t N2 = static_cast<uint32_t>(mb2.e - mb2.s);
+    const uint32_t t0 = j * kChunk;
+    if (t0 >= N2) continue;  // uniform across the CTA
+    const uint32_t t1 = min(t0 + kChunk, N2);
+    const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);  // level l+1's first half
+    const uint32_t h2 = N2 - h1;
+    const uint4 mi2 = a2.minfo[R];
+    const uint32_t T2 = mi2.x;
+    const bool first_exh2 = (mi2.y == h1);
+    const uint32_t Z0 = a2.zc[cid];
+    const uint32_t tA = min(t1, T2);  // [t0, tA): interleave part of the chunk
+    if (tid < kChunk / 128u) {
+      const uint4 c = coin_block(a2.key, a2.level, R, j * (kChunk / 128u) + tid);
+      cw2[4u * tid + 0u] = c.x;
+      cw2[4u * tid + 1u] = c.y;
+      cw2[4u * tid + 2u] = c.z;
+      cw2[4u * tid + 3u] = c.w;
+    }
+    __syncthreads();
+    uint32_t zA;  // zeros in [t0, tA)
+    {
+      uint32_t z = 0;
+      if (tid < kChunk / 32u) {
+        const uint32_t tw = t0 + 32u * tid;
+        const uint32_t valid = tw >= tA ? 0u : min(32u, tA - tw);
+        z = __popc(~cw2[tid] & low_mask(valid));
+      }
+      const uint32_t excl = block_exclusive_scan(z, scratch, &zA);
+      if (tid < kChunk / 32u) zw2[tid] = excl;
+    }
+    // ranges of the two halves (merges 2R and 2R+1 of level l) this chunk reads
+    if (tid < 2u) {
+      const uint32_t h = tid;
+      const uint32_t ni = tA > t0 ? tA - t0 : 0u;  // interleave outputs
+      const uint32_t nl = t1 > max(t0, T2) ? t1 - max(t0, T2) : 0u;  // leftover outputs
+      uint32_t lo, cnt;
+      if (h == 0) {
+        lo = t0 < T2 ? Z0 : t0 - h2;
+        cnt = zA + (first_exh2 ? 0u : nl);
+      } else {
+        lo = t0 < T2 ? t0 - Z0 : t0 - h1;
+        cnt = (ni - zA) + (first_exh2 ? nl : 0u);
+      }
+      const uint32_t r1 = 2u * R + h;
+      const MergeBounds mb1 = merge_bounds(a1, r1);
+      const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
+      const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
+      const uint4 mi1 = a1.minfo[r1];
+      const uint32_t T1 = mi1.x;
+      const uint32_t hi = min(lo + cnt, T1);  // positions needing coins: [lo, hi)
+      const uint32_t blo = lo >> 7;
+      const uint32_t nblk = hi > lo ? ((hi + 127u) >> 7) - blo : 0u;
+      hs[h][0] = r1;
+      hs[h][1] = static_cast<uint32_t>(mb1.s);
+      hs[h][2] = n11;
+      hs[h][3] = T1;
+      hs[h][4] = (mi1.y == n11) ? 0u : N1 - n11;  // leftover shift: first half exhausted -> 0
+      hs[h][5] = blo;
+      hs[h][6] = nblk;
+      hs[h][8] = N1;
+      hs[h][9] = lo;
+      hs[h][10] = cnt;
+    }
+    __syncthreads();
+    // coin words of level l for both ranges (threads 0..127: half 0, 128..255: half 1), their
+    // zero counts, and the exception bits of the ranges
+    {
+      const uint32_t h = tid >> 7;
+      const uint32_t k = tid & 127u;
+      const uint32_t nblk = hs[h][6];
+      const uint32_t blo = hs[h][5];
+      const uint32_t N1 = hs[h][8];
+      if (k < 32u) {
+        // zeros before block blo: the chunk prefix plus the blocks of the chunk before it
+        const uint32_t chunk = blo >> 5;
+        const uint32_t b = chunk * 32u + k;
+        const uint64_t row = static_cast<uint64_t>(hs[h][0]) * a1.J;
+        uint32_t zb = (nblk && b < blo) ? a1.zb[row * 32u + b] : 0u;
+        zb = warp_sum(zb);
+        if (k == 0) hs[h][7] = nblk ? a1.zc[row + chunk] + zb : 0u;
+      }
+      if (k < nblk) {
+        const uint32_t blk = blo + k;
+        const uint4 c = coin_block(a1.key, a1.level, hs[h][0], blk);
+        cw1[h][4u * k + 0u] = c.x;
+        cw1[h][4u * k + 1u] = c.y;
+        cw1[h][4u * k + 2u] = c.z;
+        cw1[h][4u * k + 3u] = c.w;
+      }
+      // exception bit words for global positions [s1 + lo, s1 + lo + cnt)
+      const uint32_t g_lo = hs[h][1] + hs[h][9];
+      const uint32_t nw = hs[h][10] ? ((g_lo + hs[h][10] + 31u) >> 5) - (g_lo >> 5) : 0u;
+      const uint64_t nbw = (a1.n + 31u) >> 5;  // words of the bitmap
+      for (uint32_t wi = k; wi < nw && wi < kPairW; wi += 128u) {
+        const uint64_t bw = (g_lo >> 5) + wi;
+        xb1[h][wi] = bw < nbw ? pa.x.bits[bw] : 0u;
+      }
+      (void)N1;
+    }
+    __syncthreads();
+    {
+      // zero counts per word (valid positions of the merge), exclusive prefix per half
+      uint32_t z0 = 0, z1 = 0;  // thread k handles words 2k, 2k+1 of the combined array
+      const uint32_t wA = 2u * tid, wB = 2u * tid + 1u;
+      auto wz = [&](uint32_t wc) -> uint32_t {
+        const uint32_t h = wc >= kPairW ? 1u : 0u;
+        const uint32_t wi = wc - h * kPairW;
+        if (wi >= 4u * hs[h][6]) return 0u;
+        const uint32_t pos = 32u * (4u * hs[h][5] + wi);  // merge position of the word
+        const uint32_t N1 = hs[h][8];
+        const uint32_t valid = pos >= N1 ? 0u : min(32u, N1 - pos);
+        return __popc(~cw1[h][wi] & low_mask(valid));
+      };
+      if (wA < 2u * kPairW) z0 = wz(wA);
+      if (wB < 2u * kPairW) z1 = wz(wB);
+      uint32_t total;
+      const uint32_t excl = block_exclusive_scan(z0 + z1, scratch, &total);
+      // the prefix restarts at half 1 (word kPairW): its base is the scan value there
+      if (wA == kPairW) scratch[32] = excl;  // scratch[32] is free after the scan returned
+      __syncthreads();
+      const uint32_t base1 = scratch[32];
+      if (wA < 2u * kPairW) {
+        const uint32_t h = wA >= kPairW ? 1u : 0u;
+        zw1[h][wA - h * kPairW] = hs[h][7] + excl - (h ? base1 : 0u);
+      }
+      if (wB < 2u * kPairW) {
+        const uint32_t h = wB >= kPairW ? 1u : 0u;
+        zw1[h][wB - h * kPairW] = hs[h][7] + excl + z0 - (h ? base1 : 0u);
+      }
+    }
+    // exceptions of both ranges, looked up once per chunk: every set bit of the range's bitmap
+    // words is a position whose element the tail moved
+    {
+      const uint32_t hmask = (1u << pa.x.hbits) - 1u;
+      for (uint32_t wc = tid; wc < 2u * kPairW; wc += kThreads) {
+        const uint32_t h = wc >= kPairW ? 1u : 0u;
+        const uint32_t wi = wc - h * kPairW;
+        const uint32_t cnt = hs[h][10];
+        if (cnt == 0) continue;
+        const uint32_t g_lo = hs[h][1] + hs[h][9];
+        const uint32_t nw = ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5);
+        if (wi >= nw) continue;
+        uint32_t bits = xb1[h][wi];
+        while (bits) {
+          const uint32_t b = __ffs(static_cast<int>(bits)) - 1u;
+          bits &= bits - 1u;
+          const uint32_t gq = (((g_lo >> 5) + wi) << 5) + b;
+          if (gq < g_lo || gq >= g_lo + cnt) continue;
+          uint32_t slot = xhash_slot(gq, pa.x.hbits);
+          uint32_t xs = 0u;
+          for (uint32_t probe = 0; probe <= hmask; ++probe) {
+            const uint32_t key = pa.x.keys[slot];
+            if (key == gq) {
+              xs = pa.x.vals[slot];
+              break;
+            }
+            if (key == 0xFFFFFFFFu) break;
+            slot = (slot + 1u) & hmask;
+          }
+          xval[h][gq - g_lo] = xs;
+        }
+      }
+    }
+    __syncthreads();
+    // per-half constants in registers
+    uint32_t hs1[2], hn11[2], hT1[2], hshift[2], hw0[2], hglo[2];
+#pragma unroll
+    for (uint32_t h = 0; h < 2u; ++h) {
+      hs1[h] = hs[h][1];
+      hn11[h] = hs[h][2];
+      hT1[h] = hs[h][3];
+      hshift[h] = hs[h][4];
+      hw0[h] = 4u * hs[h][5];
+      hglo[h] = hs[h][1] + hs[h][9];
+    }
+    // outputs: lane = position in a word of level l+1; warp w owns words w, w+8, ...
+    E *C = out + mb2.s;
+    constexpr uint32_t kWarps = kThreads / 32;
+    constexpr uint32_t kWordsPerWarp = kChunk / 32u / kWarps;
+    constexpr uint32_t kBatch = sizeof(E) >= 16 ? 4u : 8u;
+#pragma unroll
+    for (uint32_t b0 = 0; b0 < kWordsPerWarp; b0 += kBatch) {
+      E v[kBatch];
+#pragma unroll
+      for (uint32_t k = 0; k < kBatch; ++k) {
+        const uint32_t u = warp + (b0 + k) * kWarps;
+        const uint32_t t = t0 + 32u * u + lane;
+        if (t < t1) {
+          uint32_t h, p;  // half and merge position in level l's merge 2R + h
+          if (t < T2) {
+            const uint32_t word = cw2[u];
+            const uint32_t Z = Z0 + zw2[u] + __popc(~word & low_mask(lane));
+            h = (word >> lane) & 1u;
+            p = h ? t - Z : Z;
+          } else {
+            h = first_exh2 ? 1u : 0u;
+            p = first_exh2 ? t - h1 : t - h2;
+          }
+          const uint32_t s1 = h ? hs1[1] : hs1[0];
+          const uint32_t gq = s1 + p;
+          const uint32_t glo = h ? hglo[1] : hglo[0];
+          const uint32_t bw = (gq >> 5) - (glo >> 5);
+          uint32_t xs;
+          if ((xb1[h][min(bw, kPairW - 1u)] >> (gq & 31u)) & 1u) {
+            // exception: the tail moved another element here
+            xs = xval[h][min(gq - glo, kChunk - 1u)];
+          } else if (p < (h ? hT1[1] : hT1[0])) {
+            const uint32_t wi = min((p >> 5) - (h ? hw0[1] : hw0[0]), kPairW - 1u);
+            const uint32_t word = cw1[h][wi];
+            const uint32_t Z = zw1[h][wi] + __popc(~word & low_mask(p & 31u));
+            xs = s1 + (((word >> (p & 31u)) & 1u) ? (h ? hn11[1] : hn11[0]) + p - Z : Z);
+          } else {
+            xs = s1 + p - (h ? hshift[1] : hshift[0]);
+          }
+          v[k] = in[xs < a1.n ? xs : 0u];  // the clamp keeps every load inside the array
+        }
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < kBatch; ++k) {
+        const uint32_t t = t0 + 32u * (warp + (b0 + k) * kWarps) + lane;
+        if (t < t1) C[t] = v[k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kThreads) copy_kernel(LevelArgs a) {
+  if (gated_off(a)) return;
+  const E *in = static_cast<const E *>(a.in);
+  E *out = static_cast<E *>(a.out);
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x; i < a.n;
+       i += static_cast<uint64_t>(gridDim.x) * kThreads)
+    out[i] = in[i];
+}
+
 unsigned grid_for(uint64_t items, uint64_t per_block, uint64_t cap) {
   uint64_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -498,6 +861,11 @@ LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.pdst = b.pdst;
   a.psrc = b.psrc;
   a.ptmp = b.ptmp;
+  a.zb = nullptr;
+  a.gate = nullptr;
+  a.gate_on = 0;
+  a.out_alt = nullptr;
+  a.alt_sel = nullptr;
   return a;
 }
 
@@ -530,9 +898,10 @@ cudaError_t launch_data_t(const Plan &p, const LevelPlan &lv, const void *in, vo
 
 }  // namespace
 
-cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers &b, uint64_t seed,
-                              cudaStream_t s) {
-  const LevelArgs a = level_args(p, lv, nullptr, nullptr, b, seed);
+namespace {
+
+cudaError_t plan_kernels(const Plan &p, const LevelArgs &a, const LevelPlan &lv, const Buffers &b,
+                         cudaStream_t s) {
   const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
   timed(p.prof, kKindCount, s, [&] {
     count_kernel<<<grid_for(nchunks, kThreads / 32, 1u << 20), kThreads, 0, s>>>(a);
@@ -548,6 +917,97 @@ cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers 
   timed(p.prof, kKindInsert, s, [&] { tail_insert_kernel<<<kResident, kThreads, 0, s>>>(a); });
   timed(p.prof, kKindResolve, s, [&] { tail_resolve_kernel<<<kResident, kThreads, 0, s>>>(a); });
   return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t pair_data_t(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2, const void *in,
+                        void *out, const Buffers &b1, const Buffers &b2, uint64_t seed,
+                        cudaStream_t s) {
+  void *X = const_cast<void *>(in);  // dead after the pair: the fallback's scratch
+  const uint32_t *ovf = b1.ctrl + 1;  // level l's tails overflowed its capacity
+  PairArgs pa;
+  pa.in = in;
+  pa.out = out;
+  pa.l1 = level_args(p, lv1, in, out, b1, seed);
+  pa.l1.zb = b1.zb;
+  pa.l2 = level_args(p, lv2, out, out, b2, seed);
+  pa.x.bits = b1.xbits;
+  pa.x.keys = b1.xkeys;
+  pa.x.vals = b1.xvals;
+  pa.x.hbits = lv1.xhbits;
+  const uint64_t nchunks2 = static_cast<uint64_t>(lv2.M) * lv2.J;
+  timed(p.prof, kKindPairGather, s, [&] {
+    pair_gather_kernel<E><<<grid_for(nchunks2, 1, 1u << 20), kThreads, 0, s>>>(pa);
+  });
+  // unfused fallback (each kernel returns at once unless level l overflowed): level l from X
+  // into out with its tail in order, level l+1 from out back into X
+  LevelArgs f1 = level_args(p, lv1, in, out, b1, seed);
+  f1.gate = ovf;
+  f1.gate_on = 1;
+  const uint64_t nchunks1 = static_cast<uint64_t>(lv1.M) * lv1.J;
+  gather_kernel<E><<<grid_for(nchunks1, 1, 1u << 20), kThreads, 0, s>>>(f1);
+  tail_sequential_kernel<E><<<grid_for(lv1.M, kThreads, 1u << 16), kThreads, 0, s>>>(f1);
+  LevelArgs f2 = level_args(p, lv2, out, X, b2, seed);
+  f2.gate = ovf;
+  f2.gate_on = 1;
+  gather_kernel<E><<<grid_for(nchunks2, 1, 1u << 20), kThreads, 0, s>>>(f2);
+  // level l+1's tail, on out (fused) or on X (fallback)
+  LevelArgs t2 = level_args(p, lv2, nullptr, out, b2, seed);
+  t2.out_alt = X;
+  t2.alt_sel = ovf;
+  timed(p.prof, kKindTailSeq, s, [&] {
+    tail_sequential_kernel<E><<<grid_for(lv2.M, kThreads, 1u << 16), kThreads, 0, s>>>(t2);
+  });
+  timed(p.prof, kKindPatchRead, s,
+        [&] { patch_read_kernel<E><<<kResident, kThreads, 0, s>>>(t2); });
+  timed(p.prof, kKindPatchWrite, s,
+        [&] { patch_write_kernel<E><<<kResident, kThreads, 0, s>>>(t2); });
+  LevelArgs cp = level_args(p, lv2, X, out, b2, seed);
+  cp.gate = ovf;
+  cp.gate_on = 1;
+  copy_kernel<E><<<kResident, kThreads, 0, s>>>(cp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers &b, uint64_t seed,
+                              cudaStream_t s) {
+  return plan_kernels(p, level_args(p, lv, nullptr, nullptr, b, seed), lv, b, s);
+}
+
+cudaError_t launch_pair_plan(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2,
+                             const Buffers &b1, const Buffers &b2, uint64_t seed, cudaStream_t s) {
+  LevelArgs a1 = level_args(p, lv1, nullptr, nullptr, b1, seed);
+  a1.zb = b1.zb;
+  cudaError_t err = plan_kernels(p, a1, lv1, b1, s);
+  if (err != cudaSuccess) return err;
+  // the first level's tail moves as exceptions of the pair's data pass
+  err = cudaMemsetAsync(b1.xbits, 0, (p.n + 31) / 32 * 4, s);
+  if (err != cudaSuccess) return err;
+  err = cudaMemsetAsync(b1.xkeys, 0xFF, sizeof(uint32_t) << lv1.xhbits, s);
+  if (err != cudaSuccess) return err;
+  ExcArgs x;
+  x.bits = b1.xbits;
+  x.keys = b1.xkeys;
+  x.vals = b1.xvals;
+  x.hbits = lv1.xhbits;
+  timed(p.prof, kKindExceptions, s,
+        [&] { exceptions_kernel<<<kResident, kThreads, 0, s>>>(a1, x); });
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return plan_kernels(p, level_args(p, lv2, nullptr, nullptr, b2, seed), lv2, b2, s);
+}
+
+cudaError_t launch_pair_data(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2,
+                             const void *in, void *out, const Buffers &b1, const Buffers &b2,
+                             uint64_t seed, cudaStream_t s) {
+  switch (p.w) {
+    case 4: return pair_data_t<uint32_t>(p, lv1, lv2, in, out, b1, b2, seed, s);
+    case 8: return pair_data_t<uint2>(p, lv1, lv2, in, out, b1, b2, seed, s);
+    case 16: return pair_data_t<uint4>(p, lv1, lv2, in, out, b1, b2, seed, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,

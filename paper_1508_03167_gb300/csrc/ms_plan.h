@@ -38,6 +38,8 @@ enum KernelKind : int {
   kKindPatchWrite,
   kKindLocal,
   kKindEngine,
+  kKindPairGather,
+  kKindExceptions,
   kKindNum
 };
 
@@ -60,6 +62,10 @@ struct LevelPlan {
   bool local;
   bool warp_local;      // one warp per span (no CTA barriers)
   bool span;            // streamed spans with asynchronous prefetch (ms_span.cu)
+  // global levels fused in pairs: 1 = first level of a pair (its tail moves become exceptions
+  // of the pair's single data pass), 2 = second level of a pair, 0 = unpaired
+  uint32_t pair;
+  uint32_t xhbits;  // exception hash of a pair's first level: 2^xhbits slots
   uint32_t span_threads;  // 128 or 256 threads a CTA
   uint32_t warp_bytes;  // shared memory of one warp's span (warp-local mode)
   uint32_t mlog;
@@ -99,6 +105,12 @@ struct Plan {
          off_hvals = 0, off_pdst = 0, off_psrc = 0, off_ptmp = 0, ws_bytes = 0;
   size_t plan_set_bytes = 0;
   uint32_t plan_sets = 0;
+  // exception structures of a pair's first level (offsets within one copy; one copy per two
+  // plan sets): per-block zero counts (one byte per 128 coins), the exception bitmap (one bit
+  // per element) and the exception hash (keys, values)
+  size_t off_zb = 0, off_xbits = 0, off_xkeys = 0, off_xvals = 0, exc_base = 0, exc_bytes = 0;
+  uint32_t units = 0;         // global-level units: single levels and fused pairs
+  uint32_t hbm_passes = 0;    // data passes after the base-block pass
   uint32_t zc_cap = 0, minfo_cap = 0, kcap_max = 0, hbits_max = 0;
   bool buffer_in_ws = true;  // false for the host form, where both buffers live in ws
 };
@@ -111,6 +123,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
 struct Buffers {
   void *data;       // caller's array (result lands here)
   void *other;      // ping-pong partner
+  uint8_t *zb;
+  uint32_t *xbits;
+  uint32_t *xkeys;
+  uint32_t *xvals;
   uint32_t *zc;
   uint4 *minfo;
   uint32_t *ctrl;
@@ -131,6 +147,16 @@ cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers 
                               cudaStream_t s);
 cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                               const Buffers &b, uint64_t seed, cudaStream_t s);
+// Two consecutive global levels fused into one data pass (b1: the first level's plan set, with
+// its exception structures; b2: the second's). The plan builds both levels' plans and turns the
+// first level's tail moves into exceptions; the data pass gathers the second level's output
+// straight from the first level's input (unfused fallback, gated on the device, if the first
+// level's tails overflowed its capacity).
+cudaError_t launch_pair_plan(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2,
+                             const Buffers &b1, const Buffers &b2, uint64_t seed, cudaStream_t s);
+cudaError_t launch_pair_data(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2,
+                             const void *in, void *out, const Buffers &b1, const Buffers &b2,
+                             uint64_t seed, cudaStream_t s);
 cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                                uint64_t seed, cudaStream_t s);
 cudaError_t launch_warp_level(const Plan &p, const LevelPlan &lv, const void *in, void *out,

@@ -38,14 +38,22 @@ ms_status scratch_address(void **out) {
 extern "C" ms_status ms_perm_static(uint32_t *d_out, uint64_t n, uint64_t seed,
                                     const ms_params *p, ms_stream_t stream) {
   if (n > MS_STATIC_MAX_N) return MS_ERR_UNSUPPORTED;
-  const size_t need = ms_workspace_bytes(n, 4, p);
+  ms_params q;
+  ms_default_params(&q);
+  if (p) q = *p;
+  size_t need = ms_workspace_bytes(n, 4, &q);
   if (need == 0) return MS_ERR_INVALID;
+  if (need > kStaticBytes) {
+    // one data pass per level needs less plan scratch (the result is the same)
+    q.flags |= MS_FLAG_SINGLE_LEVELS;
+    need = ms_workspace_bytes(n, 4, &q);
+  }
   if (need > kStaticBytes) return MS_ERR_UNSUPPORTED;
-  if (n <= 1) return ms_perm(d_out, n, seed, nullptr, 0, p, stream);
+  if (n <= 1) return ms_perm(d_out, n, seed, nullptr, 0, &q, stream);
   void *ws = nullptr;
   const ms_status st = scratch_address(&ws);
   if (st != MS_OK) return st;
   // Nothing in the scratch has to start at zero: every kernel writes what it later reads, and
   // the merge-level hash table is reset on the stream before each level.
-  return ms_perm(d_out, n, seed, ws, kStaticBytes, p, stream);
+  return ms_perm(d_out, n, seed, ws, kStaticBytes, &q, stream);
 }

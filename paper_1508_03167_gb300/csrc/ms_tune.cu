@@ -33,7 +33,8 @@ uint32_t ceil_log2(uint64_t n) {
 bool entry_valid(const ms_tune_entry &e) {
   return (e.w == 4 || e.w == 8 || e.w == 16) && e.batch <= 1 && e.B >= 1 && e.B <= MS_MAX_B &&
          e.fuse_depth >= -1 && e.log2n_max <= 64 &&
-         (e.flags & ~(MS_FLAG_CTA_LEVELS | MS_FLAG_GLOBAL_LEVELS)) == 0;
+         (e.flags & ~(MS_FLAG_CTA_LEVELS | MS_FLAG_GLOBAL_LEVELS | MS_FLAG_SINGLE_LEVELS |
+                      MS_FLAG_PAIR_LEVELS)) == 0;
 }
 
 // First entry (w, batch) with ceil(log2 n) <= log2n_max, else the largest bucket of (w, batch),
@@ -63,7 +64,9 @@ ms_tune_entry lookup(uint64_t n, uint32_t w, uint32_t batch) {
 void apply(const ms_tune_entry &e, ms_params *p) {
   p->B = e.B;
   if (p->fuse_depth < 0) p->fuse_depth = e.fuse_depth;
-  if ((p->flags & (MS_FLAG_CTA_LEVELS | MS_FLAG_GLOBAL_LEVELS)) == 0) p->flags |= e.flags;
+  const uint32_t mode = MS_FLAG_CTA_LEVELS | MS_FLAG_GLOBAL_LEVELS | MS_FLAG_SINGLE_LEVELS |
+                        MS_FLAG_PAIR_LEVELS;
+  if ((p->flags & mode) == 0) p->flags |= e.flags;
 }
 
 }  // namespace

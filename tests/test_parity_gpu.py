@@ -154,3 +154,34 @@ def test_autotuned_B_matches_oracle_at_the_resolved_B(n):
     got = gpu_perm(n, 11, 0)
     want, _ = oracle.perm(n, 11, r.B)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n,B", [(1 << 20, 1024), (262147, 16), (100003, 3), (65537, 1),
+                                 (1000003, 64)])
+def test_fused_level_pairs_match_single_levels(n, B):
+    """Consecutive global levels share one data pass (the first level's tail moves become
+    exceptions of the second level's gather); one pass per level, the unfused device-side
+    fallback (forced by the sequential-tail flag) and the oracle all agree."""
+    want, _ = oracle.perm(n, 17, B)
+    pl = ms.MS_FLAG_PAIR_LEVELS
+    assert ms.plan(n, 4, B=B, fuse_depth=0, flags=pl | ms.MS_FLAG_GLOBAL_LEVELS)["fused_pairs"] > 0
+    assert np.array_equal(gpu_perm(n, 17, B, fuse_depth=0, flags=pl), want)
+    assert np.array_equal(gpu_perm(n, 17, B, fuse_depth=0, flags=ms.MS_FLAG_SINGLE_LEVELS), want)
+    assert np.array_equal(gpu_perm(n, 17, B, fuse_depth=0, flags=pl | ms.MS_FLAG_GLOBAL_LEVELS),
+                          want)
+    assert np.array_equal(
+        gpu_perm(n, 17, B, fuse_depth=0,
+                 flags=pl | ms.MS_FLAG_GLOBAL_LEVELS | ms.MS_FLAG_TAIL_SEQUENTIAL), want)
+
+
+@pytest.mark.parametrize("w", [8, 16])
+def test_fused_level_pairs_wide_elements(w):
+    n, B = 300017, 16
+    arr = inputs.records16(n) if w == 16 else inputs.values_u64(n, 3)
+    want, _ = oracle.shuffle(arr, 9, B)
+    pl = ms.MS_FLAG_PAIR_LEVELS
+    assert np.array_equal(
+        gpu_shuffle(arr, 9, B, fuse_depth=0, flags=pl | ms.MS_FLAG_GLOBAL_LEVELS), want)
+    assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=pl), want)
+    assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=ms.MS_FLAG_SINGLE_LEVELS),
+                          want)
