@@ -161,12 +161,6 @@ def measured_peaks() -> dict:
 GATHER_TRAFFIC_PER_ELEM = {4: 7.311, 16: 28.71}
 
 
-def g_levels(ms, n, w, p) -> int:
-    """Merge levels of the plan that run through the global streaming gather."""
-    plan = ms.ms_plan_info(n, w, p)
-    return plan.global_levels
-
-
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -232,18 +226,22 @@ def run_ours(args, world, rank, local):
     elems = n_perm + n_rec
     value = world * elems / (t_ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (the streaming gather of each HBM merge level):
-    # algorithmic bytes per launch = read n*w + write n*w
+    # roofline of the dominant kernel, the streaming gather of a global merge level (one
+    # launch per unfused level): algorithmic bytes per launch = read n*w + write n*w. Fused
+    # pairs of levels (a pair_gather launch each, also one read and one write of the array) are
+    # reported beside it.
     g = prof["gather"]
-    # bytes per gather launch: each global merge level reads and writes its array once
-    nglob_perm = g_levels(ms, n_perm, 4, p_perm)
-    nglob_rec = g_levels(ms, n_rec, 16, p_rec)
-    gather_bytes = args.steps * (nglob_perm * 2 * n_perm * 4 + nglob_rec * 2 * n_rec * 16)
+    pg = prof.get("pair_gather", {"ms": 0.0, "launches": 0})
+    single_perm = plan_perm.global_levels - 2 * plan_perm.fused_pairs
+    single_rec = plan_rec.global_levels - 2 * plan_rec.fused_pairs
+    gather_bytes = args.steps * (single_perm * 2 * n_perm * 4 + single_rec * 2 * n_rec * 16)
+    pair_bytes = args.steps * (plan_perm.fused_pairs * 2 * n_perm * 4 +
+                               plan_rec.fused_pairs * 2 * n_rec * 16)
     peaks = measured_peaks()
     achieved = gather_bytes / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else 0.0
-    nlaunch = nglob_perm + nglob_rec
-    traffic = ((nglob_perm * GATHER_TRAFFIC_PER_ELEM[4] * n_perm +
-                nglob_rec * GATHER_TRAFFIC_PER_ELEM[16] * n_rec) / nlaunch) if nlaunch else None
+    nlaunch = single_perm + single_rec
+    traffic = ((single_perm * GATHER_TRAFFIC_PER_ELEM[4] * n_perm +
+                single_rec * GATHER_TRAFFIC_PER_ELEM[16] * n_rec) / nlaunch) if nlaunch else None
     roofline = {
         "bound": "hbm",
         "kernel": "gather (HBM merge level)",
@@ -256,9 +254,18 @@ def run_ours(args, world, rank, local):
         "traffic_note": "bytes per gather launch (dram read+write), ncu on a smaller case "
                         "scaled by elements; the small case leaves ~50 MB of writes in L2",
         "algorithmic_bytes_per_launch": {"perm": 2 * n_perm * 4, "rec": 2 * n_rec * 16},
+        "launches_per_step": {"perm": single_perm, "rec": single_rec},
         "avg_launch_ms": round(g["ms"] / max(g["launches"], 1), 4),
+        "pair_gather": {
+            "launches_per_step": {"perm": plan_perm.fused_pairs, "rec": plan_rec.fused_pairs},
+            "achieved_gbs": round(pair_bytes / (pg["ms"] * 1e-3) / 1e9, 1) if pg["ms"] else None,
+        },
         "whole_path_frac": round(
             (plan_perm.passes * 2 * n_perm * 4 + plan_rec.passes * 2 * n_rec * 16) / 1e9
+            / (t_ms * 1e-3) / peaks["hbm_gbs"], 4),
+        "whole_path_frac_unfused": round(
+            ((plan_perm.passes + plan_perm.fused_pairs) * 2 * n_perm * 4 +
+             (plan_rec.passes + plan_rec.fused_pairs) * 2 * n_rec * 16) / 1e9
             / (t_ms * 1e-3) / peaks["hbm_gbs"], 4),
     }
     kernel_ms = {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}
@@ -330,6 +337,8 @@ def run_ours(args, world, rank, local):
             "B_source": "autotuner table" if args.B_perm == 0 else "command line",
             "fuse_depth_perm": plan_perm.fuse_depth, "fuse_depth_rec": plan_rec.fuse_depth,
             "passes_perm": plan_perm.passes, "passes_rec": plan_rec.passes,
+            "fused_level_pairs_perm": plan_perm.fused_pairs,
+            "fused_level_pairs_rec": plan_rec.fused_pairs,
             "l2": "inputs larger than L2 (4.3 GB and 4.8 GB arrays), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
             "profiled_events": "CUDA event pair around every kernel during the timed region",
