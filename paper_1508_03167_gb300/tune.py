@@ -23,9 +23,9 @@ HEADER = os.path.join(HERE, "csrc", "ms_tune_table.h")
 JSON_PATH = os.path.join(HERE, "tune_table.json")
 
 B_CANDIDATES = (32, 64, 128, 256, 512, 1024)
-# (fuse_depth, flags) alternatives per B: the planner's fusion depth or none; per-warp or
-# per-CTA small levels
-MODE_CANDIDATES = ((-1, 0), (0, 0), (0, 0x8))
+# (fuse_depth, flags) alternatives per B: the planner's fusion depth or none; the default small
+# levels or per-CTA ones; one data pass per global level or fused pairs of them
+MODE_CANDIDATES = ((-1, 0), (0, 0), (0, 0x8), (0, 0x80), (0, 0x100))
 # size points per width: log2 n (the largest fits a 2 x n x w footprint comfortably); sizes are
 # 2^k for w = 4 and 2^k + 17 otherwise (uneven halves), except that the last 16-byte point is
 # the 300,000,017-record workload itself
@@ -177,6 +177,8 @@ def tune(quick: bool = False, reps: int = 5, log=print) -> list[dict]:
                 if B >= n:
                     continue
                 for fd, fl in MODE_CANDIDATES:
+                    if fl in (0x80, 0x100) and lg < 20:
+                        continue  # few global levels: nothing to fuse
                     timings[(B, fd, fl)] = time_single(n, w, B, fd, fl, reps)
             B, fd, fl = pick(timings)
             log(f"single w={w:2d} n=2^{lg}: B={B} fuse_depth={fd} flags={fl:#x} "
