@@ -185,3 +185,33 @@ def test_fused_level_pairs_wide_elements(w):
     assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=pl), want)
     assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=ms.MS_FLAG_SINGLE_LEVELS),
                           want)
+
+
+def test_concurrent_calls_on_two_streams_from_two_threads():
+    """Two host threads call the library at once, each on its own stream (each caller stream gets
+    its own plan stream and events); both results equal the oracle's."""
+    import threading
+
+    torch = _torch()
+    jobs = [(1 << 20, 5, 128), (700001, 6, 64)]
+    outs = {}
+
+    def work(i, n, seed, B):
+        s = torch.cuda.Stream()
+        p = ms.params(B=B, fuse_depth=0)
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        ws = torch.empty(ms.ms_workspace_bytes(n, 4, p), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            assert ms.ms_perm(out.data_ptr(), n, seed, ws.data_ptr(), ws.numel(), p,
+                              s.cuda_stream) == ms.MS_OK
+        s.synchronize()
+        outs[i] = out.cpu().numpy().view(np.uint32)
+
+    th = [threading.Thread(target=work, args=(i, *j)) for i, j in enumerate(jobs)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i, (n, seed, B) in enumerate(jobs):
+        want, _ = oracle.perm(n, seed, B)
+        assert np.array_equal(outs[i], want), i

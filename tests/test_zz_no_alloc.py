@@ -59,3 +59,15 @@ def test_static_entry_point_rejects_sizes_beyond_its_scratch():
     big = ms.params(B=1, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS)
     assert ms.ms_workspace_bytes(1 << 20, 4, big) > ms.MS_STATIC_SCRATCH_BYTES
     assert ms.ms_perm_static(out.data_ptr(), 1 << 20, 1, big, s) == ms.MS_ERR_UNSUPPORTED
+
+
+def test_static_entry_point_at_its_size_limit():
+    """n = MS_STATIC_MAX_N with the default cutoff: the entry point runs the plan whose scratch
+    fits the fixed array (one data pass per global level) and still matches ms_perm."""
+    import torch
+
+    n = ms.MS_STATIC_MAX_N
+    p = ms.params(B=1024)
+    want = _perm_with_workspace(torch, n, 3, p)
+    got = _perm_static(torch, n, 3, p)
+    assert np.array_equal(got, want)
