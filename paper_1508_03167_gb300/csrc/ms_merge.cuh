@@ -88,6 +88,47 @@ __device__ __forceinline__ uint32_t draw_with_word0(uint2 key, uint32_t tag, uin
   return draw_continue(key, tag, level, id, pos, R);
 }
 
+// The same draw for Algorithm 1's inner loop, where every lane draws at every step: the first
+// four slices of a word are tested without branches (the first one below R wins, as above), so
+// lanes rejecting their first slice do not split the warp, and the continuation is inlined.
+__device__ __forceinline__ bool draw_from_word_flat(uint32_t word, uint32_t R, uint32_t &x) {
+  const uint32_t b = 32u - __clz(R - 1u);
+  const uint32_t mask = (b == 32u) ? 0xFFFFFFFFu : ((1u << b) - 1u);
+  // floor(32 / b), exact as in draw_from_word
+  const uint32_t slices = static_cast<uint32_t>(__fdividef(32.0f, static_cast<float>(b)));
+  uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+  for (int u = 3; u >= 0; --u) {
+    const uint32_t v = (word >> min(static_cast<uint32_t>(u) * b, 31u)) & mask;
+    if (static_cast<uint32_t>(u) < slices && v < R) best = v;
+  }
+  if (best != 0xFFFFFFFFu) {
+    x = best;
+    return true;
+  }
+  for (uint32_t u = 4; u < slices; ++u) {
+    const uint32_t v = (word >> (u * b)) & mask;
+    if (v < R) {
+      x = v;
+      return true;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t draw_with_word0_flat(uint2 key, uint32_t tag, uint32_t level,
+                                                         uint32_t id, uint32_t pos, uint32_t R,
+                                                         uint32_t word0) {
+  if (R <= 1u) return 0u;
+  uint32_t x;
+  if (draw_from_word_flat(word0, R, x)) return x;
+  for (uint32_t j = 1; j < (1u << 20); ++j) {
+    const uint4 blk = philox10(make_uint4(pos >> 2, id, (tag << 16) | level, j), key);
+    if (draw_from_word_flat(pick_word(blk, pos & 3u), R, x)) return x;
+  }
+  return 0u;
+}
+
 // Algorithm 1 (descending Fisher-Yates) on one base block of L elements in shared memory:
 // for i = L-1 .. 1, swap blk[i] with blk[j], j uniform in {0..i} from the LEAF stream of block
 // `id` at position i. Positions go in quads (one Philox block serves four of them), and the
@@ -106,7 +147,8 @@ __device__ __forceinline__ void fisher_yates_block(E *blk, uint32_t L, uint32_t 
     for (uint32_t v = 4; v-- > 0;) {
       const uint32_t pos = lo + v;
       if (pos <= i && pos >= 1u) {
-        const uint32_t j = draw_with_word0(key, kTagLeaf, 0u, id, pos, pos + 1u, pick_word(cur, v));
+        const uint32_t j =
+            draw_with_word0_flat(key, kTagLeaf, 0u, id, pos, pos + 1u, pick_word(cur, v));
         swap_smem(blk, pos, j);
       }
     }
