@@ -27,8 +27,15 @@
  *
  * Memory. The library never allocates device memory and never synchronises a stream unless
  * an entry point says so. The caller passes a device workspace of ms_workspace_bytes() bytes
- * (256-byte aligned); it holds the second ping-pong buffer of n*w bytes plus O(n/4096 + tails)
- * bytes of plan scratch. Total device footprint: 2*n*w bytes + scratch.
+ * (256-byte aligned); it holds the second ping-pong buffer of n*w bytes plus the plan scratch
+ * of the merge levels (coin prefixes per 4096 steps, tail tables sized to the expected tails,
+ * double-buffered so the next level is planned while one streams; fused level pairs add a
+ * bitmap of n/8 bytes and an exception hash). Total device footprint: 2*n*w bytes + scratch
+ * (the scratch is about 0.4*n*w for 4-byte elements at n = 2^30).
+ *
+ * Streams. Each call enqueues on the caller's stream; the data-independent plan of the global
+ * merge levels runs on a second, high-priority stream paired with the caller's (created on first
+ * use, ordered with events) unless MS_FLAG_SINGLE_STREAM is set.
  *
  * Errors. Argument errors are returned synchronously. Launch failures return MS_ERR_CUDA
  * (the CUDA error is not cleared). Nothing traps on the device.

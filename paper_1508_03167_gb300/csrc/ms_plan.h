@@ -58,20 +58,21 @@ struct LevelPlan {
   uint32_t J;      // chunks of kChunk steps per merge
   uint32_t kcap;   // capacity for tail steps summed over the level's merges
   uint32_t hbits;  // hash table of 2^hbits slots
-  // local mode: every merge finishes inside one CTA (2^mlog merges per CTA)
-  bool local;
-  bool warp_local;      // one warp per span (no CTA barriers)
-  bool span;            // streamed spans with asynchronous prefetch (ms_span.cu)
+  // local modes: every merge finishes inside one CTA or warp, 2^mlog merges at a time
+  bool local;             // any of the three local modes below (else the global plan)
+  bool warp_local;        // one warp per group of merges, global to global (ms_wlevel.cu)
+  bool span;              // streamed spans with asynchronous prefetch (ms_span.cu)
+                          // (local and neither: one CTA per span staged in shared memory)
+  uint32_t span_threads;  // span mode: 128 or 256 threads a CTA
+  uint32_t warp_bytes;    // warp mode: shared memory of one warp
+  uint32_t mlog;
+  uint32_t span_max;      // elements of the largest span (span mode: the span buffer)
+  uint32_t ucap, tcap;    // coin words and precomputed tail draws a span or warp holds
+  size_t smem;            // dynamic shared memory a CTA (span and CTA modes)
   // global levels fused in pairs: 1 = first level of a pair (its tail moves become exceptions
   // of the pair's single data pass), 2 = second level of a pair, 0 = unpaired
   uint32_t pair;
   uint32_t xhbits;  // exception hash of a pair's first level: 2^xhbits slots
-  uint32_t span_threads;  // 128 or 256 threads a CTA
-  uint32_t warp_bytes;  // shared memory of one warp's span (warp-local mode)
-  uint32_t mlog;
-  uint32_t span_max;  // elements of the largest CTA span
-  uint32_t ucap, tcap;
-  size_t smem;
 };
 
 struct Plan {
@@ -83,12 +84,9 @@ struct Plan {
   uint32_t d = 0;            // fused levels
   uint64_t tiles = 0;
   uint32_t tile_max = 0;     // elements
-  uint32_t unit_cap = 0;     // coin words per tile level (shared-memory arrays)
   uint32_t leaf_max = 0;     // largest base block: ceil(n / q)
   uint32_t leaf_stride = 0;  // odd shared-memory stride of one base block (>= leaf_max)
   uint32_t buf0_elems = 0;   // first tile buffer: max(2^d * leaf_stride, tile_max)
-  uint32_t tail_cap = 0;     // precomputed tail draws per tile level
-  uint32_t buf1_bytes = 0;   // unused
   uint32_t dw = 0;           // fused levels done by single warps (the rest, d - dw <= 3, by the CTA)
   uint32_t ucap_w = 0, tcap_w = 0, ucap_c = 0, tcap_c = 0;  // per-group coin-word / draw capacity
   uint32_t aux_w = 0;        // bytes of one warp's auxiliary shared-memory region
@@ -112,7 +110,6 @@ struct Plan {
   uint32_t units = 0;         // global-level units: single levels and fused pairs
   uint32_t hbm_passes = 0;    // data passes after the base-block pass
   uint32_t zc_cap = 0, minfo_cap = 0, kcap_max = 0, hbits_max = 0;
-  bool buffer_in_ws = true;  // false for the host form, where both buffers live in ws
 };
 
 // Builds the plan; returns 0 on success, 1 for invalid arguments, 2 for unsupported ones.
