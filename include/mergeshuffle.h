@@ -276,6 +276,14 @@ ms_status ms_profile_read(ms_profile *out, int reset);
 /* Human-readable name of a status code (static storage). */
 const char *ms_status_string(ms_status s);
 
+/*
+ * The CUDA error (a cudaError_t value, 0 = none) behind the calling thread's most recent
+ * MS_ERR_CUDA from a single-call or batched entry point, and its description (static storage).
+ * The library does not clear CUDA's own error state.
+ */
+int ms_last_cuda_error(void);
+const char *ms_last_cuda_error_string(void);
+
 /* Library version string (static storage). */
 const char *ms_version(void);
 

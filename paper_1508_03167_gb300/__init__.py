@@ -19,7 +19,7 @@ __all__ = [
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
     "ms_shuffle", "ms_perm", "ms_host_workspace_bytes", "ms_shuffle_host", "ms_perm_host",
-    "ms_status_string", "ms_version", "ms_perm_static", "MS_STATIC_MAX_N", "MS_STATIC_SCRATCH_BYTES", "params", "plan", "shuffle_", "perm", "shuffle_host",
+    "ms_status_string", "ms_version", "ms_last_cuda_error", "ms_perm_static", "MS_STATIC_MAX_N", "MS_STATIC_SCRATCH_BYTES", "params", "plan", "shuffle_", "perm", "shuffle_host",
     "perm_host", "workspace", "MsTuneEntry", "ms_resolve_params", "ms_resolve_batch_params",
     "ms_tune_install", "ms_tune_table", "resolve", "resolve_batch",
 ]
@@ -77,7 +77,11 @@ class MsTuneEntry(ctypes.Structure):
 
 class MsError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what} failed: {ms_status_string(status)} ({status})")
+        detail = ""
+        if status == MS_ERR_CUDA:
+            code, text = ms_last_cuda_error()
+            detail = f": CUDA error {code} ({text})"
+        super().__init__(f"{what} failed: {ms_status_string(status)} ({status}){detail}")
         self.status = status
 
 
@@ -146,6 +150,10 @@ def lib() -> ctypes.CDLL:
         L.ms_status_string.restype = ctypes.c_char_p
         L.ms_version.argtypes = []
         L.ms_version.restype = ctypes.c_char_p
+        L.ms_last_cuda_error.argtypes = []
+        L.ms_last_cuda_error.restype = i32
+        L.ms_last_cuda_error_string.argtypes = []
+        L.ms_last_cuda_error_string.restype = ctypes.c_char_p
         _lib = L
         return L
 
@@ -292,6 +300,11 @@ def ms_status_string(st: int) -> str:
 
 def ms_version() -> str:
     return lib().ms_version().decode()
+
+
+def ms_last_cuda_error() -> tuple[int, str]:
+    """The CUDA error behind this thread's last MS_ERR_CUDA (code, description)."""
+    return int(lib().ms_last_cuda_error()), lib().ms_last_cuda_error_string().decode()
 
 
 # ------------------------------------------------------------------ torch conveniences -------

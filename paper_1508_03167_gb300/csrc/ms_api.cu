@@ -311,6 +311,16 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
 
 using msk::Plan;
 
+namespace {
+// CUDA error behind the calling thread's last MS_ERR_CUDA (ms_last_cuda_error)
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+bool failed(cudaError_t e) {
+  if (e == cudaSuccess) return false;
+  g_last_cuda_error = e;
+  return true;
+}
+}  // namespace
+
 namespace msk {
 // autotuner lookup (ms_tune.cu): B = 0 resolved from the tuning table
 ms_params resolve_single(uint64_t n, uint32_t w, const ms_params *p);
@@ -344,9 +354,9 @@ class EventProfiler final : public msk::Prof {
     for (int k = 0; k < msk::kKindNum; ++k)
       std::strncpy(out->names[k], kKindNames[k], sizeof out->names[k] - 1);
     for (const Rec &r : recs_) {
-      if (cudaEventSynchronize(r.b) != cudaSuccess) return MS_ERR_CUDA;
+      if (failed(cudaEventSynchronize(r.b))) return MS_ERR_CUDA;
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return MS_ERR_CUDA;
+      if (failed(cudaEventElapsedTime(&ms, r.a, r.b))) return MS_ERR_CUDA;
       out->launches[r.kind] += 1;
       out->ms[r.kind] += ms;
     }
@@ -435,7 +445,7 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
   static PlanStream pool[64];
   static uint32_t used = 0;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return MS_ERR_CUDA;
+  if (failed(cudaGetDevice(&dev))) return MS_ERR_CUDA;
   std::lock_guard<std::mutex> g(mu);
   for (uint32_t i = 0; i < used; ++i)
     if (pool[i].dev == dev && pool[i].caller == caller) {
@@ -448,15 +458,15 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
   }
   PlanStream &S = pool[used];
   int lo = 0, hi = 0;
-  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return MS_ERR_CUDA;
-  if (cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, hi) != cudaSuccess)
+  if (failed(cudaDeviceGetStreamPriorityRange(&lo, &hi))) return MS_ERR_CUDA;
+  if (failed(cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, hi)))
     return MS_ERR_CUDA;
   for (int k = 0; k < 2; ++k) {
-    if (cudaEventCreateWithFlags(&S.planned[k], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&S.released[k], cudaEventDisableTiming) != cudaSuccess)
+    if (failed(cudaEventCreateWithFlags(&S.planned[k], cudaEventDisableTiming)) ||
+        failed(cudaEventCreateWithFlags(&S.released[k], cudaEventDisableTiming)))
       return MS_ERR_CUDA;
   }
-  if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess)
+  if (failed(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming)))
     return MS_ERR_CUDA;
   S.dev = dev;
   S.caller = caller;
@@ -473,10 +483,10 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   if (n <= 1) {
     if (perm && n == 1) {
       const uint32_t zero = 0;
-      if (cudaMemcpyAsync(data, &zero, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      if (failed(cudaMemcpyAsync(data, &zero, 4, cudaMemcpyHostToDevice, s)))
         return MS_ERR_CUDA;
       // the source lives on this stack frame: wait until the copy has consumed it
-      if (cudaStreamSynchronize(s) != cudaSuccess) return MS_ERR_CUDA;
+      if (failed(cudaStreamSynchronize(s))) return MS_ERR_CUDA;
     }
     return MS_OK;
   }
@@ -514,29 +524,28 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
     unit_sets(u, &b1, &b2);
     const msk::LevelPlan &lv = p.levels[unit_level[u]];
     if (lv.pair == 1)
-      return msk::launch_pair_plan(p, lv, p.levels[unit_level[u] + 1], b1, b2, seed, st) ==
-             cudaSuccess;
-    return msk::launch_level_plan(p, lv, b1, seed, st) == cudaSuccess;
+      return !failed(
+          msk::launch_pair_plan(p, lv, p.levels[unit_level[u] + 1], b1, b2, seed, st));
+    return !failed(msk::launch_level_plan(p, lv, b1, seed, st));
   };
   auto plan_on_side = [&](uint32_t u) -> bool {
     const uint32_t k = u % 2;
-    if (u >= slots && cudaStreamWaitEvent(P->side, P->released[k], 0) != cudaSuccess)
-      return false;
+    if (u >= slots && failed(cudaStreamWaitEvent(P->side, P->released[k], 0))) return false;
     if (!launch_unit_plan(u, P->side)) return false;
-    return cudaEventRecord(P->planned[k], P->side) == cudaSuccess;
+    return !failed(cudaEventRecord(P->planned[k], P->side));
   };
   std::unique_lock<std::mutex> pipe_lock;
   if (P) {
     pipe_lock = std::unique_lock<std::mutex>(P->mu);
     // the side stream starts after everything already on the caller's stream (earlier calls
     // may still be reading the plan sets)
-    if (cudaEventRecord(P->fork, s) != cudaSuccess) return MS_ERR_CUDA;
-    if (cudaStreamWaitEvent(P->side, P->fork, 0) != cudaSuccess) return MS_ERR_CUDA;
+    if (failed(cudaEventRecord(P->fork, s))) return MS_ERR_CUDA;
+    if (failed(cudaStreamWaitEvent(P->side, P->fork, 0))) return MS_ERR_CUDA;
     for (uint32_t u = 0; u < nu && u < slots; ++u)
       if (!plan_on_side(u)) return MS_ERR_CUDA;
   }
   void *cur = (p.hbm_passes % 2 == 0) ? data : b0.other;
-  if (msk::launch_leaf(p, data, cur, perm, seed, s) != cudaSuccess) return MS_ERR_CUDA;
+  if (failed(msk::launch_leaf(p, data, cur, perm, seed, s))) return MS_ERR_CUDA;
   uint32_t u = 0;  // next global unit
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     const msk::LevelPlan &lv = p.levels[i];
@@ -553,19 +562,19 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
       msk::Buffers b1, b2;
       unit_sets(u, &b1, &b2);
       if (P) {
-        if (cudaStreamWaitEvent(s, P->planned[u % 2], 0) != cudaSuccess) return MS_ERR_CUDA;
+        if (failed(cudaStreamWaitEvent(s, P->planned[u % 2], 0))) return MS_ERR_CUDA;
       } else if (!launch_unit_plan(u, s)) {
         return MS_ERR_CUDA;
       }
       e = lv.pair == 1 ? msk::launch_pair_data(p, lv, p.levels[i + 1], cur, dst, b1, b2, seed, s)
                        : msk::launch_level_data(p, lv, cur, dst, b1, seed, s);
       if (e == cudaSuccess && P) {
-        if (cudaEventRecord(P->released[u % 2], s) != cudaSuccess) return MS_ERR_CUDA;
+        if (failed(cudaEventRecord(P->released[u % 2], s))) return MS_ERR_CUDA;
         if (u + slots < nu && !plan_on_side(u + slots)) return MS_ERR_CUDA;
       }
       ++u;
     }
-    if (e != cudaSuccess) return MS_ERR_CUDA;
+    if (failed(e)) return MS_ERR_CUDA;
     cur = dst;
   }
   return MS_OK;
@@ -660,17 +669,17 @@ ms_status side_streams(SideStreams **out) {
   static std::mutex mu;
   static SideStreams per_dev[64];
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MS_ERR_CUDA;
+  if (failed(cudaGetDevice(&dev)) || dev < 0 || dev >= 64) return MS_ERR_CUDA;
   std::lock_guard<std::mutex> g(mu);
   SideStreams &S = per_dev[dev];
   if (!S.ready) {
     for (uint32_t i = 0; i < kBatchSideStreams; ++i) {
-      if (cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking) != cudaSuccess)
+      if (failed(cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking)))
         return MS_ERR_CUDA;
-      if (cudaEventCreateWithFlags(&S.join[i], cudaEventDisableTiming) != cudaSuccess)
+      if (failed(cudaEventCreateWithFlags(&S.join[i], cudaEventDisableTiming)))
         return MS_ERR_CUDA;
     }
-    if (cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming) != cudaSuccess)
+    if (failed(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming)))
       return MS_ERR_CUDA;
     S.ready = true;
   }
@@ -728,8 +737,8 @@ ms_status ms_batch_prepare(uint32_t k, void *const *h_ptrs, const uint64_t *h_n,
     e.pad = 0;
   }
   // pageable source: the copy has consumed it when the call returns
-  if (cudaMemcpyAsync(base + L.off_table, table.data(), table.size() * sizeof(BatchInstHost),
-                      cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+  if (failed(cudaMemcpyAsync(base + L.off_table, table.data(), table.size() * sizeof(BatchInstHost),
+                      cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream))))
     return MS_ERR_CUDA;
   return MS_OK;
 }
@@ -752,16 +761,16 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
     prof = &profiler();
   }
   if (!L.order.empty()) {
-    if (msk::launch_engine(w, perm, base + L.off_table, static_cast<uint32_t>(L.order.size()),
+    if (failed(msk::launch_engine(w, perm, base + L.off_table, static_cast<uint32_t>(L.order.size()),
                            reinterpret_cast<uint32_t *>(base + L.off_queue), r.B,
                            base + L.off_scratch, L.scratch_per_cta, msk::kEngineKcap,
                            msk::kEngineHbits, kEngineGrid, msk::kEngineSmem, s,
-                           prof) != cudaSuccess)
+                           prof)))
       return MS_ERR_CUDA;
   }
   if (prof_lock.owns_lock()) prof_lock.unlock();
   for (uint32_t i = 0; i < k; ++i) {
-    if (perm && h_n[i] == 1 && cudaMemsetAsync(h_ptrs[i], 0, 4, s) != cudaSuccess)
+    if (perm && h_n[i] == 1 && failed(cudaMemsetAsync(h_ptrs[i], 0, 4, s)))
       return MS_ERR_CUDA;
   }
   if (L.large.empty()) return MS_OK;
@@ -777,9 +786,9 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
   // several large instances: fork onto side streams, one workspace each, join back
   SideStreams *S = nullptr;
   if (side_streams(&S) != MS_OK) return MS_ERR_CUDA;
-  if (cudaEventRecord(S->fork, s) != cudaSuccess) return MS_ERR_CUDA;
+  if (failed(cudaEventRecord(S->fork, s))) return MS_ERR_CUDA;
   for (uint32_t j = 0; j < L.large_streams; ++j)
-    if (cudaStreamWaitEvent(S->s[j], S->fork, 0) != cudaSuccess) return MS_ERR_CUDA;
+    if (failed(cudaStreamWaitEvent(S->s[j], S->fork, 0))) return MS_ERR_CUDA;
   for (size_t t = 0; t < L.large.size(); ++t) {
     const uint32_t i = L.large[t];
     const uint32_t j = static_cast<uint32_t>(t % L.large_streams);
@@ -789,8 +798,8 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
     if (rs != MS_OK) return rs;
   }
   for (uint32_t j = 0; j < L.large_streams; ++j) {
-    if (cudaEventRecord(S->join[j], S->s[j]) != cudaSuccess) return MS_ERR_CUDA;
-    if (cudaStreamWaitEvent(s, S->join[j], 0) != cudaSuccess) return MS_ERR_CUDA;
+    if (failed(cudaEventRecord(S->join[j], S->s[j]))) return MS_ERR_CUDA;
+    if (failed(cudaStreamWaitEvent(s, S->join[j], 0))) return MS_ERR_CUDA;
   }
   return MS_OK;
 }
@@ -885,13 +894,13 @@ static ms_status host_form(void *h, bool perm, uint64_t n, uint32_t w, uint64_t 
   const size_t front = msk::round_up(n * w, 256);
   void *d_buf = d_ws;
   void *inner = static_cast<char *>(d_ws) + front;
-  if (!perm && cudaMemcpyAsync(d_buf, h, n * w, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (!perm && failed(cudaMemcpyAsync(d_buf, h, n * w, cudaMemcpyHostToDevice, s)))
     return MS_ERR_CUDA;
   const ms_status st = run(d_buf, perm, n, w, seed, inner, ws_bytes - front, params, s);
   if (st != MS_OK) return st;
-  if (cudaMemcpyAsync(h, d_buf, n * w, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (failed(cudaMemcpyAsync(h, d_buf, n * w, cudaMemcpyDeviceToHost, s)))
     return MS_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return MS_ERR_CUDA;
+  if (failed(cudaStreamSynchronize(s))) return MS_ERR_CUDA;
   return MS_OK;
 }
 
@@ -918,6 +927,10 @@ const char *ms_status_string(ms_status s) {
   }
   return "MS_ERR_UNKNOWN";
 }
+
+int ms_last_cuda_error(void) { return static_cast<int>(g_last_cuda_error); }
+
+const char *ms_last_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda_error); }
 
 const char *ms_version(void) { return "mergeshuffle-gb300 0.1 (MS-Philox v1, sm_103a)"; }
 

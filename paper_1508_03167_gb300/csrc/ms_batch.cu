@@ -519,8 +519,7 @@ cudaError_t launch_engine(uint32_t w, bool perm, const void *inst, uint32_t k, u
   cudaError_t err = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
   if (err != cudaSuccess) return err;
   auto launch = [&](auto kern) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
     if (prof) prof->begin(kKindEngine, s);
     kern<<<grid, kEngThreads, smem, s>>>(g);

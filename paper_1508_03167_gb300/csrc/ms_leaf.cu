@@ -301,8 +301,7 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
     auto fk = fy_index_kernel<E>;
     const uint32_t per = 32;
     const size_t smem = static_cast<size_t>(per) * p.leaf_stride * sizeof(uint32_t);
-    cudaError_t e2 = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(smem));
+    cudaError_t e2 = allow_dynamic_smem(fk, smem);
     if (e2 != cudaSuccess) return e2;
     const uint64_t groups = (p.q + per - 1) / per;
     const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
@@ -317,8 +316,7 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
     const uint64_t fit = (96ull * 1024) / (static_cast<uint64_t>(p.leaf_stride) * 2u);
     const uint32_t per = static_cast<uint32_t>(fit < 1 ? 1 : (fit > 32 ? 32 : fit));
     const size_t smem = (static_cast<size_t>(per) * p.leaf_stride * sizeof(uint16_t) + 15) & ~15ull;
-    cudaError_t e2 = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(smem));
+    cudaError_t e2 = allow_dynamic_smem(fk, smem);
     if (e2 != cudaSuccess) return e2;
     const uint64_t groups = (p.q + per - 1) / per;
     const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
@@ -330,8 +328,7 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
   if (p.d == 0 && p.fy_per_cta > 0) {
     auto fk = fy_kernel<E, kPerm>;
     const size_t smem = static_cast<size_t>(p.fy_per_cta) * p.leaf_stride * sizeof(E);
-    cudaError_t e2 = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(smem));
+    cudaError_t e2 = allow_dynamic_smem(fk, smem);
     if (e2 != cudaSuccess) return e2;
     const uint64_t groups = (p.q + p.fy_per_cta - 1) / p.fy_per_cta;
     const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
@@ -341,8 +338,7 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
     return cudaGetLastError();
   }
   auto kern = leaf_kernel<E, kPerm>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(p.leaf_smem));
+  cudaError_t err = allow_dynamic_smem(kern, p.leaf_smem);
   if (err != cudaSuccess) return err;
   const uint64_t grid = p.tiles < 1048576ull ? p.tiles : 1048576ull;
   if (p.prof) p.prof->begin(kKindLeaf, s);
@@ -409,8 +405,7 @@ cudaError_t launch_local_t(const Plan &p, const LevelPlan &lv, const void *in, v
   a.tcap_c = lv.tcap;
   a.aux_w = lv.warp_bytes;
   auto kern = local_level_kernel<E>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(lv.smem));
+  cudaError_t err = allow_dynamic_smem(kern, lv.smem);
   if (err != cudaSuccess) return err;
   const uint64_t spans = p.q >> (lv.mlog + lv.level + 1u);
   const uint64_t grid = spans < 1048576ull ? spans : 1048576ull;

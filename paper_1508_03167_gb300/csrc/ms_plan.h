@@ -135,6 +135,29 @@ struct Buffers {
   void *ptmp;
 };
 
+// Lets `kern` launch with `smem` bytes of dynamic shared memory. The attribute is process-wide,
+// so every caller sets the same value (the device's opt-in maximum less the kernel's static
+// shared memory): threads launching the same kernel with different sizes never lower it under
+// each other. The launch's own size still decides the occupancy.
+template <typename K>
+cudaError_t allow_dynamic_smem(K kern, size_t smem) {
+  int dev = 0, mx = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  // the kernel's static shared memory comes out of the same opt-in budget
+  const size_t room = static_cast<size_t>(mx) > fa.sharedSizeBytes
+                          ? static_cast<size_t>(mx) - fa.sharedSizeBytes
+                          : 0;
+  if (smem > room) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(room));
+}
+
 // Kernel launchers (ms_leaf.cu, ms_level.cu). Return the launch error (cudaSuccess if none).
 cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s);

@@ -435,8 +435,7 @@ cudaError_t launch_t(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.tcap = lv.tcap;
   a.flags = p.flags;
   auto kern = span_level_kernel<E, kThreads>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(lv.smem));
+  cudaError_t err = allow_dynamic_smem(kern, lv.smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, lv.smem);

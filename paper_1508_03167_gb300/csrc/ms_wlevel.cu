@@ -315,8 +315,7 @@ cudaError_t launch_t(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.warp_bytes = lv.warp_bytes;
   auto kern = warp_stream_level_kernel<E>;
   const size_t smem = static_cast<size_t>(lv.warp_bytes) * kWlWarps;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+  cudaError_t err = allow_dynamic_smem(kern, smem);
   if (err != cudaSuccess) return err;
   const uint64_t spans = p.q >> (lv.mlog + lv.level + 1u);
   const uint64_t blocks = (spans + kWlWarps - 1) / kWlWarps;

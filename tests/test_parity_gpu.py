@@ -215,3 +215,46 @@ def test_concurrent_calls_on_two_streams_from_two_threads():
     for i, (n, seed, B) in enumerate(jobs):
         want, _ = oracle.perm(n, seed, B)
         assert np.array_equal(outs[i], want), i
+
+
+def test_single_call_replays_from_a_cuda_graph():
+    """ms_perm and ms_shuffle (global levels, their plans on the paired stream, fused pairs for
+    records) captured into one CUDA graph after an eager call on the same stream; replays give
+    the oracle's results."""
+    torch = _torch()
+    n, B = (1 << 20) + 3, 128
+    rec = inputs.records16(300017)
+    p = ms.params(B=B, fuse_depth=0)
+    q = ms.params(B=B, fuse_depth=0, flags=ms.MS_FLAG_PAIR_LEVELS)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    x = torch.from_numpy(rec.view(np.uint8).reshape(rec.shape[0], 16).copy()).cuda()
+    x0 = x.clone()
+    ws1 = torch.empty(ms.ms_workspace_bytes(n, 4, p), dtype=torch.uint8, device="cuda")
+    ws2 = torch.empty(ms.ms_workspace_bytes(rec.shape[0], 16, q), dtype=torch.uint8,
+                      device="cuda")
+    s = torch.cuda.Stream()
+
+    def work():
+        assert ms.ms_perm(out.data_ptr(), n, 21, ws1.data_ptr(), ws1.numel(), p,
+                          s.cuda_stream) == ms.MS_OK
+        assert ms.ms_shuffle(x.data_ptr(), rec.shape[0], 16, 22, ws2.data_ptr(), ws2.numel(), q,
+                             s.cuda_stream) == ms.MS_OK
+
+    with torch.cuda.stream(s):
+        work()  # eager: creates the paired plan stream and sets kernel attributes
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    x.copy_(x0)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        work()
+    want_p, _ = oracle.perm(n, 21, B)
+    want_r, _ = oracle.shuffle(rec, 22, B)
+    for _ in range(2):
+        out.fill_(-1)
+        x.copy_(x0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), want_p)
+        assert np.array_equal(x.cpu().numpy().view(rec.dtype).reshape(rec.shape), want_r)
