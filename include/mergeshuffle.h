@@ -75,7 +75,10 @@ typedef void *ms_stream_t;
 #define MS_FLAG_CTA_LEVELS 0x8u      /* small merge levels finish per CTA rather than per warp
                                         (the result is identical) */
 #define MS_FLAG_PERM 0x10u           /* batch calls: fill every instance with its permutation of
-                                        0..n_i-1 instead of shuffling it (w must be 4) */
+                                        0..n_i-1 instead of shuffling it (w must be 4).
+                                        ms_plan_info: describe the plan of ms_perm rather than
+                                        ms_shuffle (ms_perm and ms_shuffle set or clear it
+                                        themselves) */
 #define MS_FLAG_WARP_LEVELS 0x40u    /* small merge levels run one warp per group of merges,
                                         global to global, instead of streamed spans (the
                                         result is identical) */
@@ -86,6 +89,9 @@ typedef void *ms_stream_t;
                                         every element width (by default only 16-byte elements,
                                         where the pass is bound by memory rather than by its
                                         instructions; the result is identical) */
+#define MS_FLAG_CTA_TILES 0x200u     /* fused merge levels (fuse_depth > 0) run on the CTA-wide
+                                        base-block kernel rather than the one-warp tile kernel
+                                        on 16-bit indices (the result is identical) */
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level

@@ -78,6 +78,51 @@ bool leaf_fits(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
   return L.bytes <= kSmemLimit && L.tile_max < 65536 && d - L.dw <= 3;
 }
 
+// Shared-memory layout of the tile kernel (16-bit tile-local indices, two warps a tile): two
+// buffers (the first holds block k at k*P, P = 2 mod 64 and at least the largest block; merge r
+// of level l writes at r*S[l]), then two sets of a level's (coin word, zero prefix) pairs and
+// two sets of its tail draws (which also hold the per-thread queues of second-word
+// Fisher-Yates draws: 64 threads x 16 entries x 4 bytes over both sets).
+struct TileSmem {
+  bool ok = false;
+  uint32_t P = 0, buf = 0, wcap = 0, tcap = 0;
+  uint32_t S[kTileMaxDepth] = {};
+  size_t bytes = 0;
+};
+
+TileSmem tile_smem(uint64_t n, uint32_t c, uint32_t d) {
+  TileSmem T;
+  if (d == 0 || d > kTileMaxDepth || d > c) return T;
+  const uint64_t tile_max = ceil_scaled(n, d, c);
+  if (tile_max >= 65536) return T;
+  const uint32_t lmax = static_cast<uint32_t>(ceil_scaled(n, 0, c));
+  uint32_t P = lmax;
+  while (P % 64u != 2u) ++P;
+  uint64_t buf = (1ull << d) * P;
+  uint64_t wcap = 4, tcap = 1024;  // (two sets of tail draws hold the 4 KiB of queues)
+  for (uint32_t l = 0; l < d; ++l) {
+    const uint64_t R = 1ull << (d - l - 1);
+    const uint64_t Nmax = ceil_scaled(n, l + 1, c);
+    const uint64_t S = (Nmax + 7) & ~7ull;
+    T.S[l] = static_cast<uint32_t>(S);
+    buf = std::max(buf, R * S);
+    wcap = std::max(wcap, R * (Nmax / 32 + 1));
+    // tail draws made ahead: the mean sum over the level's merges plus 4.8 spreads
+    const double per = std::sqrt(2.0 * static_cast<double>(Nmax) / 3.14159265358979) + 2.0;
+    double tc = static_cast<double>(R) * per +
+                4.8 * std::sqrt(static_cast<double>(R) * static_cast<double>(Nmax)) + 64.0;
+    tc = std::min(tc, static_cast<double>(R * Nmax));
+    tcap = std::max<uint64_t>(tcap, static_cast<uint64_t>(tc));
+  }
+  T.P = P;
+  T.buf = static_cast<uint32_t>((buf + 7) & ~7ull);
+  T.wcap = static_cast<uint32_t>((wcap + 1) & ~1ull);
+  T.tcap = static_cast<uint32_t>((tcap + 7) & ~7ull);
+  T.bytes = 4ull * T.buf + 2ull * (8ull * T.wcap + 2ull * T.tcap);
+  T.ok = T.bytes <= kSmemLimit;
+  return T;
+}
+
 }  // namespace
 
 int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t tile_bytes,
@@ -109,9 +154,21 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       if (ceil_scaled(n, t, c) * w <= tile_bytes && leaf_fits(n, c, t, w)) d = t;
   } else {
     d = static_cast<uint32_t>(fuse_depth) < dmax ? static_cast<uint32_t>(fuse_depth) : dmax;
-    while (d > 0 && !leaf_fits(n, c, d, w)) --d;
+    while (d > 0 && !leaf_fits(n, c, d, w) &&
+           ((flags & MS_FLAG_CTA_TILES) || !tile_smem(n, c, d).ok))
+      --d;
   }
   p.d = d;
+  const TileSmem TS = tile_smem(n, c, d);
+  p.tile_mode = TS.ok && !(flags & MS_FLAG_CTA_TILES);
+  if (p.tile_mode) {
+    p.tile_P = TS.P;
+    p.tile_buf = TS.buf;
+    p.tile_wcap = TS.wcap;
+    p.tile_tcap = TS.tcap;
+    for (uint32_t l = 0; l < kTileMaxDepth; ++l) p.tile_S[l] = TS.S[l];
+    p.tile_smem = TS.bytes;
+  }
   p.tiles = p.q >> d;
   p.tile_max = static_cast<uint32_t>(ceil_scaled(n, d, c));
   const LeafSmem L = leaf_smem(n, c, d, w);
@@ -133,7 +190,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     if (per < 1) per = 1;
     p.fy_per_cta = static_cast<uint32_t>(per);
   }
-  if (p.leaf_smem > kSmemLimit) return 2;
+  if (!p.tile_mode && p.leaf_smem > kSmemLimit) return 2;
 
   // HBM levels d..c-1
   p.nlevels = c - d;
@@ -265,6 +322,25 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       while ((1ull << xb) < 4ull * lv.kcap) ++xb;
       lv.xhbits = xb;
       xhbits_max = std::max(xhbits_max, xb);
+    }
+  }
+  // The tile kernel of a shuffle reads its input rows after computing their order, so its
+  // pass must not be in place: the passes after it must be odd in number (the last lands in
+  // the caller's array). Split the last fused pair, else fuse one level less. (A perm reads
+  // nothing.)
+  if (p.tile_mode && !(flags & MS_FLAG_PERM) && (nlocal + units) % 2 == 0) {
+    int last = -1;
+    for (uint32_t i = 0; i < p.nlevels; ++i)
+      if (p.levels[i].pair == 1) last = static_cast<int>(i);
+    if (last >= 0) {
+      p.levels[last].pair = 0;
+      p.levels[last].xhbits = 0;
+      p.levels[last + 1].pair = 0;
+      ++units;
+      xhbits_max = 0;
+      for (uint32_t i = 0; i < p.nlevels; ++i) xhbits_max = std::max(xhbits_max, p.levels[i].xhbits);
+    } else if (d > 0) {
+      return make_plan(n, w, B, static_cast<int32_t>(d - 1), tile_bytes, flags, out);
     }
   }
   p.units = units;
@@ -478,7 +554,12 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
 ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
               size_t ws_bytes, const ms_params *params, cudaStream_t s) {
   Plan p;
-  const ms_status st = plan_for(n, w, params, &p);
+  ms_params pp;
+  ms_default_params(&pp);
+  if (params) pp = *params;
+  if (perm) pp.flags |= MS_FLAG_PERM;
+  else pp.flags &= ~MS_FLAG_PERM;
+  const ms_status st = plan_for(n, w, &pp, &p);
   if (st != MS_OK) return st;
   if (n <= 1) {
     if (perm && n == 1) {
@@ -863,9 +944,21 @@ ms_status ms_profile_read(ms_profile *out, int reset) {
 }
 
 size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *params) {
+  // enough for ms_shuffle and (w = 4) ms_perm, whose plans may differ in how the levels after
+  // the base-block pass are grouped
+  ms_params pp;
+  ms_default_params(&pp);
+  if (params) pp = *params;
   Plan p;
-  if (plan_for(n, w, params, &p) != MS_OK) return 0;
-  return p.ws_bytes;
+  pp.flags &= ~MS_FLAG_PERM;
+  if (plan_for(n, w, &pp, &p) != MS_OK) return 0;
+  size_t ws = p.ws_bytes;
+  if (w == 4) {
+    pp.flags |= MS_FLAG_PERM;
+    if (plan_for(n, w, &pp, &p) != MS_OK) return 0;
+    ws = std::max(ws, p.ws_bytes);
+  }
+  return ws;
 }
 
 ms_status ms_shuffle(void *d_data, uint64_t n, uint32_t w, uint64_t seed, void *d_ws,

@@ -429,6 +429,7 @@ cudaError_t launch_local_level(const Plan &p, const LevelPlan &lv, const void *i
 
 cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s) {
+  if (p.tile_mode) return launch_tile(p, in, out, perm, seed, s);
   if (perm) return launch_leaf_t<uint32_t, true>(p, in, out, seed, s);
   switch (p.w) {
     case 4: return launch_leaf_t<uint32_t, false>(p, in, out, seed, s);

@@ -129,6 +129,35 @@ __device__ __forceinline__ uint32_t draw_with_word0_flat(uint2 key, uint32_t tag
   return 0u;
 }
 
+// The same draw from word 0 without the reciprocal: slice u = 1, 2, 3 exists for b <= 16, 10,
+// 8 (floor(32/b) > u), so the first four slices need no division; the rest of the word (b <= 6)
+// is tested in a loop. False if the whole word rejects.
+__device__ __forceinline__ bool draw_first_word(uint32_t word, uint32_t R, uint32_t &x) {
+  const uint32_t b = 32u - __clz(R - 1u);
+  const uint32_t mask = 0xFFFFFFFFu >> (32u - b);
+  const uint32_t v0 = word & mask;
+  const uint32_t v1 = __funnelshift_rc(word, 0u, b) & mask;
+  const uint32_t v2 = __funnelshift_rc(word, 0u, 2u * b) & mask;
+  const uint32_t v3 = __funnelshift_rc(word, 0u, 3u * b) & mask;
+  const bool a0 = v0 < R;
+  const bool a1 = b <= 16u && v1 < R;
+  const bool a2 = b <= 10u && v2 < R;
+  const bool a3 = b <= 8u && v3 < R;
+  x = a0 ? v0 : (a1 ? v1 : (a2 ? v2 : v3));
+  if (a0 | a1 | a2 | a3) return true;
+  if (b <= 6u) {
+    const uint32_t slices = 32u / b;
+    for (uint32_t u = 4; u < slices; ++u) {
+      const uint32_t v = (word >> (u * b)) & mask;
+      if (v < R) {
+        x = v;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
 // Algorithm 1 (descending Fisher-Yates) on one base block of L elements in shared memory:
 // for i = L-1 .. 1, swap blk[i] with blk[j], j uniform in {0..i} from the LEAF stream of block
 // `id` at position i. Positions go in quads (one Philox block serves four of them), and the

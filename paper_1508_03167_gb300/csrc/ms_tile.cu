@@ -1,0 +1,437 @@
+// ms_tile.cu -- the base blocks of a tile of 2^d consecutive base blocks and the tile's first d
+// merge levels (Algorithms 1 to 3 of arXiv 1508.03167), one warp per tile, computed on 16-bit
+// tile-local indices in shared memory; the tile is then written once (perm: the indices plus
+// the tile's first element; shuffle: the input rows they name).
+//
+// Per tile:
+//   * Algorithm 1's draws for every position of every base block (lane k: block k). A draw
+//     whose first Philox word rejects all its slices is queued by its lane and finished after
+//     the loop, so no lane holds the warp up with a second Philox block inline;
+//   * Algorithm 1's swap chain per block, reading those draws;
+//   * per merge level: coin words and their zero prefix, the break step T of every merge,
+//     the stable interleave (a lane places eight consecutive positions, walking the two
+//     halves with one index each), the tail draws, and the random insertions of Algorithm 3's
+//     second loop in order, one lane per merge;
+//   * one store of the tile.
+// Block k of the tile sits at k*P in the first buffer (P = 2 mod 64, so the 32 lanes at one
+// position of their blocks touch 32 different banks); merge r of level l writes its output at
+// r*S[l] (S[l] a multiple of eight: a lane stores its eight 16-bit results in one 16-byte store).
+// The shared-memory reads of the interleave are clamped to the buffers, so an inconsistent
+// plan fails the parity tests instead of reading outside shared memory.
+#include "ms_merge.cuh"
+
+namespace msk {
+namespace {
+
+constexpr uint32_t kFailPerLane = 16;  // queued second-word draws per lane and block group
+
+struct TileArgs {
+  const void *in;
+  void *out;
+  uint64_t n;
+  uint2 key;
+  uint32_t c, d;
+  uint32_t P;     // stride of a base block in the Fisher-Yates layout
+  uint32_t buf;   // 16-bit entries of each tile buffer (a multiple of eight)
+  uint32_t wcap;  // coin words of one level
+  uint32_t tcap;  // tail draws of one level made ahead of the data (else drawn in the loop)
+  uint32_t S[kTileMaxDepth];  // output stride of one merge of level l
+};
+
+__device__ __forceinline__ uint32_t warp_exclusive(uint32_t v, uint32_t *total) {
+  const uint32_t incl = warp_inclusive_scan(v);
+  *total = __shfl_sync(kFullMask, incl, 31);
+  return incl - v;
+}
+
+// Control data of one merge level (two sets: the control warp builds level l+1's while the
+// data warp finishes level l): (coin word, zero prefix) pairs, tail draws, and per merge its
+// size, break step, half bases, leftover base, first word and first tail draw.
+struct LevelCtl {
+  uint2 *cz;
+  uint16_t *mv;
+  uint32_t *m;  // kTileCtlWords words: 7 arrays of 32 and the flag "tail draws made"
+};
+constexpr uint32_t kTileCtlWords = 7u * 32u + 1u;
+__device__ __forceinline__ uint32_t *ctl_N(const LevelCtl &c) { return c.m; }
+__device__ __forceinline__ uint32_t *ctl_T(const LevelCtl &c) { return c.m + 32; }
+__device__ __forceinline__ uint32_t *ctl_a(const LevelCtl &c) { return c.m + 64; }
+__device__ __forceinline__ uint32_t *ctl_b(const LevelCtl &c) { return c.m + 96; }
+__device__ __forceinline__ uint32_t *ctl_lb(const LevelCtl &c) { return c.m + 128; }
+__device__ __forceinline__ uint32_t *ctl_woff(const LevelCtl &c) { return c.m + 160; }
+__device__ __forceinline__ uint32_t *ctl_koff(const LevelCtl &c) { return c.m + 192; }
+__device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m + 224; }
+
+// The data-independent part of merge level lv of the tile, by one warp: coin words, zero
+// prefixes and break step of every merge, the leftover base, and the tail draws. G = 32 / R
+// lanes per merge: lane (r, sub) = (lane / G, lane % G).
+__device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *boff, uint64_t k0,
+                                            uint32_t lv, uint32_t Sin, uint32_t lane,
+                                            const LevelCtl &c) {
+  const uint32_t idbase = static_cast<uint32_t>(k0 >> (lv + 1u));
+  const uint32_t lgG = 5u - (a.d - lv - 1u);  // (R = 2^(d-lv-1) <= 32)
+  const uint32_t G = 1u << lgG;
+  const uint32_t r = lane >> lgG;
+  const uint32_t sub = lane & (G - 1u);
+  const uint32_t leader = lane & ~(G - 1u);
+  const uint32_t kb = (2u * r) << lv;
+  const uint32_t n1 = boff[kb + (1u << lv)] - boff[kb];
+  const uint32_t N = boff[kb + (2u << lv)] - boff[kb];
+  const uint32_t Wm = (N >> 5) + 1u;  // coin words for steps 0..N (the break step is <= N)
+  uint32_t Wtot;
+  const uint32_t woff = __shfl_sync(kFullMask, warp_exclusive(sub == 0u ? Wm : 0u, &Wtot), leader);
+  uint2 *const cz = c.cz + woff;
+  // coin words (one Philox block: four words, 128 steps)
+  const uint32_t nblk = (Wm + 3u) >> 2;
+  for (uint32_t jb = sub; jb < nblk; jb += G) {
+    const uint4 blk = coin_block(a.key, lv, idbase + r, jb);
+    const uint32_t j = 4u * jb;
+    cz[j].x = blk.x;
+    if (j + 1u < Wm) cz[j + 1u].x = blk.y;
+    if (j + 2u < Wm) cz[j + 2u].x = blk.z;
+    if (j + 3u < Wm) cz[j + 3u].x = blk.w;
+  }
+  __syncwarp();
+  // zeros before each word of the merge: lane (r, sub) takes a run of C words, then a scan over
+  // the merge's G lanes; the same pass finds the break step, the (n1+1)-th zero or the
+  // (n2+1)-th one, whichever comes first
+  const uint32_t C = (Wm + G - 1u) >> lgG;
+  const uint32_t j0 = min(sub * C, Wm), j1 = min(j0 + C, Wm);
+  uint32_t zrun = 0;
+  for (uint32_t j = j0; j < j1; ++j) zrun += static_cast<uint32_t>(__popc(~cz[j].x));
+  uint32_t Zs = zrun;
+#pragma unroll
+  for (uint32_t o = 1; o < 32u; o <<= 1) {
+    const uint32_t up = __shfl_up_sync(kFullMask, Zs, o, G);
+    if (o < G && sub >= o) Zs += up;
+  }
+  Zs -= zrun;  // zeros before word j0
+  const uint32_t n2 = N - n1;
+  uint32_t T = N;
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint32_t w = cz[j].x;
+    cz[j].y = Zs;
+    const uint32_t Os = 32u * j - Zs;
+    const uint32_t zeros = static_cast<uint32_t>(__popc(~w));
+    if (Zs <= n1 && n1 < Zs + zeros) T = min(T, 32u * j + select_set_bit(~w, n1 - Zs));
+    if (Os <= n2 && n2 < Os + (32u - zeros)) T = min(T, 32u * j + select_set_bit(w, n2 - Os));
+    Zs += zeros;
+  }
+#pragma unroll
+  for (uint32_t o = 1; o < 32u; o <<= 1)
+    if (o < G) T = min(T, __shfl_xor_sync(kFullMask, T, o, G));
+  __syncwarp();
+  const uint32_t Ab = 2u * r * Sin;
+  const uint32_t Bb = Ab + Sin;
+  // positions t >= T take the rest of the half that did not run out, in order; the coin at T
+  // names the half that ran out (0: the first half, so t reads X[Bb + t - n1])
+  uint32_t lb = Ab - n2;
+  if (T < N && ((cz[T >> 5].x >> (T & 31u)) & 1u) == 0u) lb = Bb - n1;
+  const uint32_t K = N - T;
+  const uint32_t Q = K ? ((N - 1u) >> 2) - (T >> 2) + 1u : 0u;
+  uint32_t Ktot;
+  const uint32_t koff = __shfl_sync(kFullMask, warp_exclusive(sub == 0u ? K : 0u, &Ktot), leader);
+  if (sub == 0u) {
+    ctl_N(c)[r] = N;
+    ctl_T(c)[r] = T;
+    ctl_a(c)[r] = Ab;
+    ctl_b(c)[r] = Bb;
+    ctl_lb(c)[r] = lb;
+    ctl_woff(c)[r] = woff;
+    ctl_koff(c)[r] = koff;
+  }
+  const bool drawn = Ktot <= a.tcap;
+  if (lane == 0) *ctl_drawn(c) = drawn ? 1u : 0u;
+  // tail draws, one Philox block per four consecutive positions (lane (r, sub): quads sub,
+  // sub + G, ... of merge r's tail); else the tails draw in their loop
+  if (drawn) {
+    for (uint32_t gq = sub; gq < Q; gq += G) {
+      const uint32_t quad = (T >> 2) + gq;
+      const uint32_t id = idbase + r;
+      const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lv, 0u), a.key);
+#pragma unroll
+      for (uint32_t v = 0; v < 4u; ++v) {
+        const uint32_t i = 4u * quad + v;
+        if (i >= T && i < N) {
+          uint32_t x;
+          if (!draw_first_word(pick_word(w0, v), i + 1u, x))
+            x = draw_continue(a.key, kTagTail, lv, id, i, i + 1u);
+          c.mv[koff + (i - T)] = static_cast<uint16_t>(x);
+        }
+      }
+    }
+  }
+}
+
+// Two warps per tile. Both make the Fisher-Yates draws and the interleaves; the data warp runs
+// the serial parts (Algorithm 1's swaps, the merge tails) while the control warp builds the
+// next level's control data.
+template <typename E, bool kPerm>
+__global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t boff[(1u << kTileMaxDepth) + 1u];
+  __shared__ uint32_t ctlm[2][kTileCtlWords];
+  __shared__ uint32_t s_S[kTileMaxDepth];  // (a.S indexed by level, without a local copy)
+  uint16_t *const bufA = reinterpret_cast<uint16_t *>(smem_raw);
+  uint16_t *const bufB = bufA + a.buf;
+  uint2 *const cz0 = reinterpret_cast<uint2 *>(bufB + a.buf);
+  uint16_t *const mv0 = reinterpret_cast<uint16_t *>(cz0 + 2u * a.wcap);
+  auto ctl = [&](uint32_t set) {
+    LevelCtl c;
+    c.cz = cz0 + set * a.wcap;
+    c.mv = mv0 + set * a.tcap;
+    c.m = &ctlm[0][0] + set * kTileCtlWords;
+    return c;
+  };
+  // per-thread queues of second-word Fisher-Yates draws (aliased with the tail draws)
+  uint32_t *const flist = reinterpret_cast<uint32_t *>(mv0);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint32_t nb = 1u << a.d;
+  const uint64_t tiles = (1ull << a.c) >> a.d;
+  if (tid < kTileMaxDepth) {
+#pragma unroll
+    for (uint32_t l = 0; l < kTileMaxDepth; ++l)
+      if (tid == l) s_S[l] = a.S[l];
+  }
+  __syncthreads();
+
+  for (uint64_t tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const uint64_t k0 = tt << a.d;
+    const uint64_t g0 = boundary(a.n, a.c, k0);
+    for (uint32_t k = tid; k <= nb; k += 64u)
+      boff[k] = static_cast<uint32_t>(boundary(a.n, a.c, k0 + k) - g0);
+    __syncthreads();
+
+    // ---- Algorithm 1's draws (warp w: quads w, w+2, ... of every block; lane: the block)
+    for (uint32_t kg = 0; kg < nb; kg += 32u) {
+      const uint32_t k = kg + lane;
+      const bool act = k < nb;
+      const uint32_t off = act ? boff[k] : 0u;
+      const uint32_t L = act ? boff[k + 1u] - off : 0u;
+      uint16_t *const A = bufA + k * a.P;
+      uint16_t *const D = bufB + k * a.P;  // D[i]: the draw of position i
+      uint32_t *const F = flist + tid * kFailPerLane;
+      const uint32_t id = static_cast<uint32_t>(k0 + k);
+      const uint32_t nq = L ? ((L - 1u) >> 2) + 1u : 0u;
+      uint32_t nf = 0;
+#pragma unroll 2
+      for (uint32_t qd = warp; qd < nq; qd += 2u) {
+        const uint4 blk = philox10(make_uint4(qd, id, kTagLeaf << 16, 0u), a.key);
+#pragma unroll
+        for (uint32_t v = 0; v < 4u; ++v) {
+          const uint32_t pos = 4u * qd + v;
+          if (pos < L) {
+            A[pos] = static_cast<uint16_t>(off + pos);
+            if (pos >= 1u) {
+              uint32_t x;
+              if (draw_first_word(pick_word(blk, v), pos + 1u, x)) {
+                D[pos] = static_cast<uint16_t>(x);
+              } else if (nf < kFailPerLane) {
+                F[nf++] = pos;
+              } else {
+                D[pos] = static_cast<uint16_t>(
+                    draw_continue(a.key, kTagLeaf, 0u, id, pos, pos + 1u));
+              }
+            }
+          }
+        }
+      }
+      // draws whose first word rejected every slice: words 1, 2, ... of their streams
+      for (uint32_t e = 0; e < nf; ++e) {
+        const uint32_t pos = F[e];
+        D[pos] = static_cast<uint16_t>(draw_continue(a.key, kTagLeaf, 0u, id, pos, pos + 1u));
+      }
+    }
+    __syncthreads();
+
+    // The two roles swap from tile to tile (the warps of a CTA sit on different SM
+    // sub-partitions, which would otherwise carry unequal loads): the data warp runs the serial
+    // parts, the control warp builds the next level's control data meanwhile.
+    const uint32_t dw = static_cast<uint32_t>(tt & 1u);  // data warp of this tile
+    const uint32_t role = warp ^ dw;                     // 0: data, 1: control
+
+    // ---- Algorithm 1's swaps, i = L-1 .. 1 (role q: blocks 32q .. 32q+31; the draws are read
+    // four ahead of the chain and clamped to the block); the control warp then builds level 0's
+    for (uint32_t kg = 32u * role; kg < nb; kg += 64u) {
+      const uint32_t k = kg + lane;
+      const uint32_t L = k < nb ? boff[k + 1u] - boff[k] : 0u;
+      uint16_t *const A = bufA + k * a.P;
+      const uint16_t *const D = bufB + k * a.P;
+      uint32_t i = L;
+      while (i >= 5u) {
+        const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
+        const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
+        const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
+        const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
+        swap_smem(A, i - 1u, j0);
+        swap_smem(A, i - 2u, j1);
+        swap_smem(A, i - 3u, j2);
+        swap_smem(A, i - 4u, j3);
+        i -= 4u;
+      }
+      for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+    }
+    if (role == 1u) level_setup(a, boff, k0, 0u, a.P, lane, ctl(0u));
+    __syncthreads();
+
+    // ---- merge levels 0 .. d-1 of the tile (Algorithm 2)
+    for (uint32_t lv = 0; lv < a.d; ++lv) {
+      const uint16_t *const X = (lv & 1u) ? bufB : bufA;
+      uint16_t *const Y = (lv & 1u) ? bufA : bufB;
+      const uint32_t Sout = s_S[lv];
+      const uint32_t R = nb >> (lv + 1u);
+      const LevelCtl c = ctl(lv & 1u);
+      // stable interleave: thread places positions t .. t+7 of merge rr (both warps; which
+      // warp takes the upper 256 positions of each 512 alternates between merges)
+      for (uint32_t rr = 0; rr < R; ++rr) {
+        const uint32_t gi = 32u * (warp ^ (rr & 1u)) + lane;
+        const uint32_t Nr = ctl_N(c)[rr], Tr = ctl_T(c)[rr], ar = ctl_a(c)[rr],
+                       br = ctl_b(c)[rr], lbr = ctl_lb(c)[rr];
+        const uint2 *const czr = c.cz + ctl_woff(c)[rr];
+        uint16_t *const Yr = Y + rr * Sout;
+        for (uint32_t t0 = 0; t0 < Nr; t0 += 512u) {
+          const uint32_t t = t0 + 8u * gi;
+          if (t >= Nr) continue;
+          const uint2 wz = czr[t >> 5];
+          const uint32_t sh = t & 31u;
+          const uint32_t zz = wz.y + static_cast<uint32_t>(__popc(~wz.x & low_mask(sh)));
+          const uint32_t bits = wz.x >> sh;
+          // (reads past a clamped index stay inside shared memory: 8 entries at most)
+          uint32_t pa = min(ar + zz, a.buf);
+          uint32_t pb = min(br + t - zz, a.buf);
+          uint32_t v[8];
+          if (t + 8u <= Tr) {
+#pragma unroll
+            for (uint32_t i = 0; i < 8u; ++i) {
+              const uint32_t bit = (bits >> i) & 1u;
+              v[i] = X[bit ? pb : pa];
+              pa += bit ^ 1u;
+              pb += bit;
+            }
+          } else {
+#pragma unroll
+            for (uint32_t i = 0; i < 8u; ++i) {
+              const uint32_t ti = t + i;
+              const uint32_t bit = (bits >> i) & 1u;
+              const uint32_t src = ti < Tr ? (bit ? pb : pa) : lbr + ti;
+              v[i] = ti < Nr ? X[min(src, a.buf - 1u)] : 0u;
+              pa += bit ^ 1u;
+              pb += bit;
+            }
+          }
+          uint4 o;
+          o.x = v[0] | (v[1] << 16);
+          o.y = v[2] | (v[3] << 16);
+          o.z = v[4] | (v[5] << 16);
+          o.w = v[6] | (v[7] << 16);
+          *reinterpret_cast<uint4 *>(Yr + t) = o;
+        }
+      }
+      __syncthreads();
+      if (role == 0u) {
+        // random insertion of positions T .. N-1, in order, one lane per merge
+        if (lane < R) {
+          const uint32_t Tq = ctl_T(c)[lane], Nq = ctl_N(c)[lane];
+          uint16_t *const Cq = Y + lane * Sout;
+          if (*ctl_drawn(c)) {
+            const uint16_t *const mk = c.mv + ctl_koff(c)[lane];
+            for (uint32_t i = Tq; i < Nq; ++i)
+              swap_smem(Cq, i, min(static_cast<uint32_t>(mk[i - Tq]), i));
+          } else {
+            const uint32_t id = static_cast<uint32_t>(k0 >> (lv + 1u)) + lane;
+            DrawMemo memo;
+            for (uint32_t i = Tq; i < Nq; ++i)
+              swap_smem(Cq, i, draw_uniform(a.key, kTagTail, lv, id, i, i + 1u, memo));
+          }
+        }
+      } else if (lv + 1u < a.d) {
+        level_setup(a, boff, k0, lv + 1u, Sout, lane, ctl((lv + 1u) & 1u));
+      }
+      __syncthreads();
+    }
+
+    // ---- the tile's result (level d-1 wrote the second buffer if d is odd, else the first)
+    {
+      const uint16_t *const Z = (a.d & 1u) ? bufB : bufA;
+      const uint32_t Lt = boff[nb];
+      if constexpr (kPerm) {
+        uint32_t *const o = static_cast<uint32_t *>(a.out) + g0;
+        const uint32_t gb = static_cast<uint32_t>(g0);
+        uint32_t t = tid;
+        if ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u) {
+          const uint32_t n4 = Lt >> 2;
+          for (uint32_t c4 = tid; c4 < n4; c4 += 64u) {
+            const uint2 pr = *reinterpret_cast<const uint2 *>(Z + 4u * c4);
+            uint4 vv;
+            vv.x = gb + (pr.x & 0xFFFFu);
+            vv.y = gb + (pr.x >> 16);
+            vv.z = gb + (pr.y & 0xFFFFu);
+            vv.w = gb + (pr.y >> 16);
+            *reinterpret_cast<uint4 *>(o + 4u * c4) = vv;
+          }
+          t = 4u * n4 + tid;
+        }
+        for (; t < Lt; t += 64u) o[t] = gb + Z[t];
+      } else {
+        const E *const src = static_cast<const E *>(a.in) + g0;
+        E *const o = static_cast<E *>(a.out) + g0;
+        for (uint32_t t = tid; t < Lt; t += 64u)
+          o[t] = src[min(static_cast<uint32_t>(Z[t]), Lt - 1u)];
+      }
+    }
+    __syncthreads();  // the buffers are reused by the next tile
+  }
+}
+
+template <typename E, bool kPerm>
+cudaError_t launch_t(const Plan &p, const void *in, void *out, uint64_t seed, cudaStream_t s) {
+  TileArgs a;
+  a.in = in;
+  a.out = out;
+  a.n = p.n;
+  a.key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  a.c = p.c;
+  a.d = p.d;
+  a.P = p.tile_P;
+  a.buf = p.tile_buf;
+  a.wcap = p.tile_wcap;
+  a.tcap = p.tile_tcap;
+  for (uint32_t l = 0; l < kTileMaxDepth; ++l) a.S[l] = p.tile_S[l];
+  auto kern = tile_kernel<E, kPerm>;
+  cudaError_t err = allow_dynamic_smem(kern, p.tile_smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, p.tile_smem);
+  if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaErrorUnknown;
+  const uint64_t tiles = p.q >> p.d;
+  const uint64_t resident = static_cast<uint64_t>(per_sm > 0 ? per_sm : 1) * sms;
+  const uint64_t grid = tiles < resident ? tiles : resident;
+  if (p.prof) p.prof->begin(kKindLeaf, s);
+  kern<<<static_cast<unsigned>(grid), 64, p.tile_smem, s>>>(a);
+  if (p.prof) p.prof->end(s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tile(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
+                        cudaStream_t s) {
+  if (p.d == 0 || p.d > kTileMaxDepth) return cudaErrorInvalidValue;
+  if (perm) return launch_t<uint32_t, true>(p, in, out, seed, s);
+  // the tile reads its input rows after computing its indices: never in place
+  if (in == out) return cudaErrorInvalidValue;
+  switch (p.w) {
+    case 4: return launch_t<uint32_t, false>(p, in, out, seed, s);
+    case 8: return launch_t<uint2, false>(p, in, out, seed, s);
+    case 16: return launch_t<uint4, false>(p, in, out, seed, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace msk

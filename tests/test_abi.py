@@ -69,8 +69,19 @@ def test_plan_fusion_depth_and_workspace():
     assert ms.ms_host_workspace_bytes(2**30, 4, ms.params(B=1024)) >= ws + 2**30 * 4
     # forced depth is honoured (capped by c)
     assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=0)).fuse_depth == 0
-    assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2)).fuse_depth == 2
-    assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9)).fuse_depth == 2
+    perm = ms.MS_FLAG_PERM
+    assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2, flags=perm)).fuse_depth == 2
+    # a shuffle's one-warp tile pass must not run in place: with 1 span level and 7 global
+    # levels after it, it fuses one level less (an odd number of passes follows)
+    sh = ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2))
+    assert sh.fuse_depth == 1 and (sh.passes - 1) % 2 == 1
+    # the workspace covers both forms
+    for fl in (0, perm):
+        assert ms.ms_workspace_bytes(2**20, 4, ms.params(B=1024, fuse_depth=2)) >= \
+            ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2, flags=fl)).workspace_bytes
+    assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9, flags=perm)).fuse_depth == 2
+    # (all of a shuffle's levels fused would leave its tile pass in place)
+    assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9)).fuse_depth == 1
 
 
 def test_plan_records():

@@ -2,8 +2,8 @@
 and a shuffle of 300,000,017 16-byte records, seed 7, autotuned B), where the oracle would take
 minutes: properties that hold at any size.
   * the 2^30 output is a permutation of 0..n-1;
-  * it does not depend on the level kernels (every HBM level through the global plan gives the
-    same array as the default mix of warp, CTA and global levels);
+  * it does not depend on the kernels (no fused levels and every level through the global
+    plan gives the same array as the tuned plan, whose tile kernel fuses the first levels);
   * the record shuffle is data-oblivious: its output equals the input gathered by the perm of the
     same (n, seed, B), so the 16-byte path agrees with the 4-byte path element by element."""
 from __future__ import annotations
@@ -39,9 +39,9 @@ def test_perm_2p30_is_a_permutation_and_level_mode_independent():
     seen[out.long()] = True
     assert bool(seen.all())
     del seen
-    q = ms.params(B=p.B, fuse_depth=p.fuse_depth, flags=ms.MS_FLAG_GLOBAL_LEVELS)
-    assert ms.plan(n, 4, B=p.B, fuse_depth=p.fuse_depth,
-                   flags=ms.MS_FLAG_GLOBAL_LEVELS)["global_levels"] > \
+    # the same permutation with no fused levels and every level through the global plan
+    q = ms.params(B=p.B, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS)
+    assert ms.plan(n, 4, B=p.B, fuse_depth=0, flags=ms.MS_FLAG_GLOBAL_LEVELS)["global_levels"] > \
         ms.ms_plan_info(n, 4, p).global_levels
     other = _perm(n, q)
     assert torch.equal(out, other)
