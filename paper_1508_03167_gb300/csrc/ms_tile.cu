@@ -1,17 +1,20 @@
 // ms_tile.cu -- the base blocks of a tile of 2^d consecutive base blocks and the tile's first d
-// merge levels (Algorithms 1 to 3 of arXiv 1508.03167), one warp per tile, computed on 16-bit
-// tile-local indices in shared memory; the tile is then written once (perm: the indices plus
-// the tile's first element; shuffle: the input rows they name).
+// merge levels (Algorithms 1 to 3 of arXiv 1508.03167), one CTA of four warps per tile,
+// computed on 16-bit tile-local indices in shared memory; the tile is then written once (perm:
+// the indices plus the tile's first element; shuffle: the input rows they name).
 //
 // Per tile:
-//   * Algorithm 1's draws for every position of every base block (lane k: block k). A draw
-//     whose first Philox word rejects all its slices is queued by its lane and finished after
-//     the loop, so no lane holds the warp up with a second Philox block inline;
+//   * Algorithm 1's draws for every position of every base block (lane k of each warp: block
+//     k; the warps split its positions). A draw whose first Philox word rejects all its slices
+//     is queued by its thread and finished after the loop, so no lane holds its warp up with a
+//     second Philox block inline;
 //   * Algorithm 1's swap chain per block, reading those draws;
 //   * per merge level: coin words and their zero prefix, the break step T of every merge,
 //     the stable interleave (a lane places eight consecutive positions, walking the two
 //     halves with one index each), the tail draws, and the random insertions of Algorithm 3's
-//     second loop in order, one lane per merge;
+//     second loop in order, one lane per merge. The data-independent part of level l+1 (coins,
+//     prefixes, break steps, tail draws) is built by one warp while another runs level l's
+//     tails;
 //   * one store of the tile.
 // Block k of the tile sits at k*P in the first buffer (P = 2 mod 64, so the 32 lanes at one
 // position of their blocks touch 32 different banks); merge r of level l writes its output at
@@ -23,7 +26,7 @@
 namespace msk {
 namespace {
 
-constexpr uint32_t kFailPerLane = 16;  // queued second-word draws per lane and block group
+constexpr uint32_t kFailPerThread = 8;  // queued second-word draws per thread and block group
 
 struct TileArgs {
   const void *in;
@@ -65,11 +68,16 @@ __device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m +
 // The data-independent part of merge level lv of the tile, by one warp: coin words, zero
 // prefixes and break step of every merge, the leftover base, and the tail draws. G = 32 / R
 // lanes per merge: lane (r, sub) = (lane / G, lane % G).
-__device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *boff, uint64_t k0,
-                                            uint32_t lv, uint32_t Sin, uint32_t lane,
-                                            const LevelCtl &c) {
+__device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
+                                        const uint32_t *boff, uint64_t k0, uint32_t lv,
+                                        uint32_t Sin, uint32_t lane, uint2 *czb, uint16_t *mvb,
+                                        uint32_t *mb) {
+  LevelCtl c;
+  c.cz = czb;
+  c.mv = mvb;
+  c.m = mb;
   const uint32_t idbase = static_cast<uint32_t>(k0 >> (lv + 1u));
-  const uint32_t lgG = 5u - (a.d - lv - 1u);  // (R = 2^(d-lv-1) <= 32)
+  const uint32_t lgG = 5u - (d - lv - 1u);  // (R = 2^(d-lv-1) <= 32)
   const uint32_t G = 1u << lgG;
   const uint32_t r = lane >> lgG;
   const uint32_t sub = lane & (G - 1u);
@@ -84,7 +92,7 @@ __device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *b
   // coin words (one Philox block: four words, 128 steps)
   const uint32_t nblk = (Wm + 3u) >> 2;
   for (uint32_t jb = sub; jb < nblk; jb += G) {
-    const uint4 blk = coin_block(a.key, lv, idbase + r, jb);
+    const uint4 blk = coin_block(key, lv, idbase + r, jb);
     const uint32_t j = 4u * jb;
     cz[j].x = blk.x;
     if (j + 1u < Wm) cz[j + 1u].x = blk.y;
@@ -140,7 +148,7 @@ __device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *b
     ctl_woff(c)[r] = woff;
     ctl_koff(c)[r] = koff;
   }
-  const bool drawn = Ktot <= a.tcap;
+  const bool drawn = Ktot <= tcap;
   if (lane == 0) *ctl_drawn(c) = drawn ? 1u : 0u;
   // tail draws, one Philox block per four consecutive positions (lane (r, sub): quads sub,
   // sub + G, ... of merge r's tail); else the tails draw in their loop
@@ -148,14 +156,14 @@ __device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *b
     for (uint32_t gq = sub; gq < Q; gq += G) {
       const uint32_t quad = (T >> 2) + gq;
       const uint32_t id = idbase + r;
-      const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lv, 0u), a.key);
+      const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lv, 0u), key);
 #pragma unroll
       for (uint32_t v = 0; v < 4u; ++v) {
         const uint32_t i = 4u * quad + v;
         if (i >= T && i < N) {
           uint32_t x;
           if (!draw_first_word(pick_word(w0, v), i + 1u, x))
-            x = draw_continue(a.key, kTagTail, lv, id, i, i + 1u);
+            x = draw_continue(key, kTagTail, lv, id, i, i + 1u);
           c.mv[koff + (i - T)] = static_cast<uint16_t>(x);
         }
       }
@@ -163,11 +171,15 @@ __device__ __forceinline__ void level_setup(const TileArgs &a, const uint32_t *b
   }
 }
 
-// Two warps per tile. Both make the Fisher-Yates draws and the interleaves; the data warp runs
-// the serial parts (Algorithm 1's swaps, the merge tails) while the control warp builds the
-// next level's control data.
+// Four warps per tile, in three roles that rotate from tile to tile (the warps of a CTA sit on
+// different SM sub-partitions, which would otherwise carry unequal loads): all four make the
+// Fisher-Yates draws and the interleaves; the data warp runs the serial parts (Algorithm 1's
+// swaps, the merge tails) while the control warp builds the next level's control data.
+constexpr uint32_t kTileWarps = 4;
+constexpr uint32_t kTileThreads = 32u * kTileWarps;
+
 template <typename E, bool kPerm>
-__global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
+__global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t boff[(1u << kTileMaxDepth) + 1u];
   __shared__ uint32_t ctlm[2][kTileCtlWords];
@@ -200,11 +212,13 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
   for (uint64_t tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
     const uint64_t k0 = tt << a.d;
     const uint64_t g0 = boundary(a.n, a.c, k0);
-    for (uint32_t k = tid; k <= nb; k += 64u)
+    for (uint32_t k = tid; k <= nb; k += kTileThreads)
       boff[k] = static_cast<uint32_t>(boundary(a.n, a.c, k0 + k) - g0);
+    // roles of this tile: 0 data, 1 control, 2 and 3 helpers
+    const uint32_t role = (warp - static_cast<uint32_t>(tt)) & (kTileWarps - 1u);
     __syncthreads();
 
-    // ---- Algorithm 1's draws (warp w: quads w, w+2, ... of every block; lane: the block)
+    // ---- Algorithm 1's draws (warp w: quads w, w+4, ... of every block; lane: the block)
     for (uint32_t kg = 0; kg < nb; kg += 32u) {
       const uint32_t k = kg + lane;
       const bool act = k < nb;
@@ -212,12 +226,12 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
       const uint32_t L = act ? boff[k + 1u] - off : 0u;
       uint16_t *const A = bufA + k * a.P;
       uint16_t *const D = bufB + k * a.P;  // D[i]: the draw of position i
-      uint32_t *const F = flist + tid * kFailPerLane;
+      uint32_t *const F = flist + tid * kFailPerThread;
       const uint32_t id = static_cast<uint32_t>(k0 + k);
       const uint32_t nq = L ? ((L - 1u) >> 2) + 1u : 0u;
       uint32_t nf = 0;
 #pragma unroll 2
-      for (uint32_t qd = warp; qd < nq; qd += 2u) {
+      for (uint32_t qd = warp; qd < nq; qd += kTileWarps) {
         const uint4 blk = philox10(make_uint4(qd, id, kTagLeaf << 16, 0u), a.key);
 #pragma unroll
         for (uint32_t v = 0; v < 4u; ++v) {
@@ -228,7 +242,7 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
               uint32_t x;
               if (draw_first_word(pick_word(blk, v), pos + 1u, x)) {
                 D[pos] = static_cast<uint16_t>(x);
-              } else if (nf < kFailPerLane) {
+              } else if (nf < kFailPerThread) {
                 F[nf++] = pos;
               } else {
                 D[pos] = static_cast<uint16_t>(
@@ -246,16 +260,11 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
     }
     __syncthreads();
 
-    // The two roles swap from tile to tile (the warps of a CTA sit on different SM
-    // sub-partitions, which would otherwise carry unequal loads): the data warp runs the serial
-    // parts, the control warp builds the next level's control data meanwhile.
-    const uint32_t dw = static_cast<uint32_t>(tt & 1u);  // data warp of this tile
-    const uint32_t role = warp ^ dw;                     // 0: data, 1: control
-
-    // ---- Algorithm 1's swaps, i = L-1 .. 1 (role q: blocks 32q .. 32q+31; the draws are read
-    // four ahead of the chain and clamped to the block); the control warp then builds level 0's
-    for (uint32_t kg = 32u * role; kg < nb; kg += 64u) {
-      const uint32_t k = kg + lane;
+    // ---- Algorithm 1's swaps, i = L-1 .. 1 (blocks 0..31: the data warp, 32..63: a helper; the
+    // draws are read four ahead of the chain and clamped to the block); meanwhile the control
+    // warp builds level 0's control data
+    if (role == 0u || role == 2u) {
+      const uint32_t k = (role == 0u ? 0u : 32u) + lane;
       const uint32_t L = k < nb ? boff[k + 1u] - boff[k] : 0u;
       uint16_t *const A = bufA + k * a.P;
       const uint16_t *const D = bufB + k * a.P;
@@ -272,8 +281,10 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
         i -= 4u;
       }
       for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+    } else if (role == 1u) {
+      const LevelCtl c0 = ctl(0u);
+      level_setup(a.key, a.d, a.tcap, boff, k0, 0u, a.P, lane, c0.cz, c0.mv, c0.m);
     }
-    if (role == 1u) level_setup(a, boff, k0, 0u, a.P, lane, ctl(0u));
     __syncthreads();
 
     // ---- merge levels 0 .. d-1 of the tile (Algorithm 2)
@@ -283,16 +294,18 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
       const uint32_t Sout = s_S[lv];
       const uint32_t R = nb >> (lv + 1u);
       const LevelCtl c = ctl(lv & 1u);
-      // stable interleave: thread places positions t .. t+7 of merge rr (both warps; which
-      // warp takes the upper 256 positions of each 512 alternates between merges)
-      for (uint32_t rr = 0; rr < R; ++rr) {
-        const uint32_t gi = 32u * (warp ^ (rr & 1u)) + lane;
+      // stable interleave: a thread places positions t .. t+7 of a merge. With R >= 4 merges a
+      // warp takes whole merges (r = w, w+4, ...); with fewer, 4/R warps share each merge
+      const uint32_t wpm = R >= kTileWarps ? 1u : kTileWarps / R;  // warps per merge
+      const uint32_t rstep = kTileWarps / wpm;
+      const uint32_t sw = warp % wpm;
+      for (uint32_t rr = warp / wpm; rr < R; rr += rstep) {
         const uint32_t Nr = ctl_N(c)[rr], Tr = ctl_T(c)[rr], ar = ctl_a(c)[rr],
                        br = ctl_b(c)[rr], lbr = ctl_lb(c)[rr];
         const uint2 *const czr = c.cz + ctl_woff(c)[rr];
         uint16_t *const Yr = Y + rr * Sout;
-        for (uint32_t t0 = 0; t0 < Nr; t0 += 512u) {
-          const uint32_t t = t0 + 8u * gi;
+        for (uint32_t t0 = 256u * sw; t0 < Nr; t0 += 256u * wpm) {
+          const uint32_t t = t0 + 8u * lane;
           if (t >= Nr) continue;
           const uint2 wz = czr[t >> 5];
           const uint32_t sh = t & 31u;
@@ -346,8 +359,9 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
               swap_smem(Cq, i, draw_uniform(a.key, kTagTail, lv, id, i, i + 1u, memo));
           }
         }
-      } else if (lv + 1u < a.d) {
-        level_setup(a, boff, k0, lv + 1u, Sout, lane, ctl((lv + 1u) & 1u));
+      } else if (role == 1u && lv + 1u < a.d) {
+        const LevelCtl cn = ctl((lv + 1u) & 1u);
+        level_setup(a.key, a.d, a.tcap, boff, k0, lv + 1u, Sout, lane, cn.cz, cn.mv, cn.m);
       }
       __syncthreads();
     }
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
         uint32_t t = tid;
         if ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u) {
           const uint32_t n4 = Lt >> 2;
-          for (uint32_t c4 = tid; c4 < n4; c4 += 64u) {
+          for (uint32_t c4 = tid; c4 < n4; c4 += kTileThreads) {
             const uint2 pr = *reinterpret_cast<const uint2 *>(Z + 4u * c4);
             uint4 vv;
             vv.x = gb + (pr.x & 0xFFFFu);
@@ -373,11 +387,11 @@ __global__ void __launch_bounds__(64, 8) tile_kernel(TileArgs a) {
           }
           t = 4u * n4 + tid;
         }
-        for (; t < Lt; t += 64u) o[t] = gb + Z[t];
+        for (; t < Lt; t += kTileThreads) o[t] = gb + Z[t];
       } else {
         const E *const src = static_cast<const E *>(a.in) + g0;
         E *const o = static_cast<E *>(a.out) + g0;
-        for (uint32_t t = tid; t < Lt; t += 64u)
+        for (uint32_t t = tid; t < Lt; t += kTileThreads)
           o[t] = src[min(static_cast<uint32_t>(Z[t]), Lt - 1u)];
       }
     }
@@ -403,7 +417,7 @@ cudaError_t launch_t(const Plan &p, const void *in, void *out, uint64_t seed, cu
   cudaError_t err = allow_dynamic_smem(kern, p.tile_smem);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, p.tile_smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, p.tile_smem);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -413,7 +427,7 @@ cudaError_t launch_t(const Plan &p, const void *in, void *out, uint64_t seed, cu
   const uint64_t resident = static_cast<uint64_t>(per_sm > 0 ? per_sm : 1) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
   if (p.prof) p.prof->begin(kKindLeaf, s);
-  kern<<<static_cast<unsigned>(grid), 64, p.tile_smem, s>>>(a);
+  kern<<<static_cast<unsigned>(grid), kTileThreads, p.tile_smem, s>>>(a);
   if (p.prof) p.prof->end(s);
   return cudaGetLastError();
 }
