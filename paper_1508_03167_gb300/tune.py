@@ -23,9 +23,11 @@ HEADER = os.path.join(HERE, "csrc", "ms_tune_table.h")
 JSON_PATH = os.path.join(HERE, "tune_table.json")
 
 B_CANDIDATES = (32, 64, 128, 256, 512, 1024)
-# (fuse_depth, flags) alternatives per B: the planner's fusion depth or none; the default small
-# levels or per-CTA ones; one data pass per global level or fused pairs of them
-MODE_CANDIDATES = ((-1, 0), (0, 0), (0, 0x8), (0, 0x80), (0, 0x100))
+# (fuse_depth, flags) alternatives per B: the planner's fusion depth, none, or 3 .. 6 levels in
+# the tile kernel; the default small levels or per-CTA ones; one data pass per global level or
+# fused pairs of them
+MODE_CANDIDATES = ((-1, 0), (0, 0), (0, 0x8), (0, 0x80), (0, 0x100), (3, 0), (4, 0), (5, 0),
+                   (6, 0), (5, 0x80), (5, 0x100))
 # size points per width: log2 n (the largest fits a 2 x n x w footprint comfortably); sizes are
 # 2^k for w = 4 and 2^k + 17 otherwise (uneven halves), except that the last 16-byte point is
 # the 300,000,017-record workload itself
