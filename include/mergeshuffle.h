@@ -34,7 +34,7 @@
  * (the scratch is about 0.4*n*w for 4-byte elements at n = 2^30).
  *
  * Streams. Each call enqueues on the caller's stream; the data-independent plan of the global
- * merge levels runs on a second, high-priority stream paired with the caller's (created on first
+ * merge levels runs on a second, low-priority stream paired with the caller's (created on first
  * use, ordered with events) unless MS_FLAG_SINGLE_STREAM is set.
  *
  * Errors. Argument errors are returned synchronously. Launch failures return MS_ERR_CUDA
@@ -95,7 +95,7 @@ typedef void *ms_stream_t;
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level
-                                        runs on a second, high-priority stream paired with the
+                                        runs on a second, low-priority stream paired with the
                                         caller's, one or two levels ahead; make the first call
                                         on a stream before capturing it into a CUDA graph */
 

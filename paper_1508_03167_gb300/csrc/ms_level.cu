@@ -483,6 +483,187 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(LevelArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ staged gather (w <= 8) --
+// The same data pass for 4- and 8-byte elements, one CTA per 4096-step chunk. The chunk's
+// outputs read one contiguous run of each half: its zeros from the first half and its ones from
+// the second, and after the break step the rest of the half that did not run out. The runs'
+// bounds follow from the chunk's zero prefix and the merge's break step alone, so both runs are
+// copied into shared memory with 16-byte asynchronous copies while the chunk's coins are
+// generated. Each thread then places eight consecutive outputs, walking one index per run
+// (past the break step the coin is replaced by the half that did not run out), and stores them
+// as 16-byte vectors aligned to the output.
+constexpr uint32_t kStageGroup = 8;  // outputs per thread group
+constexpr uint32_t kStageThreads = 128;  // (16 CTAs an SM: more chunks in flight than 256)
+
+// copies n elements from global src to shared dst (dst at src's 16-byte phase)
+template <typename E>
+__device__ __forceinline__ void stage_run(E *dst, const E *src, uint32_t n) {
+  constexpr uint32_t kV = 16u / sizeof(E);
+  const uint32_t ph = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(src) & 15u) / sizeof(E));
+  const uint32_t head = min(n, (kV - ph) % kV);
+  const uint32_t body = (n - head) / kV;
+  const uint32_t tail0 = head + body * kV;
+  const uint32_t tid = threadIdx.x;
+  if (tid < head) cp_async_elem(dst + tid, src + tid);
+  for (uint32_t c = tid; c < body; c += kStageThreads)
+    cp_async_elem(reinterpret_cast<uint4 *>(dst + head) + c,
+                  reinterpret_cast<const uint4 *>(src + head) + c);
+  if (tid < n - tail0) cp_async_elem(dst + tail0 + tid, src + tail0 + tid);
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kStageThreads) gather_staged_kernel(LevelArgs a) {
+  constexpr uint32_t kV = 16u / sizeof(E);      // elements per 16 bytes
+  // both runs with their 16-byte phases (at most kChunk + 3 kV - 2 entries), plus one group of
+  // slack so that a clamped walk of eight steps stays inside
+  constexpr uint32_t kBuf = kChunk + 4u * kV + kStageGroup;
+  __shared__ __align__(16) E sbuf[kBuf];
+  __shared__ uint32_t cw[kChunk / 32u + 1u];
+  __shared__ uint32_t zw[kChunk / 32u];
+  if (gated_off(a)) return;
+  const E *__restrict__ in = static_cast<const E *>(a.in);
+  E *__restrict__ out = static_cast<E *>(a.out);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t r = static_cast<uint32_t>(cid / a.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(r) * a.J);
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t t0 = j * kChunk;
+    if (t0 >= N) continue;  // uniform across the CTA
+    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint32_t len = t1 - t0;
+    const uint4 mi = a.minfo[r];
+    const uint32_t T = mi.x;
+    const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+    const uint32_t n2 = N - n1;
+    const bool a_out = (mi.y == n1);  // the first half ran out at T (or T = N)
+    // chunk-relative break step, zeros before it, and the two runs (half-relative start, size)
+    uint32_t Tc, zT, za, na, ob, nb;
+    if (t0 >= T) {
+      Tc = 0;
+      zT = 0;
+      za = a_out ? 0u : t0 - n2;
+      ob = a_out ? t0 - n1 : 0u;
+      na = a_out ? 0u : len;
+      nb = a_out ? len : 0u;
+    } else {
+      const uint32_t Z0 = a.zc[cid];
+      Tc = min(t1, T) - t0;
+      const uint32_t Jr = (N + kChunk - 1u) / kChunk;
+      zT = (t1 <= T) ? ((j + 1u < Jr) ? a.zc[cid + 1] - Z0 : n1 - Z0) : mi.y - Z0;
+      za = Z0;
+      ob = t0 - Z0;
+      na = zT + (a_out ? 0u : len - Tc);
+      nb = (Tc - zT) + (a_out ? len - Tc : 0u);
+    }
+    // (the runs stay inside their halves even for an inconsistent plan)
+    za = min(za, n1);
+    na = min(na, n1 - za);
+    ob = min(ob, n2);
+    nb = min(nb, n2 - ob);
+    const E *const srcA = in + mb.s + za;
+    const E *const srcB = in + mb.mid + ob;
+    const uint32_t offA = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(srcA) & 15u) / sizeof(E));
+    const uint32_t offB = ((offA + na + kV - 1u) / kV) * kV +
+                          static_cast<uint32_t>((reinterpret_cast<uintptr_t>(srcB) & 15u) / sizeof(E));
+    stage_run(sbuf + offA, srcA, min(na, kBuf - offA));
+    stage_run(sbuf + offB, srcB, min(nb, kBuf - min(offB, kBuf)));
+    cp_async_commit();
+    // coins of steps [t0, t0 + Tc) and the zeros before each of their words (warp 0)
+    if (tid < 32u) {
+      const uint32_t nwords = (Tc + 31u) >> 5;
+      if (4u * lane < nwords) {
+        const uint4 c = coin_block(a.key, a.level, r, j * (kChunk / 128u) + lane);
+        cw[4u * lane + 0u] = c.x;
+        cw[4u * lane + 1u] = c.y;
+        cw[4u * lane + 2u] = c.z;
+        cw[4u * lane + 3u] = c.w;
+      }
+      __syncwarp();
+      uint32_t z4[4], zs = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        z4[k] = (4u * lane + k < nwords) ? static_cast<uint32_t>(__popc(~cw[4u * lane + k])) : 0u;
+        zs += z4[k];
+      }
+      uint32_t ex = warp_inclusive_scan(zs) - zs;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        zw[4u * lane + k] = ex;
+        ex += z4[k];
+      }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    // groups of eight outputs aligned to 16 bytes of the output (group 0: the head before the
+    // first aligned one)
+    E *const C = out + mb.s + t0;
+    const uint32_t cph = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(C) & 15u) / sizeof(E));
+    const uint32_t hd = min(len, (kV - cph) % kV);
+    const uint32_t ngroups = 1u + (len - hd + kStageGroup - 1u) / kStageGroup;
+    const uint32_t abit = a_out ? 1u : 0u;
+    for (uint32_t gi = tid; gi < ngroups; gi += kStageThreads) {
+      const uint32_t p0 = gi == 0u ? 0u : hd + kStageGroup * (gi - 1u);
+      const uint32_t cnt = gi == 0u ? hd : min(kStageGroup, len - p0);
+      if (cnt == 0u) continue;
+      uint32_t pa, pb, bits;
+      if (p0 < Tc) {
+        const uint32_t u = p0 >> 5, sh = p0 & 31u;
+        const uint32_t w0 = cw[u];
+        pa = zw[u] + static_cast<uint32_t>(__popc(~w0 & low_mask(sh)));
+        pb = p0 - pa;
+        bits = __funnelshift_r(w0, cw[u + 1u], sh);  // coins of p0 .. p0+31
+      } else {
+        pa = zT + (p0 - Tc) * (1u - abit);
+        pb = (Tc - zT) + (p0 - Tc) * abit;
+        bits = 0u;
+      }
+      // (the walk stays inside the buffer even for an inconsistent plan)
+      pa = min(offA + pa, kBuf - kStageGroup);
+      pb = min(offB + pb, kBuf - kStageGroup);
+      E v[kStageGroup];
+      if (p0 + kStageGroup <= Tc) {
+#pragma unroll
+        for (uint32_t i = 0; i < kStageGroup; ++i) {
+          const uint32_t bit = (bits >> i) & 1u;
+          v[i] = sbuf[bit ? pb : pa];
+          pa += bit ^ 1u;
+          pb += bit;
+        }
+      } else {
+#pragma unroll
+        for (uint32_t i = 0; i < kStageGroup; ++i) {
+          const uint32_t bit = (p0 + i < Tc) ? ((bits >> i) & 1u) : abit;
+          v[i] = sbuf[bit ? pb : pa];
+          pa += bit ^ 1u;
+          pb += bit;
+        }
+      }
+      if (gi != 0u && cnt == kStageGroup) {
+        uint4 *const dst = reinterpret_cast<uint4 *>(C + p0);
+#pragma unroll
+        for (uint32_t q = 0; q < kStageGroup / kV; ++q) {
+          uint4 o;
+          if constexpr (sizeof(E) == 4) {
+            o = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            o = make_uint4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+          }
+          dst[q] = o;
+        }
+      } else {
+#pragma unroll
+        for (uint32_t i = 0; i < kStageGroup; ++i)
+          if (i < cnt) C[p0 + i] = v[i];
+      }
+    }
+    __syncthreads();  // the staging buffer is reused by the next chunk
+  }
+}
+
 // ---------------------------------------------------------------------------- fused pairs --
 // Two consecutive levels l, l+1 in one data pass. Level l's output (never written) is the
 // stable interleave of its halves with the tail moves applied; a tail move is an exception:
@@ -884,7 +1065,10 @@ cudaError_t launch_data_t(const Plan &p, const LevelPlan &lv, const void *in, vo
   const LevelArgs a = level_args(p, lv, in, out, b, seed);
   const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
   timed(p.prof, kKindGather, s, [&] {
-    gather_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(a);
+    if constexpr (sizeof(E) <= 8)
+      gather_staged_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kStageThreads, 0, s>>>(a);
+    else
+      gather_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(a);
   });
   timed(p.prof, kKindTailSeq, s, [&] {
     tail_sequential_kernel<E><<<grid_for(lv.M, kThreads, 1u << 16), kThreads, 0, s>>>(a);

@@ -30,27 +30,6 @@ struct SpanArgs {
   uint32_t flags;      // MS_FLAG_TAIL_SEQUENTIAL (0x1): draws made in the loop
 };
 
-// asynchronous global -> shared copy of one element (cp.async, L1-allocating for 4 and 8 bytes,
-// L2-only for 16)
-template <typename E>
-__device__ __forceinline__ void cp_async_elem(E *dst, const E *src) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  if constexpr (sizeof(E) == 4) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
-  } else if constexpr (sizeof(E) == 8) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
-  } else {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
-  }
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 __host__ __device__ __forceinline__ size_t r16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // kThreads = 128 or 256; the register budget (64 a thread) lets 1024 / kThreads CTAs share an SM
