@@ -1002,6 +1002,330 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
   }
 }
 
+// ---------------------------------------------------------- staged fused pair (w = 4) ----
+// Two levels l, l+1 in one pass for 4-byte elements. A CTA takes 4096 outputs of level l+1;
+// they read one range of each of its halves (merges 2R and 2R+1 of level l), and each range is
+// the interleave of one run of each half of its level-l merge (then that merge's leftover),
+// with level l's tail moves as exceptions. The four input runs are copied to shared memory
+// with 16-byte asynchronous copies; the two level-l ranges are built there (walking the runs
+// with level l's coins, then overwriting the exception positions from the exception hash); the
+// level l+1 outputs are placed from them as in the staged single gather.
+__global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa) {
+  using E = uint32_t;
+  constexpr uint32_t kV = 4;
+  constexpr uint32_t kRunBuf = kChunk + 8u * kV + kStageGroup;  // four runs with their phases
+  constexpr uint32_t kValBuf = kChunk + 2u * kStageGroup;       // two ranges, group-aligned
+  __shared__ __align__(16) E sruns[kRunBuf];
+  __shared__ __align__(16) E svals[kValBuf];
+  __shared__ uint32_t cw2[kChunk / 32u + 1u];
+  __shared__ uint32_t zw2[kChunk / 32u];
+  __shared__ uint32_t cw1[2][kPairW + 1u];
+  __shared__ uint32_t zw1[2][kPairW];
+  __shared__ uint32_t xb1[2][kPairW];
+  __shared__ uint32_t hs[2][12];
+  const LevelArgs &a1 = pa.l1;
+  const LevelArgs &a2 = pa.l2;
+  if (a1.ctrl[1]) return;  // level l's tails overflowed: the unfused fallback runs instead
+  const E *__restrict__ in = static_cast<const E *>(pa.in);
+  E *__restrict__ out = static_cast<E *>(pa.out);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint64_t nchunks = static_cast<uint64_t>(a2.M) * a2.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t R = static_cast<uint32_t>(cid / a2.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(R) * a2.J);
+    const MergeBounds mb2 = merge_bounds(a2, R);
+    const uint32_t N2 = static_cast<uint32_t>(mb2.e - mb2.s);
+    const uint32_t t0 = j * kChunk;
+    if (t0 >= N2) continue;  // uniform across the CTA
+    const uint32_t t1 = min(t0 + kChunk, N2);
+    const uint32_t len = t1 - t0;
+    const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);  // level l+1's first half
+    const uint32_t h2 = N2 - h1;
+    const uint4 mi2 = a2.minfo[R];
+    const uint32_t T2 = mi2.x;
+    const uint32_t abit2 = (mi2.y == h1) ? 1u : 0u;  // 1: level l+1's first half ran out
+    // level l+1: chunk-relative break step Tc2, zeros before it zT2; the two level-l ranges
+    uint32_t Tc2, zT2, lo0, lo1;
+    if (t0 >= T2) {
+      Tc2 = 0;
+      zT2 = 0;
+      lo0 = abit2 ? 0u : t0 - h2;
+      lo1 = abit2 ? t0 - h1 : 0u;
+    } else {
+      const uint32_t Z0 = a2.zc[cid];
+      Tc2 = min(t1, T2) - t0;
+      const uint32_t Jr = (N2 + kChunk - 1u) / kChunk;
+      zT2 = (t1 <= T2) ? ((j + 1u < Jr) ? a2.zc[cid + 1] - Z0 : h1 - Z0) : mi2.y - Z0;
+      lo0 = Z0;
+      lo1 = t0 - Z0;
+    }
+    const uint32_t cnt0 = min(zT2 + (abit2 ? 0u : len - Tc2), h1 - min(lo0, h1));
+    const uint32_t cnt1 = min((Tc2 - zT2) + (abit2 ? len - Tc2 : 0u), h2 - min(lo1, h2));
+    if (warp == 2u) {
+      // coins of level l+1 for steps [t0, t0 + Tc2) and the zeros before each word
+      const uint32_t nwords = (Tc2 + 31u) >> 5;
+      if (4u * lane < nwords) {
+        const uint4 c = coin_block(a2.key, a2.level, R, j * (kChunk / 128u) + lane);
+        cw2[4u * lane + 0u] = c.x;
+        cw2[4u * lane + 1u] = c.y;
+        cw2[4u * lane + 2u] = c.z;
+        cw2[4u * lane + 3u] = c.w;
+      }
+      __syncwarp();
+      uint32_t z4[4], zs = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        z4[k] = (4u * lane + k < nwords) ? static_cast<uint32_t>(__popc(~cw2[4u * lane + k])) : 0u;
+        zs += z4[k];
+      }
+      uint32_t ex = warp_inclusive_scan(zs) - zs;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        zw2[4u * lane + k] = ex;
+        ex += z4[k];
+      }
+    } else if (warp < 2u) {
+      // level l, half h = warp: merge r1 = 2R + h, positions [lo, lo + cnt)
+      const uint32_t h = warp;
+      const uint32_t lo = h ? lo1 : lo0;
+      const uint32_t cnt = h ? cnt1 : cnt0;
+      const uint32_t r1 = 2u * R + h;
+      const MergeBounds mb1 = merge_bounds(a1, r1);
+      const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
+      const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
+      const uint32_t n12 = N1 - n11;
+      const uint4 mi1 = a1.minfo[r1];
+      const uint32_t T1 = mi1.x;
+      const uint32_t abit1 = (mi1.y == n11) ? 1u : 0u;
+      const uint32_t qe = min(lo + cnt, T1);  // [lo, qe): interleave positions
+      const uint32_t blo = lo >> 7;
+      const uint32_t nblk = qe > lo ? min(((qe + 127u) >> 7) - blo, kPairW / 4u) : 0u;
+      const uint64_t row = static_cast<uint64_t>(r1) * a1.J;
+      // zeros before block blo: the chunk prefix plus the chunk's earlier blocks
+      uint32_t zb = 0;
+      if (nblk) {
+        const uint32_t b = (blo & ~31u) + lane;
+        if (b < blo) zb = a1.zb[row * 32u + b];
+      }
+      zb = warp_sum(zb);
+      const uint32_t zbase = nblk ? a1.zc[row + (blo >> 5)] + zb : 0u;
+      for (uint32_t k = lane; k < nblk; k += 32u) {
+        const uint4 c = coin_block(a1.key, a1.level, r1, blo + k);
+        cw1[h][4u * k + 0u] = c.x;
+        cw1[h][4u * k + 1u] = c.y;
+        cw1[h][4u * k + 2u] = c.z;
+        cw1[h][4u * k + 3u] = c.w;
+      }
+      __syncwarp();
+      // zeros before each word (merge-relative): lane takes words 5*lane .. 5*lane+4
+      {
+        const uint32_t nw = 4u * nblk;
+        uint32_t z5[5], zs = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 5u; ++k) {
+          const uint32_t wi = 5u * lane + k;
+          z5[k] = wi < nw ? static_cast<uint32_t>(__popc(~cw1[h][wi])) : 0u;
+          zs += z5[k];
+        }
+        uint32_t ex = zbase + warp_inclusive_scan(zs) - zs;
+#pragma unroll
+        for (uint32_t k = 0; k < 5u; ++k) {
+          const uint32_t wi = 5u * lane + k;
+          if (wi < kPairW) zw1[h][wi] = ex;
+          ex += z5[k];
+        }
+      }
+      // exception bit words for global positions [s1 + lo, s1 + lo + cnt)
+      const uint32_t g_lo = static_cast<uint32_t>(mb1.s) + lo;
+      const uint32_t nxw = cnt ? ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5) : 0u;
+      const uint64_t nbw = (a1.n + 31u) >> 5;
+      for (uint32_t wi = lane; wi < nxw && wi < kPairW; wi += 32u) {
+        const uint64_t bw = (g_lo >> 5) + wi;
+        xb1[h][wi] = bw < nbw ? pa.x.bits[bw] : 0u;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        uint32_t Tc1 = 0, zT1 = 0, Zlo = 0, za, na, ob, nb;
+        if (lo >= T1) {
+          za = abit1 ? 0u : lo - n12;
+          ob = abit1 ? lo - n11 : 0u;
+          na = abit1 ? 0u : cnt;
+          nb = abit1 ? cnt : 0u;
+        } else {
+          auto zpref = [&](uint32_t q) {
+            const uint32_t wi = min((q >> 5) - 4u * blo, kPairW - 1u);
+            return zw1[h][wi] + static_cast<uint32_t>(__popc(~cw1[h][wi] & low_mask(q & 31u)));
+          };
+          Zlo = zpref(lo);
+          const uint32_t Zqe = (qe == T1) ? mi1.y : zpref(qe);
+          Tc1 = qe - lo;
+          zT1 = Zqe - Zlo;
+          const uint32_t rest = lo + cnt - qe;
+          za = Zlo;
+          ob = lo - Zlo;
+          na = zT1 + (abit1 ? 0u : rest);
+          nb = (Tc1 - zT1) + (abit1 ? rest : 0u);
+        }
+        // (the runs stay inside their halves even for an inconsistent plan)
+        za = min(za, n11);
+        na = min(na, n11 - za);
+        ob = min(ob, n12);
+        nb = min(nb, n12 - ob);
+        hs[h][0] = lo;
+        hs[h][1] = cnt;
+        hs[h][2] = Tc1;
+        hs[h][3] = zT1;
+        hs[h][4] = abit1;
+        hs[h][5] = blo;
+        hs[h][6] = static_cast<uint32_t>(mb1.s) + za;    // first half's run (input index)
+        hs[h][7] = na;
+        hs[h][8] = static_cast<uint32_t>(mb1.mid) + ob;  // second half's run (input index)
+        hs[h][9] = nb;
+        hs[h][10] = g_lo;
+        hs[h][11] = Zlo;
+      }
+    }
+    __syncthreads();
+    // stage the four input runs, each at its own 16-byte phase
+    auto phase_of = [](const E *p) {
+      return static_cast<uint32_t>((reinterpret_cast<uintptr_t>(p) & 15u) / sizeof(E));
+    };
+    auto up = [](uint32_t x) { return ((x + kV - 1u) / kV) * kV; };
+    const E *const sa0 = in + hs[0][6];
+    const E *const sb0 = in + hs[0][8];
+    const E *const sa1 = in + hs[1][6];
+    const E *const sb1 = in + hs[1][8];
+    const uint32_t offA0 = phase_of(sa0);
+    const uint32_t offB0 = up(offA0 + hs[0][7]) + phase_of(sb0);
+    const uint32_t offA1 = up(offB0 + hs[0][9]) + phase_of(sa1);
+    const uint32_t offB1 = up(offA1 + hs[1][7]) + phase_of(sb1);
+    stage_run(sruns + offA0, sa0, min(hs[0][7], kRunBuf - min(offA0, kRunBuf)));
+    stage_run(sruns + offB0, sb0, min(hs[0][9], kRunBuf - min(offB0, kRunBuf)));
+    stage_run(sruns + offA1, sa1, min(hs[1][7], kRunBuf - min(offA1, kRunBuf)));
+    stage_run(sruns + offB1, sb1, min(hs[1][9], kRunBuf - min(offB1, kRunBuf)));
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    // level l: the two ranges into svals (half 0 at 0, half 1 at voff1), eight positions a thread
+    const uint32_t voff1 = (cnt0 + kStageGroup - 1u) & ~(kStageGroup - 1u);
+    {
+      const uint32_t ng0 = (cnt0 + kStageGroup - 1u) / kStageGroup;
+      const uint32_t ng = ng0 + (cnt1 + kStageGroup - 1u) / kStageGroup;
+      for (uint32_t g = tid; g < ng; g += kStageThreads) {
+        const uint32_t h = g < ng0 ? 0u : 1u;
+        const uint32_t p0 = kStageGroup * (h ? g - ng0 : g);
+        const uint32_t lo = hs[h][0], Tc1 = hs[h][2], zT1 = hs[h][3], abit1 = hs[h][4];
+        uint32_t pa, pb, bits;
+        if (p0 < Tc1) {
+          const uint32_t q0 = lo + p0;
+          const uint32_t u = min((q0 >> 5) - 4u * hs[h][5], kPairW - 1u);
+          const uint32_t sh = q0 & 31u;
+          const uint32_t w0 = cw1[h][u];
+          pa = zw1[h][u] + static_cast<uint32_t>(__popc(~w0 & low_mask(sh))) - hs[h][11];
+          pb = p0 - pa;
+          bits = __funnelshift_r(w0, cw1[h][u + 1u], sh);
+        } else {
+          pa = zT1 + (p0 - Tc1) * (1u - abit1);
+          pb = (Tc1 - zT1) + (p0 - Tc1) * abit1;
+          bits = 0u;
+        }
+        pa = min((h ? offA1 : offA0) + pa, kRunBuf - kStageGroup);
+        pb = min((h ? offB1 : offB0) + pb, kRunBuf - kStageGroup);
+        uint32_t v[kStageGroup];
+#pragma unroll
+        for (uint32_t i = 0; i < kStageGroup; ++i) {
+          const uint32_t bit = (p0 + i < Tc1) ? ((bits >> i) & 1u) : abit1;
+          v[i] = sruns[bit ? pb : pa];
+          pa += bit ^ 1u;
+          pb += bit;
+        }
+        uint4 *const dst = reinterpret_cast<uint4 *>(svals + (h ? voff1 : 0u) + p0);
+        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+      }
+    }
+    __syncthreads();
+    // level l's tail moves: the element at an exception position comes from the exception hash
+    {
+      const uint32_t hmask = (1u << pa.x.hbits) - 1u;
+      for (uint32_t wc = tid; wc < 2u * kPairW; wc += kStageThreads) {
+        const uint32_t h = wc >= kPairW ? 1u : 0u;
+        const uint32_t wi = wc - h * kPairW;
+        const uint32_t cnt = hs[h][1];
+        if (cnt == 0u) continue;
+        const uint32_t g_lo = hs[h][10];
+        const uint32_t nxw = ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5);
+        if (wi >= nxw) continue;
+        uint32_t xbits = xb1[h][wi];
+        while (xbits) {
+          const uint32_t b = __ffs(static_cast<int>(xbits)) - 1u;
+          xbits &= xbits - 1u;
+          const uint32_t gq = (((g_lo >> 5) + wi) << 5) + b;
+          if (gq < g_lo || gq >= g_lo + cnt) continue;
+          uint32_t slot = xhash_slot(gq, pa.x.hbits);
+          uint32_t xs = 0u;
+          for (uint32_t probe = 0; probe <= hmask; ++probe) {
+            const uint32_t key = pa.x.keys[slot];
+            if (key == gq) {
+              xs = pa.x.vals[slot];
+              break;
+            }
+            if (key == 0xFFFFFFFFu) break;
+            slot = (slot + 1u) & hmask;
+          }
+          svals[(h ? voff1 : 0u) + (gq - g_lo)] = in[xs < a1.n ? xs : 0u];
+        }
+      }
+    }
+    __syncthreads();
+    // level l+1: outputs placed from the two ranges, in groups of eight aligned to 16 bytes of
+    // the output (group 0: the head before the first aligned one)
+    E *const C = out + mb2.s + t0;
+    const uint32_t cph = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(C) & 15u) / sizeof(E));
+    const uint32_t hd = min(len, (kV - cph) % kV);
+    const uint32_t ngroups = 1u + (len - hd + kStageGroup - 1u) / kStageGroup;
+    for (uint32_t gi = tid; gi < ngroups; gi += kStageThreads) {
+      const uint32_t p0 = gi == 0u ? 0u : hd + kStageGroup * (gi - 1u);
+      const uint32_t cnt = gi == 0u ? hd : min(kStageGroup, len - p0);
+      if (cnt == 0u) continue;
+      uint32_t pa2, pb2, bits;
+      if (p0 < Tc2) {
+        const uint32_t u = p0 >> 5, sh = p0 & 31u;
+        const uint32_t w0 = cw2[u];
+        pa2 = zw2[u] + static_cast<uint32_t>(__popc(~w0 & low_mask(sh)));
+        pb2 = p0 - pa2;
+        bits = __funnelshift_r(w0, cw2[u + 1u], sh);
+      } else {
+        pa2 = zT2 + (p0 - Tc2) * (1u - abit2);
+        pb2 = (Tc2 - zT2) + (p0 - Tc2) * abit2;
+        bits = 0u;
+      }
+      pa2 = min(pa2, kValBuf - kStageGroup);
+      pb2 = min(voff1 + pb2, kValBuf - kStageGroup);
+      E v[kStageGroup];
+#pragma unroll
+      for (uint32_t i = 0; i < kStageGroup; ++i) {
+        const uint32_t bit = (p0 + i < Tc2) ? ((bits >> i) & 1u) : abit2;
+        v[i] = svals[bit ? pb2 : pa2];
+        pa2 += bit ^ 1u;
+        pb2 += bit;
+      }
+      if (gi != 0u && cnt == kStageGroup) {
+        uint4 *const dst = reinterpret_cast<uint4 *>(C + p0);
+        dst[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_uint4(v[4], v[5], v[6], v[7]);
+      } else {
+#pragma unroll
+        for (uint32_t i = 0; i < kStageGroup; ++i)
+          if (i < cnt) C[p0 + i] = v[i];
+      }
+    }
+    __syncthreads();  // the buffers are reused by the next chunk
+  }
+}
+
 template <typename E>
 __global__ void __launch_bounds__(kThreads) copy_kernel(LevelArgs a) {
   if (gated_off(a)) return;
@@ -1121,7 +1445,10 @@ cudaError_t pair_data_t(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv
   pa.x.hbits = lv1.xhbits;
   const uint64_t nchunks2 = static_cast<uint64_t>(lv2.M) * lv2.J;
   timed(p.prof, kKindPairGather, s, [&] {
-    pair_gather_kernel<E><<<grid_for(nchunks2, 1, 1u << 20), kThreads, 0, s>>>(pa);
+    if constexpr (sizeof(E) == 4)
+      pair_staged_kernel<<<grid_for(nchunks2, 1, 1u << 20), kStageThreads, 0, s>>>(pa);
+    else
+      pair_gather_kernel<E><<<grid_for(nchunks2, 1, 1u << 20), kThreads, 0, s>>>(pa);
   });
   // unfused fallback (each kernel returns at once unless level l overflowed): level l from X
   // into out with its tail in order, level l+1 from out back into X
