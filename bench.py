@@ -156,9 +156,10 @@ def measured_peaks() -> dict:
 
 
 # DRAM bytes (read + written) per element of one gather launch, from an ncu capture of the
-# gather kernel on a smaller case with inputs above L2 (perm 2^26, records 2^24 + 17), scaled to
-# a full launch by the elements it processes
-GATHER_TRAFFIC_PER_ELEM = {4: 7.311, 16: 28.71}
+# gather kernels on a smaller case with inputs above L2 (perm 2^26: the staged gather of 4-byte
+# elements; records 2^24 + 17: the 16-byte gather), scaled to a full launch by the elements it
+# processes
+GATHER_TRAFFIC_PER_ELEM = {4: 7.182, 16: 28.71}
 
 
 def run_ours(args, world, rank, local):
