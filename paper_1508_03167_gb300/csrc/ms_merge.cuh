@@ -158,6 +158,35 @@ __device__ __forceinline__ bool draw_first_word(uint32_t word, uint32_t R, uint3
   return false;
 }
 
+// draw_first_word with the slice width b (and mask, 2b, 3b) computed by the caller, for a run of
+// positions that share it: R - 1 in [4q, 4q + 3] with q >= 1 never crosses a power of two
+// (those of 4 and above are multiples of 4), so one quad of Algorithm 1's positions shares b.
+__device__ __forceinline__ bool draw_first_word_b(uint32_t word, uint32_t R, uint32_t b,
+                                                  uint32_t mask, uint32_t b2, uint32_t b3,
+                                                  uint32_t &x) {
+  const uint32_t v0 = word & mask;
+  const uint32_t v1 = __funnelshift_rc(word, 0u, b) & mask;
+  const uint32_t v2 = __funnelshift_rc(word, 0u, b2) & mask;
+  const uint32_t v3 = __funnelshift_rc(word, 0u, b3) & mask;
+  const bool a0 = v0 < R;
+  const bool a1 = b <= 16u && v1 < R;
+  const bool a2 = b <= 10u && v2 < R;
+  const bool a3 = b <= 8u && v3 < R;
+  x = a0 ? v0 : (a1 ? v1 : (a2 ? v2 : v3));
+  if (a0 | a1 | a2 | a3) return true;
+  if (b <= 6u) {
+    const uint32_t slices = 32u / b;
+    for (uint32_t u = 4; u < slices; ++u) {
+      const uint32_t v = (word >> (u * b)) & mask;
+      if (v < R) {
+        x = v;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
 // Algorithm 1 (descending Fisher-Yates) on one base block of L elements in shared memory:
 // for i = L-1 .. 1, swap blk[i] with blk[j], j uniform in {0..i} from the LEAF stream of block
 // `id` at position i. Positions go in quads (one Philox block serves four of them), and the

@@ -49,13 +49,14 @@ __device__ __forceinline__ uint32_t warp_exclusive(uint32_t v, uint32_t *total) 
 
 // Control data of one merge level (two sets: the control warp builds level l+1's while the
 // data warp finishes level l): (coin word, zero prefix) pairs, tail draws, and per merge its
-// size, break step, half bases, leftover base, first word and first tail draw.
+// size, break step, half bases, leftover base, first word, first tail draw and first tail quad;
+// then whether the tail draws are made ahead and how many quads of them there are.
 struct LevelCtl {
   uint2 *cz;
   uint16_t *mv;
   uint32_t *m;  // kTileCtlWords words: 7 arrays of 32 and the flag "tail draws made"
 };
-constexpr uint32_t kTileCtlWords = 7u * 32u + 1u;
+constexpr uint32_t kTileCtlWords = 8u * 32u + 2u;
 __device__ __forceinline__ uint32_t *ctl_N(const LevelCtl &c) { return c.m; }
 __device__ __forceinline__ uint32_t *ctl_T(const LevelCtl &c) { return c.m + 32; }
 __device__ __forceinline__ uint32_t *ctl_a(const LevelCtl &c) { return c.m + 64; }
@@ -63,11 +64,13 @@ __device__ __forceinline__ uint32_t *ctl_b(const LevelCtl &c) { return c.m + 96;
 __device__ __forceinline__ uint32_t *ctl_lb(const LevelCtl &c) { return c.m + 128; }
 __device__ __forceinline__ uint32_t *ctl_woff(const LevelCtl &c) { return c.m + 160; }
 __device__ __forceinline__ uint32_t *ctl_koff(const LevelCtl &c) { return c.m + 192; }
-__device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m + 224; }
+__device__ __forceinline__ uint32_t *ctl_qoff(const LevelCtl &c) { return c.m + 224; }
+__device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m + 256; }
+__device__ __forceinline__ uint32_t *ctl_qtot(const LevelCtl &c) { return c.m + 257; }
 
 // The data-independent part of merge level lv of the tile, by one warp: coin words, zero
-// prefixes and break step of every merge, the leftover base, and the tail draws. G = 32 / R
-// lanes per merge: lane (r, sub) = (lane / G, lane % G).
+// prefixes and break step of every merge, the leftover base, and the offsets of the tail draws
+// (made by tail_draws). G = 32 / R lanes per merge: lane (r, sub) = (lane / G, lane % G).
 __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
                                         const uint32_t *boff, uint64_t k0, uint32_t lv,
                                         uint32_t Sin, uint32_t lane, uint2 *czb, uint16_t *mvb,
@@ -137,8 +140,9 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   if (T < N && ((cz[T >> 5].x >> (T & 31u)) & 1u) == 0u) lb = Bb - n1;
   const uint32_t K = N - T;
   const uint32_t Q = K ? ((N - 1u) >> 2) - (T >> 2) + 1u : 0u;
-  uint32_t Ktot;
+  uint32_t Ktot, Qtot;
   const uint32_t koff = __shfl_sync(kFullMask, warp_exclusive(sub == 0u ? K : 0u, &Ktot), leader);
+  const uint32_t qoff = __shfl_sync(kFullMask, warp_exclusive(sub == 0u ? Q : 0u, &Qtot), leader);
   if (sub == 0u) {
     ctl_N(c)[r] = N;
     ctl_T(c)[r] = T;
@@ -147,28 +151,57 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
     ctl_lb(c)[r] = lb;
     ctl_woff(c)[r] = woff;
     ctl_koff(c)[r] = koff;
+    ctl_qoff(c)[r] = qoff;
   }
-  const bool drawn = Ktot <= tcap;
-  if (lane == 0) *ctl_drawn(c) = drawn ? 1u : 0u;
-  // tail draws, one Philox block per four consecutive positions (lane (r, sub): quads sub,
-  // sub + G, ... of merge r's tail); else the tails draw in their loop
-  if (drawn) {
-    for (uint32_t gq = sub; gq < Q; gq += G) {
-      const uint32_t quad = (T >> 2) + gq;
-      const uint32_t id = idbase + r;
-      const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lv, 0u), key);
+  if (lane == 0) {
+    *ctl_drawn(c) = Ktot <= tcap ? 1u : 0u;  // else the tails draw in their loop
+    *ctl_qtot(c) = Qtot;
+  }
+}
+
+// The tail draws of level lv (one Philox block per four consecutive positions of a merge's
+// tail), made ahead of the data by nthreads threads (t: this thread's index among them); quad x
+// of the level belongs to the last merge whose first quad is at most x.
+__device__ __noinline__ void tail_draws(uint2 key, uint32_t d, uint32_t lv, uint64_t k0,
+                                        uint32_t t, uint32_t nthreads, uint16_t *mvb,
+                                        const uint32_t *mb) {
+  LevelCtl c;
+  c.cz = nullptr;
+  c.mv = mvb;
+  c.m = const_cast<uint32_t *>(mb);
+  if (*ctl_drawn(c) == 0u) return;
+  const uint32_t R = 1u << (d - lv - 1u);
+  const uint32_t idbase = static_cast<uint32_t>(k0 >> (lv + 1u));
+  const uint32_t Qtot = *ctl_qtot(c);
+  const uint32_t *const qoff = ctl_qoff(c);
+  for (uint32_t x = t; x < Qtot; x += nthreads) {
+    uint32_t lo = 0, hi = R;
+    while (hi - lo > 1u) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (qoff[mid] <= x) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t r = lo;
+    const uint32_t T = ctl_T(c)[r], N = ctl_N(c)[r], koff = ctl_koff(c)[r];
+    const uint32_t quad = (T >> 2) + (x - qoff[r]);
+    const uint32_t id = idbase + r;
+    const uint4 w0 = philox10(make_uint4(quad, id, (kTagTail << 16) | lv, 0u), key);
 #pragma unroll
-      for (uint32_t v = 0; v < 4u; ++v) {
-        const uint32_t i = 4u * quad + v;
-        if (i >= T && i < N) {
-          uint32_t x;
-          if (!draw_first_word(pick_word(w0, v), i + 1u, x))
-            x = draw_continue(key, kTagTail, lv, id, i, i + 1u);
-          c.mv[koff + (i - T)] = static_cast<uint16_t>(x);
-        }
+    for (uint32_t v = 0; v < 4u; ++v) {
+      const uint32_t i = 4u * quad + v;
+      if (i >= T && i < N) {
+        uint32_t xv;
+        if (!draw_first_word(pick_word(w0, v), i + 1u, xv))
+          xv = draw_continue(key, kTagTail, lv, id, i, i + 1u);
+        c.mv[koff + (i - T)] = static_cast<uint16_t>(xv);
       }
     }
   }
+}
+
+// named barrier 1 among the nthreads threads of the warps that build a level's control data
+__device__ __forceinline__ void control_barrier(uint32_t nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 // Four warps per tile, in three roles that rotate from tile to tile (the warps of a CTA sit on
@@ -233,6 +266,9 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
 #pragma unroll 2
       for (uint32_t qd = warp; qd < nq; qd += kTileWarps) {
         const uint4 blk = philox10(make_uint4(qd, id, kTagLeaf << 16, 0u), a.key);
+        // slice width of the quad's ranges (positions 1..3 of quad 0 take the general draw)
+        const uint32_t qb = 32u - __clz(4u * qd + 1u);  // (= bits of 4qd for qd >= 1)
+        const uint32_t qmask = 0xFFFFFFFFu >> (32u - qb);
 #pragma unroll
         for (uint32_t v = 0; v < 4u; ++v) {
           const uint32_t pos = 4u * qd + v;
@@ -240,7 +276,10 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
             A[pos] = static_cast<uint16_t>(off + pos);
             if (pos >= 1u) {
               uint32_t x;
-              if (draw_first_word(pick_word(blk, v), pos + 1u, x)) {
+              const uint32_t word = pick_word(blk, v);
+              const bool ok = qd ? draw_first_word_b(word, pos + 1u, qb, qmask, 2u * qb, 3u * qb, x)
+                                 : draw_first_word(word, pos + 1u, x);
+              if (ok) {
                 D[pos] = static_cast<uint16_t>(x);
               } else if (nf < kFailPerThread) {
                 F[nf++] = pos;
@@ -281,9 +320,12 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
         i -= 4u;
       }
       for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
-    } else if (role == 1u) {
+    } else {
+      // roles 1 and 3: level 0's control data, then its tail draws shared
       const LevelCtl c0 = ctl(0u);
-      level_setup(a.key, a.d, a.tcap, boff, k0, 0u, a.P, lane, c0.cz, c0.mv, c0.m);
+      if (role == 1u) level_setup(a.key, a.d, a.tcap, boff, k0, 0u, a.P, lane, c0.cz, c0.mv, c0.m);
+      control_barrier(64u);
+      tail_draws(a.key, a.d, 0u, k0, (role == 1u ? 0u : 32u) + lane, 64u, c0.mv, c0.m);
     }
     __syncthreads();
 
@@ -359,9 +401,13 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
               swap_smem(Cq, i, draw_uniform(a.key, kTagTail, lv, id, i, i + 1u, memo));
           }
         }
-      } else if (role == 1u && lv + 1u < a.d) {
+      } else if (lv + 1u < a.d) {
+        // roles 1, 2, 3: level lv+1's control data (role 1), then its tail draws shared
         const LevelCtl cn = ctl((lv + 1u) & 1u);
-        level_setup(a.key, a.d, a.tcap, boff, k0, lv + 1u, Sout, lane, cn.cz, cn.mv, cn.m);
+        if (role == 1u)
+          level_setup(a.key, a.d, a.tcap, boff, k0, lv + 1u, Sout, lane, cn.cz, cn.mv, cn.m);
+        control_barrier(96u);
+        tail_draws(a.key, a.d, lv + 1u, k0, (role - 1u) * 32u + lane, 96u, cn.mv, cn.m);
       }
       __syncthreads();
     }
