@@ -361,6 +361,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     p.off_pdst = off;   off += round_up(2 * kcap_max * 4, 256);
     p.off_psrc = off;   off += round_up(2 * kcap_max * 4, 256);
     p.off_ptmp = off;   off += round_up(2 * kcap_max * w, 256);
+    p.off_ostart = off; off += round_up((kcap_max / 1024 + 2) * 4, 256);
     p.plan_set_bytes = off - base;
     // a unit (a level or a fused pair) uses two plan sets; two units' sets, so that the next
     // unit's plan can be built during a unit's data pass
@@ -499,6 +500,7 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   b.pdst = reinterpret_cast<uint32_t *>(ps + p.off_pdst);
   b.psrc = reinterpret_cast<uint32_t *>(ps + p.off_psrc);
   b.ptmp = ps + p.off_ptmp;
+  b.ostart = reinterpret_cast<uint32_t *>(ps + p.off_ostart);
   return b;
 }
 

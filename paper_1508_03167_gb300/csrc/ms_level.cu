@@ -46,6 +46,7 @@ struct LevelArgs {
   uint32_t *pdst;
   uint32_t *psrc;
   void *ptmp;
+  uint32_t *ostart;        // first merge of every 1024 tail steps (kscan), then a sentinel
   uint8_t *zb;             // optional: zero coins per 128-step block (count_kernel)
   const uint32_t *gate;    // optional: the kernel runs only if (*gate != 0) == gate_on
   uint32_t gate_on;
@@ -231,12 +232,20 @@ __global__ void __launch_bounds__(1024) kscan_kernel(LevelArgs a) {
     const uint32_t k = r < a.M ? a.minfo[r].w : 0u;
     uint32_t total;
     const uint32_t excl = block_exclusive_scan(k, scratch, &total);
-    if (r < a.M) a.minfo[r].z = carry + excl;
+    if (r < a.M) {
+      const uint32_t koff = carry + excl;
+      a.minfo[r].z = koff;
+      // merge r owns the tail steps [koff, koff + k): record it for every 1024-step block that
+      // starts inside (within the capacity; beyond it the level runs its tails in order)
+      for (uint32_t b = (koff + 1023u) >> 10; 1024ull * b < koff + k && 1024ull * b < a.kcap; ++b)
+        a.ostart[b] = r;
+    }
     carry += total;
   }
   if (threadIdx.x == 0) {
     a.ctrl[0] = carry;
     a.ctrl[1] = (carry > a.kcap || (a.flags & 1u)) ? 1u : 0u;
+    if (carry <= a.kcap) a.ostart[(carry + 1023u) >> 10] = a.M - 1u;  // sentinel
   }
 }
 
@@ -252,7 +261,11 @@ __device__ __forceinline__ unsigned long long tail_key(uint32_t r, uint32_t pos)
 // merge owning tail step g: the largest r whose tail offset is <= g (offsets are
 // non-decreasing; merges with an empty tail share their successor's offset and are skipped)
 __device__ __forceinline__ uint32_t owner_merge(const LevelArgs &a, uint32_t g) {
-  uint32_t lo = 0, hi = a.M;  // invariant: offset[lo] <= g, and offset[hi] > g or hi == M
+  // the owner lies between the owners of the 1024-step block starts around g (kscan's table)
+  uint32_t lo = min(a.ostart[g >> 10], a.M - 1u);
+  uint32_t hi = min(a.ostart[(g >> 10) + 1u] + 1u, a.M);
+  if (hi <= lo) hi = a.M;
+  // invariant: offset[lo] <= g, and offset[hi] > g or hi == M
   while (hi - lo > 1u) {
     const uint32_t mid = (lo + hi) >> 1;
     if (a.minfo[mid].z <= g) lo = mid;
@@ -1366,6 +1379,7 @@ LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.pdst = b.pdst;
   a.psrc = b.psrc;
   a.ptmp = b.ptmp;
+  a.ostart = b.ostart;
   a.zb = nullptr;
   a.gate = nullptr;
   a.gate_on = 0;

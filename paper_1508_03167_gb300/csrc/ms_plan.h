@@ -108,7 +108,7 @@ struct Plan {
   // levels comes in plan_sets copies, plan_set_bytes apart: level j of the global levels uses
   // set j % plan_sets, so the plan of the next level can be built while this one streams.
   size_t off_buf = 0, off_zc = 0, off_minfo = 0, off_ctrl = 0, off_mv = 0, off_hkeys = 0,
-         off_hvals = 0, off_pdst = 0, off_psrc = 0, off_ptmp = 0, ws_bytes = 0;
+         off_hvals = 0, off_pdst = 0, off_psrc = 0, off_ptmp = 0, off_ostart = 0, ws_bytes = 0;
   size_t plan_set_bytes = 0;
   uint32_t plan_sets = 0;
   // exception structures of a pair's first level (offsets within one copy; one copy per two
@@ -141,6 +141,7 @@ struct Buffers {
   uint32_t *pdst;
   uint32_t *psrc;
   void *ptmp;
+  uint32_t *ostart;  // first merge of every 1024 tail steps of a level (kscan), + one sentinel
 };
 
 // Lets `kern` launch with `smem` bytes of dynamic shared memory. The attribute is process-wide,
