@@ -258,3 +258,34 @@ def test_single_call_replays_from_a_cuda_graph():
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint32), want_p)
         assert np.array_equal(x.cpu().numpy().view(rec.dtype).reshape(rec.shape), want_r)
+
+
+@pytest.mark.parametrize("fd", [0, 5])
+def test_element_aligned_buffers(fd):
+    """The API asks only for w-aligned data: buffers 4 (w = 4) or 8 (w = 8) bytes past a 16-byte
+    boundary take the element-wise heads and tails of the staged copies and 16-byte stores, in
+    every pass that lands in the caller's buffer."""
+    torch = _torch()
+    stream = torch.cuda.current_stream().cuda_stream
+    for n, B in ((262147, 256), (100003, 64)):
+        want, _ = oracle.perm(n, 5, B)
+        p = ms.params(B, fd, 0)
+        raw = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+        ws = torch.empty(ms.ms_workspace_bytes(n, 4, p), dtype=torch.uint8, device="cuda")
+        st = ms.ms_perm(raw.data_ptr() + 4, n, 5, ws.data_ptr(), ws.numel(), p, stream)
+        assert st == ms.MS_OK, ms.ms_status_string(st)
+        torch.cuda.synchronize()
+        got = raw[1:n + 1].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), (n, B, fd)
+        for w, off in ((4, 4), (8, 8), (8, 24)):
+            arr = inputs.values_u64(n, 3) if w == 8 else inputs.identity_u32(n) * np.uint32(2654435761)
+            want_s, _ = oracle.shuffle(arr, 5, B)
+            nb = arr.nbytes
+            buf = torch.zeros(nb + 64, dtype=torch.uint8, device="cuda")
+            buf[off:off + nb] = torch.from_numpy(arr.view(np.uint8).copy()).cuda()
+            ws = torch.empty(ms.ms_workspace_bytes(n, w, p), dtype=torch.uint8, device="cuda")
+            st = ms.ms_shuffle(buf.data_ptr() + off, n, w, 5, ws.data_ptr(), ws.numel(), p, stream)
+            assert st == ms.MS_OK, ms.ms_status_string(st)
+            torch.cuda.synchronize()
+            got_s = buf[off:off + nb].cpu().numpy().view(arr.dtype)
+            assert np.array_equal(got_s, want_s), (n, B, fd, w, off)
