@@ -5,13 +5,17 @@
 //   count    zero coins per 4096-step chunk of every merge (Philox only, no array traffic);
 //   scan     per merge: exclusive prefix of the chunk counts and the break step T, where a coin
 //            first asks for an exhausted half (Algorithm 3's first loop);
-//   kscan    prefix of the tail lengths N - T over the level's merges;
+//   kscan    prefix of the tail lengths N - T over the level's merges, and the first merge of
+//            every 1024 tail steps (so a tail step finds its merge in a few probes);
 //   insert   tail draws m_i (i = T..N-1, uniform in {0..i}) into a hash table keyed by
 //            (merge, target position);
 //   resolve  replays the random insertions (Algorithm 3's second loop) on indices only: every
 //            displaced element's trajectory gives one (destination, source) patch;
 //   gather   the streaming pass: out[s+t] = coin t ? B[t - Z_t] : A[Z_t] for t < T, the
-//            remainder of the non-exhausted half for t >= T (coalesced reads of both halves);
+//            remainder of the non-exhausted half for t >= T. For 4- and 8-byte elements each
+//            4096-step chunk first copies its two source runs into shared memory (16-byte
+//            asynchronous copies), then places eight outputs a thread; 16-byte records are
+//            read straight from both halves (coalesced);
 //   patch    two small kernels apply the patches (read all sources, then write).
 // If a level's tails exceed the planned capacity, a sequential per-merge tail (in place on the
 // output) runs instead of insert/resolve/patch; the result is the same.

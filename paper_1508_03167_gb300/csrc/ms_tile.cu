@@ -13,8 +13,8 @@
 //     the stable interleave (a lane places eight consecutive positions, walking the two
 //     halves with one index each), the tail draws, and the random insertions of Algorithm 3's
 //     second loop in order, one lane per merge. The data-independent part of level l+1 (coins,
-//     prefixes, break steps, tail draws) is built by one warp while another runs level l's
-//     tails;
+//     prefixes, break steps by one warp, then the tail draws shared by the three warps that do
+//     not run the tails) is built while the data warp runs level l's tails;
 //   * one store of the tile.
 // Block k of the tile sits at k*P in the first buffer (P = 2 mod 64, so the 32 lanes at one
 // position of their blocks touch 32 different banks); merge r of level l writes its output at
