@@ -34,8 +34,8 @@
  * (the scratch is about 0.4*n*w for 4-byte elements at n = 2^30).
  *
  * Streams. Each call enqueues on the caller's stream; the data-independent plan of the global
- * merge levels runs on a second, low-priority stream paired with the caller's (created on first
- * use, ordered with events) unless MS_FLAG_SINGLE_STREAM is set.
+ * merge levels runs on a second stream at the caller's priority, paired with it (created on
+ * first use, ordered with events) unless MS_FLAG_SINGLE_STREAM is set.
  *
  * Errors. Argument errors are returned synchronously. Launch failures return MS_ERR_CUDA
  * (the CUDA error is not cleared). Nothing traps on the device.
@@ -95,9 +95,10 @@ typedef void *ms_stream_t;
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level
-                                        runs on a second, low-priority stream paired with the
-                                        caller's, one or two levels ahead; make the first call
-                                        on a stream before capturing it into a CUDA graph */
+                                        runs on a second stream, at the caller's priority,
+                                        paired with the caller's, one or two levels ahead; make
+                                        the first call on a stream before capturing it into a
+                                        CUDA graph */
 
 typedef struct {
   uint32_t B;          /* cutoff: base blocks have at most B+1 elements (1 <= B <= MS_MAX_B);

@@ -505,11 +505,12 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
 }
 
 // The plan stream paired with a caller's stream (per device, created on first use), with the
-// events of the two-set pipeline. It runs at the lowest priority: its short kernels fill the
-// SMs between the data pass's blocks instead of displacing them (measured on GB300: at the
-// highest priority the plan kernels slowed the 128-thread staged gathers of a 2^30 perm by
-// more than they saved). A mutex serialises the enqueue of one call's pipeline per caller
-// stream.
+// events of the two-set pipeline. It runs at the caller's priority (the lowest for a default
+// stream): its short kernels fill the SMs between the data pass's blocks instead of displacing
+// them (measured on GB300: one priority above the data pass, the plan kernels slowed the
+// 128-thread staged gathers of a 2^30 perm by more than they saved), and a call made on a
+// high-priority stream keeps its plans ahead of other callers' work. A mutex serialises the
+// enqueue of one call's pipeline per caller stream.
 struct PlanStream {
   int dev = -1;
   cudaStream_t caller = nullptr;
@@ -537,9 +538,9 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
     return MS_OK;
   }
   PlanStream &S = pool[used];
-  int lo = 0, hi = 0;  // (numerically, lo >= hi: lo is the lowest priority)
-  if (failed(cudaDeviceGetStreamPriorityRange(&lo, &hi))) return MS_ERR_CUDA;
-  if (failed(cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, lo)))
+  int prio = 0;
+  if (failed(cudaStreamGetPriority(caller, &prio))) return MS_ERR_CUDA;
+  if (failed(cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, prio)))
     return MS_ERR_CUDA;
   for (int k = 0; k < 2; ++k) {
     if (failed(cudaEventCreateWithFlags(&S.planned[k], cudaEventDisableTiming)) ||
