@@ -339,6 +339,18 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p_perm.B, p_rec.B)
 
+    # random bits consumed (the paper's Table 1 measure), counted on the GPU outside the timed
+    # region: n log2 n + Theta(n) for this method
+    import math
+
+    bits = {}
+    for tag, n_, B_ in (("perm", n_perm, p_perm.B), ("rec", n_rec, p_rec.B)):
+        rb = ms.random_bits(n_, SEED, device=dev, B=B_)
+        bits[tag] = {"bits_per_element": round(rb["total_bits"] / n_, 4),
+                     "log2_n": round(math.log2(n_), 4),
+                     "coin_bits": rb["coin_bits"], "leaf_bits": rb["leaf_bits"],
+                     "tail_bits": rb["tail_bits"]}
+
     line = {
         "metric": "Gelem/s",
         "value": round(value, 4),
@@ -373,6 +385,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "random_bits": bits,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -275,6 +275,24 @@ ms_status ms_perm_static(uint32_t *d_out, uint64_t n, uint64_t seed, const ms_pa
                          ms_stream_t stream);
 
 /*
+ * Random-bit accounting of ms_perm(n, seed) with parameters p (B = 0: autotuned, as ms_perm
+ * resolves it): the random-bit model of Section 1 of arXiv 1508.03167, the count its Table 1
+ * reports. Nothing is permuted; the counts follow from the coin and draw streams alone and
+ * equal the CPU oracle's for the same (n, seed, B).
+ *   h_out   host array of 8 uint64: [0] coin bits (T + 1 per merge: the coin that asks for an
+ *           exhausted half is drawn and counted), [1] bits of Algorithm 1's draws, [2] bits of
+ *           the merge tails' draws (a draw costs its tested slices times b = ceil(log2 R)),
+ *           [3] Algorithm 1's draws, [4] tail draws, [5] merges, [6] leftover positions
+ *           (sum of N - T), [7] levels c.
+ *   d_ws    device workspace of ms_random_bits_workspace(n, p) bytes, 256-byte aligned.
+ * Enqueued on stream; the call waits for it (the counts are copied to the host).
+ * Errors: MS_ERR_INVALID for bad arguments, MS_ERR_CUDA for a failed launch or copy.
+ */
+size_t ms_random_bits_workspace(uint64_t n, const ms_params *p);
+ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *p, void *d_ws,
+                         size_t ws_bytes, uint64_t *h_out, ms_stream_t stream);
+
+/*
  * Collect the timings of every launch recorded since the last reset (waits for the recorded
  * events; process-wide state, not thread-safe) and optionally reset the record.
  */

@@ -14,7 +14,7 @@ import threading
 
 __all__ = [
     "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
-    "MS_ERR_TIMEOUT", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_FLAG_SINGLE_LEVELS", "MS_FLAG_PAIR_LEVELS", "MS_FLAG_CTA_TILES", "MS_MAX_B", "ms_batch_workspace_bytes",
+    "MS_ERR_TIMEOUT", "RANDOM_BIT_FIELDS", "ms_random_bits", "ms_random_bits_workspace", "random_bits", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_FLAG_SINGLE_LEVELS", "MS_FLAG_PAIR_LEVELS", "MS_FLAG_CTA_TILES", "MS_MAX_B", "ms_batch_workspace_bytes",
     "ms_batch_prepare", "ms_batch_run", "ms_shuffle_batch", "batch_workspace", "shuffle_batch", "MsParams",
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
@@ -151,6 +151,10 @@ def lib() -> ctypes.CDLL:
         L.ms_status_string.restype = ctypes.c_char_p
         L.ms_version.argtypes = []
         L.ms_version.restype = ctypes.c_char_p
+        L.ms_random_bits_workspace.argtypes = [u64, P]
+        L.ms_random_bits_workspace.restype = sz
+        L.ms_random_bits.argtypes = [u64, u64, P, vp, sz, pu64, vp]
+        L.ms_random_bits.restype = i32
         L.ms_last_cuda_error.argtypes = []
         L.ms_last_cuda_error.restype = i32
         L.ms_last_cuda_error_string.argtypes = []
@@ -301,6 +305,38 @@ def ms_status_string(st: int) -> str:
 
 def ms_version() -> str:
     return lib().ms_version().decode()
+
+
+RANDOM_BIT_FIELDS = ("coin_bits", "leaf_bits", "tail_bits", "leaf_draws", "tail_draws",
+                     "merges", "leftover", "levels")
+
+
+def ms_random_bits_workspace(n: int, p: MsParams | None = None) -> int:
+    return int(lib().ms_random_bits_workspace(n, _p(p)))
+
+
+def ms_random_bits(n: int, seed: int, d_ws: int, ws_bytes: int, p: MsParams | None = None,
+                   stream: int = 0) -> dict:
+    """Random bits consumed by ms_perm(n, seed) with parameters p (see the header)."""
+    out = (ctypes.c_uint64 * 8)()
+    st = lib().ms_random_bits(n, seed, _p(p), d_ws, ws_bytes, out, stream)
+    if st != MS_OK:
+        raise MsError(st, "ms_random_bits")
+    d = {k: int(v) for k, v in zip(RANDOM_BIT_FIELDS, out)}
+    d["total_bits"] = d["coin_bits"] + d["leaf_bits"] + d["tail_bits"]
+    return d
+
+
+def random_bits(n: int, seed: int, device=None, **kw) -> dict:
+    """ms_random_bits with a workspace allocated by PyTorch on `device` (default cuda:0)."""
+    import torch
+
+    p = params(**kw)
+    dev = torch.device(device) if device is not None else torch.device("cuda")
+    nbytes = ms_random_bits_workspace(n, p)
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+    return ms_random_bits(n, seed, ws.data_ptr(), nbytes, p,
+                          torch.cuda.current_stream(dev).cuda_stream)
 
 
 def ms_last_cuda_error() -> tuple[int, str]:

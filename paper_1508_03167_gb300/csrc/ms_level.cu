@@ -1539,6 +1539,15 @@ cudaError_t launch_pair_data(const Plan &p, const LevelPlan &lv1, const LevelPla
   }
 }
 
+cudaError_t launch_level_breaks(const Plan &p, const LevelPlan &lv, const Buffers &b,
+                                uint64_t seed, cudaStream_t s) {
+  const LevelArgs a = level_args(p, lv, nullptr, nullptr, b, seed);
+  const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
+  count_kernel<<<grid_for(nchunks, kThreads / 32, 1u << 20), kThreads, 0, s>>>(a);
+  scan_kernel<<<grid_for(lv.M, 1, 1u << 20), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                               const Buffers &b, uint64_t seed, cudaStream_t s) {
   switch (p.w) {

@@ -177,6 +177,10 @@ cudaError_t launch_tile(const Plan &p, const void *in, void *out, bool perm, uin
 // tail draws and their replay on indices) and the data pass (streaming gather, tail patches).
 cudaError_t launch_level_plan(const Plan &p, const LevelPlan &lv, const Buffers &b, uint64_t seed,
                               cudaStream_t s);
+// The break step T (and Z_T, N - T) of every merge of one level into b.minfo (count + scan only:
+// the random-bit accounting of ms_bits.cu).
+cudaError_t launch_level_breaks(const Plan &p, const LevelPlan &lv, const Buffers &b,
+                                uint64_t seed, cudaStream_t s);
 cudaError_t launch_level_data(const Plan &p, const LevelPlan &lv, const void *in, void *out,
                               const Buffers &b, uint64_t seed, cudaStream_t s);
 // Two consecutive global levels fused into one data pass (b1: the first level's plan set, with
