@@ -78,11 +78,11 @@ bool leaf_fits(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
   return L.bytes <= kSmemLimit && L.tile_max < 65536 && d - L.dw <= 3;
 }
 
-// Shared-memory layout of the tile kernel (16-bit tile-local indices, four warps a tile): two
+// Shared-memory layout of the tile kernel (16-bit tile-local indices, eight warps a tile): two
 // buffers (the first holds block k at k*P, P = 2 mod 64 and at least the largest block; merge r
 // of level l writes at r*S[l]), then two sets of a level's (coin word, zero prefix) pairs and
 // two sets of its tail draws (which also hold the per-thread queues of second-word
-// Fisher-Yates draws: 128 threads x 8 entries x 4 bytes over both sets).
+// Fisher-Yates draws: 256 threads x 4 entries x 4 bytes over both sets).
 struct TileSmem {
   bool ok = false;
   uint32_t P = 0, buf = 0, wcap = 0, tcap = 0;

@@ -1,5 +1,5 @@
 // ms_tile.cu -- the base blocks of a tile of 2^d consecutive base blocks and the tile's first d
-// merge levels (Algorithms 1 to 3 of arXiv 1508.03167), one CTA of four warps per tile,
+// merge levels (Algorithms 1 to 3 of arXiv 1508.03167), one CTA of eight warps per tile,
 // computed on 16-bit tile-local indices in shared memory; the tile is then written once (perm:
 // the indices plus the tile's first element; shuffle: the input rows they name).
 //
@@ -26,7 +26,7 @@
 namespace msk {
 namespace {
 
-constexpr uint32_t kFailPerThread = 8;  // queued second-word draws per thread and block group
+// (kFailPerThread is defined with the CTA shape below)
 
 struct TileArgs {
   const void *in;
@@ -204,15 +204,19 @@ __device__ __forceinline__ void control_barrier(uint32_t nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// Four warps per tile, in three roles that rotate from tile to tile (the warps of a CTA sit on
-// different SM sub-partitions, which would otherwise carry unequal loads): all four make the
+// Eight warps per tile, in three roles that rotate from tile to tile (the warps of a CTA sit on
+// different SM sub-partitions, which would otherwise carry unequal loads): all of them make the
 // Fisher-Yates draws and the interleaves; the data warp runs the serial parts (Algorithm 1's
-// swaps, the merge tails) while the control warp builds the next level's control data.
-constexpr uint32_t kTileWarps = 4;
+// swaps, the merge tails) while the control warp builds the next level's coins, prefixes and
+// break steps and the other warps join it for the tail draws.
+constexpr uint32_t kTileWarps = 8;
 constexpr uint32_t kTileThreads = 32u * kTileWarps;
+constexpr uint32_t kTileMinBlocks = kTileWarps == 4u ? 5u : 4u;  // CTAs an SM the registers allow
+// queued second-word Fisher-Yates draws per thread and block group (4 KB of queues in all)
+constexpr uint32_t kFailPerThread = 32u / kTileWarps;
 
 template <typename E, bool kPerm>
-__global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(TileArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t boff[(1u << kTileMaxDepth) + 1u];
   __shared__ uint32_t ctlm[2][kTileCtlWords];
@@ -321,11 +325,12 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
       }
       for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
     } else {
-      // roles 1 and 3: level 0's control data, then its tail draws shared
+      // the other roles (1, 3, ...): level 0's control data (role 1), then its tail draws
       const LevelCtl c0 = ctl(0u);
       if (role == 1u) level_setup(a.key, a.d, a.tcap, boff, k0, 0u, a.P, lane, c0.cz, c0.mv, c0.m);
-      control_barrier(64u);
-      tail_draws(a.key, a.d, 0u, k0, (role == 1u ? 0u : 32u) + lane, 64u, c0.mv, c0.m);
+      control_barrier((kTileWarps - 2u) * 32u);
+      tail_draws(a.key, a.d, 0u, k0, (role == 1u ? 0u : role - 2u) * 32u + lane,
+                 (kTileWarps - 2u) * 32u, c0.mv, c0.m);
     }
     __syncthreads();
 
@@ -402,12 +407,13 @@ __global__ void __launch_bounds__(kTileThreads, 5) tile_kernel(TileArgs a) {
           }
         }
       } else if (lv + 1u < a.d) {
-        // roles 1, 2, 3: level lv+1's control data (role 1), then its tail draws shared
+        // every role but the data warp: level lv+1's control data (role 1), then its tail draws
         const LevelCtl cn = ctl((lv + 1u) & 1u);
         if (role == 1u)
           level_setup(a.key, a.d, a.tcap, boff, k0, lv + 1u, Sout, lane, cn.cz, cn.mv, cn.m);
-        control_barrier(96u);
-        tail_draws(a.key, a.d, lv + 1u, k0, (role - 1u) * 32u + lane, 96u, cn.mv, cn.m);
+        control_barrier((kTileWarps - 1u) * 32u);
+        tail_draws(a.key, a.d, lv + 1u, k0, (role - 1u) * 32u + lane, (kTileWarps - 1u) * 32u,
+                   cn.mv, cn.m);
       }
       __syncthreads();
     }
