@@ -43,7 +43,15 @@ def parse():
     ap.add_argument("--tile-bytes", type=int, default=0)
     ap.add_argument("--fuse-depth", type=int, default=-1,
                     help="merge levels fused into the base-block kernel (-1: autotuned)")
+    ap.add_argument("--fuse-depth-perm", type=int, default=None,
+                    help="as --fuse-depth, for the perm only")
+    ap.add_argument("--fuse-depth-rec", type=int, default=None,
+                    help="as --fuse-depth, for the records only")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--overlap", choices=["none", "equal", "perm-high", "rec-high"],
+                    default="none",
+                    help="device step: run the perm and the records one after the other on one "
+                         "stream (none), or on two streams at the given priorities")
     ap.add_argument("--serve-window", type=float, default=0.25,
                     help="seconds of 20k/s arrivals in the serving overload run")
     ap.add_argument("--serve-sub-rate", type=float, default=1500.0)
@@ -178,11 +186,17 @@ def run_ours(args, world, rank, local):
     seed = SEED + rank
     flags = ms.MS_FLAG_PROFILE
     # B = 0 resolves through the autotuner's table; the resolved parameters define the result
-    p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=args.fuse_depth,
+    fd_perm = args.fuse_depth if args.fuse_depth_perm is None else args.fuse_depth_perm
+    fd_rec = args.fuse_depth if args.fuse_depth_rec is None else args.fuse_depth_rec
+    p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=fd_perm,
                         tile_bytes=args.tile_bytes, flags=flags)
-    p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=args.fuse_depth,
+    p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=fd_rec,
                        tile_bytes=args.tile_bytes, flags=flags)
-    plan_perm = ms.ms_plan_info(n_perm, 4, p_perm)
+    # (the perm's plan, not the 4-byte shuffle's: a shuffle whose first pass is the tile kernel
+    # may fuse one level less so that this pass does not run in place)
+    plan_perm = ms.ms_plan_info(n_perm, 4, ms.params(p_perm.B, p_perm.fuse_depth,
+                                                     p_perm.flags | ms.MS_FLAG_PERM,
+                                                     p_perm.tile_bytes))
     plan_rec = ms.ms_plan_info(n_rec, 16, p_rec)
 
     out = torch.empty(n_perm, dtype=torch.int32, device=dev)
@@ -191,15 +205,37 @@ def run_ours(args, world, rank, local):
     rec = rec_host.to(dev)
     ws_rec = torch.empty(ms.ms_workspace_bytes(n_rec, 16, p_rec), dtype=torch.uint8, device=dev)
 
+    # the two calls are independent; with --overlap the records run on a second stream, forked
+    # from and joined back into the timed stream every step, so that one call's latency-bound
+    # base-block pass can overlap the other's memory-bound level passes
+    s_perm, s_rec = sh, sh
+    fork = join = None
+    if args.overlap != "none":
+        prio = {"equal": (0, 0), "perm-high": (-1, 0), "rec-high": (0, -1)}[args.overlap]
+        st_perm = torch.cuda.Stream(device=dev, priority=prio[0])
+        st_rec = torch.cuda.Stream(device=dev, priority=prio[1])
+        s_perm, s_rec = st_perm.cuda_stream, st_rec.cuda_stream
+        fork = torch.cuda.Event()
+        join = [torch.cuda.Event(), torch.cuda.Event()]
+
     def step():
+        if fork is not None:
+            fork.record(stream)
+            st_perm.wait_event(fork)
+            st_rec.wait_event(fork)
         st = ms.ms_perm(out.data_ptr(), n_perm, seed, ws_perm.data_ptr(), ws_perm.numel(),
-                        p_perm, sh)
+                        p_perm, s_perm)
         if st != ms.MS_OK:
             raise ms.MsError(st, "ms_perm")
         st = ms.ms_shuffle(rec.data_ptr(), n_rec, 16, seed, ws_rec.data_ptr(), ws_rec.numel(),
-                           p_rec, sh)
+                           p_rec, s_rec)
         if st != ms.MS_OK:
             raise ms.MsError(st, "ms_shuffle")
+        if fork is not None:
+            join[0].record(st_perm)
+            join[1].record(st_rec)
+            stream.wait_event(join[0])
+            stream.wait_event(join[1])
 
     for _ in range(args.warmup):
         step()
@@ -377,6 +413,7 @@ def run_ours(args, world, rank, local):
             "fused_level_pairs_rec": plan_rec.fused_pairs,
             "l2": "inputs larger than L2 (4.3 GB and 4.8 GB arrays), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "overlap": args.overlap,
             "profiled_events": "CUDA event pair around every kernel during the timed region",
         },
         "roofline": roofline,

@@ -23,6 +23,8 @@ constexpr uint32_t kSpanBytes = 32u * 1024u;  // span buffer of the streamed sma
 constexpr uint32_t kSpanMaxMerges = 64u;      // merges per span at most
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kTileMaxDepth = 6u;        // one-warp tiles: at most 2^6 base blocks
+constexpr uint64_t kPairParityBytes = 1ull << 28;  // arrays from which a shuffle fixes its pass
+                                                   // parity with a fused pair of levels
 
 // Kernel classes timed by the optional profiler (MS_FLAG_PROFILE).
 enum KernelKind : int {

@@ -441,9 +441,22 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
         }
         for (; t < Lt; t += kTileThreads) o[t] = gb + Z[t];
       } else {
+        // the tile's input rows in the order of the indices: eight independent row loads per
+        // thread are in flight before their stores (one at a time, each tile would wait out
+        // Lt / kTileThreads memory latencies in a row)
         const E *const src = static_cast<const E *>(a.in) + g0;
         E *const o = static_cast<E *>(a.out) + g0;
-        for (uint32_t t = tid; t < Lt; t += kTileThreads)
+        constexpr uint32_t kRows = sizeof(E) >= 16u ? 4u : 8u;
+        uint32_t t0 = 0;
+        for (; t0 + kRows * kTileThreads <= Lt; t0 += kRows * kTileThreads) {
+          E v[kRows];
+#pragma unroll
+          for (uint32_t u = 0; u < kRows; ++u)
+            v[u] = __ldg(src + min(static_cast<uint32_t>(Z[t0 + u * kTileThreads + tid]), Lt - 1u));
+#pragma unroll
+          for (uint32_t u = 0; u < kRows; ++u) o[t0 + u * kTileThreads + tid] = v[u];
+        }
+        for (uint32_t t = t0 + tid; t < Lt; t += kTileThreads)
           o[t] = src[min(static_cast<uint32_t>(Z[t]), Lt - 1u)];
       }
     }

@@ -82,6 +82,14 @@ def test_plan_fusion_depth_and_workspace():
     assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9, flags=perm)).fuse_depth == 2
     # (all of a shuffle's levels fused would leave its tile pass in place)
     assert ms.ms_plan_info(3000, 4, ms.params(B=1024, fuse_depth=9)).fuse_depth == 1
+    # from 2^28 bytes on, the shuffle fuses its last two global levels into one pass instead
+    big = ms.ms_plan_info(1 << 26, 4, ms.params(B=512, fuse_depth=5))
+    assert big.fuse_depth == 5 and big.fused_pairs == 1 and (big.passes - 1) % 2 == 1
+    assert ms.ms_plan_info(1 << 26, 4, ms.params(B=512, fuse_depth=5, flags=perm)).fused_pairs == 0
+    # (one level less where single passes are forced)
+    single = ms.ms_plan_info(1 << 26, 4, ms.params(B=512, fuse_depth=5,
+                                                   flags=ms.MS_FLAG_SINGLE_LEVELS))
+    assert single.fuse_depth == 4 and single.fused_pairs == 0
 
 
 def test_plan_records():

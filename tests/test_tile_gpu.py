@@ -93,3 +93,51 @@ def test_tile_sequential_tails_and_tiny_blocks():
             if ms.plan(n, 4, B=1, fuse_depth=d, flags=ms.MS_FLAG_PERM)["fuse_depth"] != d:
                 continue
             assert np.array_equal(_perm(n, 9, 1, d), want), (n, d)
+
+
+def test_tile_large_blocks_of_the_tuned_scale_rows():
+    """The tuned rows of the largest arrays use base blocks of up to 512 (perm) and 573 (16-byte
+    records) elements, tiles of 32 blocks: the same shapes on arrays the oracle finishes in
+    seconds (Fisher-Yates draws of up to 10-bit slices, tiles above 16,000 elements)."""
+    n = (1 << 22) + 7  # c = 13: blocks of 512 and 513
+    want, _ = oracle.perm(n, 11, 512)
+    assert ms.plan(n, 4, B=512, fuse_depth=5, flags=ms.MS_FLAG_PERM)["fuse_depth"] == 5
+    assert np.array_equal(_perm(n, 11, 512, 5), want)
+    n = 572 * 4096 + 17  # c = 12: blocks of 572 and 573
+    arr = inputs.records16(n)
+    want, _ = oracle.shuffle(arr, 11, 572)
+    assert ms.plan(n, 16, B=572, fuse_depth=5)["fuse_depth"] == 5
+    assert np.array_equal(_shuffle(arr, 11, 572, 5), want)
+
+
+@pytest.mark.parametrize("lg,w", [(26, 4), (26, 8)])
+def test_tile_shuffle_pass_parity_by_fused_pair(lg, w):
+    """A shuffle of at least 2^28 bytes whose tile pass would be followed by an even number of
+    global passes fuses its last two global levels into one pass (instead of fusing one level
+    less in the tile). The result is still that of the definition: the shuffle of the identity
+    equals the perm of the same (n, seed, B), whose plan has no fused pair."""
+    import torch
+
+    n, B, d, seed = 1 << lg, 512, 5, 13
+    sh = ms.plan(n, w, B=B, fuse_depth=d)
+    assert sh["fuse_depth"] == d and sh["fused_pairs"] == 1
+    assert ms.plan(n, 4, B=B, fuse_depth=d, flags=ms.MS_FLAG_PERM)["fused_pairs"] == 0
+    p = ms.params(B, d, 0)
+    ref = torch.empty(n, dtype=torch.int32, device="cuda")
+    nbytes = max(ms.ms_workspace_bytes(n, w, p), ms.ms_workspace_bytes(n, 4, p))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_perm(ref.data_ptr(), n, seed, ws.data_ptr(), ws.numel(), p,
+                    torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    x = torch.arange(n, dtype=torch.int64 if w == 8 else torch.int32, device="cuda")
+    if w == 8:
+        x = x | (x << 32)  # both halves of a row carry its index
+    st = ms.ms_shuffle(x.data_ptr(), n, w, seed, ws.data_ptr(), ws.numel(), p,
+                       torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    if w == 8:
+        assert torch.equal((x >> 32).to(torch.int32), ref)
+        assert torch.equal((x & 0xFFFFFFFF).to(torch.int32), ref)
+    else:
+        assert torch.equal(x, ref)
