@@ -140,14 +140,19 @@ typedef struct {
 /*
  * Autotuner lookup. B = 0 in ms_params asks for the cutoff (and, where fuse_depth is -1 or the
  * level-mode flags are unset, the fusion depth and level mode) measured fastest for the call's
- * element width and size on a GB300. The paper leaves the cutoff open (Algorithm 2 only asks for
- * "blocks of roughly the same size"; its listing takes it as a parameter); B changes the result
- * (the block split depends on it), so the resolved value is a pure function of (n, w, installed
- * table) and a caller who needs to reproduce a result records it.
+ * element width and size on a GB300. The paper leaves the cutoff open (its driver, Algorithm 2,
+ * splits the array into 2^c nearly equal blocks, and the appendix listing takes the cutoff as a
+ * parameter); B changes the result through c = min{c : floor(n / 2^c) <= B}, so the resolved
+ * value is a pure function of (n, w, installed table) and a caller who needs to reproduce a
+ * result records it.
  *   ms_tune_entry            one row: applies to calls of width w, single (batch = 0) or batched
  *                            (batch = 1), with ceil(log2 n) <= log2n_max (the smallest such
  *                            bucket wins; beyond every bucket the largest applies). For batched
- *                            calls n is the median instance size. flags may hold
+ *                            calls n is the median instance size. B is a block size: a single
+ *                            call of n > B resolves to B' = floor(n / 2^c) for the c whose
+ *                            blocks are nearest to B by ratio (of the two around n / B), so
+ *                            that its blocks stay near the measured size whatever n (a batch
+ *                            keeps B itself). flags may hold
  *                            MS_FLAG_CTA_LEVELS, MS_FLAG_GLOBAL_LEVELS,
  *                            MS_FLAG_SINGLE_LEVELS and MS_FLAG_PAIR_LEVELS only.
  *   ms_resolve_params        replaces B = 0 in *inout by the table's choice for (n, w); other

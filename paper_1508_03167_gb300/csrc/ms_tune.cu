@@ -3,7 +3,13 @@
 // bucket) to parameters measured fastest on the GPU by the tuner of the Python package; its
 // built-in copy is ms_tune_table.h, written by that tuner. The lookup is a pure function of
 // (n, w, table), so a caller who records the resolved B can reproduce the result (B is part of
-// the result's definition: the block split of the appendix listing depends on it).
+// the result's definition: the block split of the appendix listing depends on it, through the
+// number of levels c = min{c : floor(n / 2^c) <= B} alone).
+//
+// A row's B is the block size measured best at the tuner's power-of-two sizes. A single call of
+// another n runs with the c whose blocks floor(n / 2^c) are nearest to it (by ratio), and
+// resolves B to that block size: a row of 512 gives n = 3*10^8 blocks of 572 (c = 19), where
+// the cutoff 512 itself would give blocks of 286.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -61,6 +67,17 @@ ms_tune_entry lookup(uint64_t n, uint32_t w, uint32_t batch) {
   return d;
 }
 
+// The cutoff whose blocks are nearest to `target` by ratio: floor(n / 2^c) for the c among the
+// two around n / target, so that c is also the listing's smallest c with floor(n / 2^c) <= B.
+uint32_t block_for(uint64_t n, uint32_t target) {
+  if (n <= target) return target;  // one block (c = 0) either way
+  uint32_t c0 = 0;  // n >> c0 >= target > n >> (c0 + 1)
+  while ((n >> (c0 + 1)) >= target) ++c0;
+  const uint64_t b0 = n >> c0, b1 = n >> (c0 + 1);
+  const bool lower = b1 >= 1 && (b0 > MS_MAX_B || b0 * b1 > static_cast<uint64_t>(target) * target);
+  return static_cast<uint32_t>(lower ? b1 : b0);
+}
+
 void apply(const ms_tune_entry &e, ms_params *p) {
   p->B = e.B;
   if (p->fuse_depth < 0) p->fuse_depth = e.fuse_depth;
@@ -77,7 +94,10 @@ ms_params resolve_single(uint64_t n, uint32_t w, const ms_params *p) {
   ms_params r;
   ms_default_params(&r);
   if (p) r = *p;
-  if (r.B == 0) apply(lookup(n, w, 0), &r);
+  if (r.B == 0) {
+    apply(lookup(n, w, 0), &r);
+    r.B = block_for(n, r.B);
+  }
   return r;
 }
 

@@ -40,12 +40,42 @@ def test_buckets_pick_the_smallest_covering_row():
     assert ms.resolve(1 << 30, 4, B=0).B == 256          # beyond every bucket: the largest
     r = ms.resolve(1000, 4, B=0)
     assert r.flags == ms.MS_FLAG_CTA_LEVELS and r.fuse_depth == -1
-    # a caller's own level-mode flag and fusion depth win over the table's
+    # a caller's own level-mode flag and fusion depth win over the table's (B: the row's 512
+    # as a block size, 1000 / 2 = 500 being nearer to it than 1000)
     r = ms.resolve(1000, 4, B=0, fuse_depth=1, flags=ms.MS_FLAG_GLOBAL_LEVELS)
-    assert (r.B, r.fuse_depth, r.flags) == (512, 1, ms.MS_FLAG_GLOBAL_LEVELS)
+    assert (r.B, r.fuse_depth, r.flags) == (500, 1, ms.MS_FLAG_GLOBAL_LEVELS)
     # no row for w = 8: B = 1024
     assert ms.resolve(1 << 20, 8, B=0).B == 1024
     assert ms.resolve_batch([10, 1 << 20, 5], 4, B=0).B == 64
+
+
+def test_row_B_is_a_block_size():
+    """A single call resolves the row's B to the block size floor(n / 2^c) nearest to it by
+    ratio; that B gives the listing's cutoff the same c, and n of a power of two times B keeps
+    B itself."""
+    ms.ms_tune_install([dict(w=16, batch=0, log2n_max=64, B=512, fuse_depth=5, flags=0),
+                        dict(w=16, batch=1, log2n_max=64, B=512, fuse_depth=-1, flags=0)])
+
+    def cutoff_levels(n, B):
+        c = 0
+        while (n >> c) > B:
+            c += 1
+        return c
+
+    for n, want in [(300_000_017, 572), (1 << 28, 512), (5 << 24, 640), (402_653_184, 384),
+                    (700_000, 683), (512, 512), (100, 512), (1025, 512)]:
+        r = ms.resolve(n, 16, B=0)
+        assert r.B == want, (n, r.B)
+        c = cutoff_levels(n, r.B)
+        if n > 512:
+            assert n >> c == r.B  # blocks of B and B + 1 elements
+            # nearest by ratio among the two neighbouring cutoffs
+            lo, hi = n >> (c + 1), n >> max(c - 1, 0)
+            assert max(r.B, 512) / min(r.B, 512) <= max(lo, 512) / min(lo, 512) or lo == 0
+            assert max(r.B, 512) / min(r.B, 512) <= max(hi, 512) / min(hi, 512) or c == 0
+        assert ms.plan(n, 16, B=0)["B"] == r.B
+    # a batch keeps the row's value
+    assert ms.resolve_batch([300_000_017] * 3, 16, B=0).B == 512
 
 
 def test_batch_resolves_by_the_median():
