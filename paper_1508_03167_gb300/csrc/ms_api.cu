@@ -80,9 +80,9 @@ bool leaf_fits(uint64_t n, uint32_t c, uint32_t d, uint32_t w) {
 
 // Shared-memory layout of the tile kernel (16-bit tile-local indices, eight warps a tile): two
 // buffers (the first holds block k at k*P, P = 2 mod 64 and at least the largest block; merge r
-// of level l writes at r*S[l]), then two sets of a level's (coin word, zero prefix) pairs and
-// two sets of its tail draws (which also hold the per-thread queues of second-word
-// Fisher-Yates draws: 256 threads x 4 entries x 4 bytes over both sets).
+// of level l writes at r*S[l]), then one level's (coin word, zero prefix) pairs and two sets of
+// a level's tail draws (which also hold the per-thread queues of second-word Fisher-Yates
+// draws: 256 threads x 4 entries x 4 bytes over both sets).
 struct TileSmem {
   bool ok = false;
   uint32_t P = 0, buf = 0, wcap = 0, tcap = 0;
@@ -118,7 +118,8 @@ TileSmem tile_smem(uint64_t n, uint32_t c, uint32_t d) {
   T.buf = static_cast<uint32_t>((buf + 7) & ~7ull);
   T.wcap = static_cast<uint32_t>((wcap + 1) & ~1ull);
   T.tcap = static_cast<uint32_t>((tcap + 7) & ~7ull);
-  T.bytes = 4ull * T.buf + 2ull * (8ull * T.wcap + 2ull * T.tcap);
+  // two index buffers, one set of (coin word, zero prefix) pairs, two sets of tail draws
+  T.bytes = 4ull * T.buf + 8ull * T.wcap + 4ull * T.tcap;
   T.ok = T.bytes <= kSmemLimit;
   return T;
 }

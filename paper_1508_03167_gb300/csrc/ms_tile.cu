@@ -47,26 +47,27 @@ __device__ __forceinline__ uint32_t warp_exclusive(uint32_t v, uint32_t *total) 
   return incl - v;
 }
 
-// Control data of one merge level (two sets: the control warp builds level l+1's while the
-// data warp finishes level l): (coin word, zero prefix) pairs, tail draws, and per merge its
-// size, break step, half bases, leftover base, first word, first tail draw and first tail quad;
-// then whether the tail draws are made ahead and how many quads of them there are.
+// Control data of one merge level: (coin word, zero prefix) pairs, tail draws, and per merge
+// its size, break step, leftover base, first word, first tail draw and first tail quad; then
+// whether the tail draws are made ahead and how many quads of them there are (a merge's half
+// bases follow from its index and the level's input stride). The control warp builds level
+// l+1's while the data warp finishes level l's tails: the tail draws and per-merge words come
+// in two sets, the (coin word, zero prefix) pairs in one, as level l's are dead once its
+// interleave is done (one set less keeps a tile of 16,384 elements at three CTAs an SM).
 struct LevelCtl {
   uint2 *cz;
   uint16_t *mv;
-  uint32_t *m;  // kTileCtlWords words: 7 arrays of 32 and the flag "tail draws made"
+  uint32_t *m;  // kTileCtlWords words: 6 arrays of 32, the flag "tail draws made", the quads
 };
-constexpr uint32_t kTileCtlWords = 8u * 32u + 2u;
+constexpr uint32_t kTileCtlWords = 6u * 32u + 2u;
 __device__ __forceinline__ uint32_t *ctl_N(const LevelCtl &c) { return c.m; }
 __device__ __forceinline__ uint32_t *ctl_T(const LevelCtl &c) { return c.m + 32; }
-__device__ __forceinline__ uint32_t *ctl_a(const LevelCtl &c) { return c.m + 64; }
-__device__ __forceinline__ uint32_t *ctl_b(const LevelCtl &c) { return c.m + 96; }
-__device__ __forceinline__ uint32_t *ctl_lb(const LevelCtl &c) { return c.m + 128; }
-__device__ __forceinline__ uint32_t *ctl_woff(const LevelCtl &c) { return c.m + 160; }
-__device__ __forceinline__ uint32_t *ctl_koff(const LevelCtl &c) { return c.m + 192; }
-__device__ __forceinline__ uint32_t *ctl_qoff(const LevelCtl &c) { return c.m + 224; }
-__device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m + 256; }
-__device__ __forceinline__ uint32_t *ctl_qtot(const LevelCtl &c) { return c.m + 257; }
+__device__ __forceinline__ uint32_t *ctl_lb(const LevelCtl &c) { return c.m + 64; }
+__device__ __forceinline__ uint32_t *ctl_woff(const LevelCtl &c) { return c.m + 96; }
+__device__ __forceinline__ uint32_t *ctl_koff(const LevelCtl &c) { return c.m + 128; }
+__device__ __forceinline__ uint32_t *ctl_qoff(const LevelCtl &c) { return c.m + 160; }
+__device__ __forceinline__ uint32_t *ctl_drawn(const LevelCtl &c) { return c.m + 192; }
+__device__ __forceinline__ uint32_t *ctl_qtot(const LevelCtl &c) { return c.m + 193; }
 
 // The data-independent part of merge level lv of the tile, by one warp: coin words, zero
 // prefixes and break step of every merge, the leftover base, and the offsets of the tail draws
@@ -146,8 +147,6 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   if (sub == 0u) {
     ctl_N(c)[r] = N;
     ctl_T(c)[r] = T;
-    ctl_a(c)[r] = Ab;
-    ctl_b(c)[r] = Bb;
     ctl_lb(c)[r] = lb;
     ctl_woff(c)[r] = woff;
     ctl_koff(c)[r] = koff;
@@ -224,10 +223,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
   uint16_t *const bufA = reinterpret_cast<uint16_t *>(smem_raw);
   uint16_t *const bufB = bufA + a.buf;
   uint2 *const cz0 = reinterpret_cast<uint2 *>(bufB + a.buf);
-  uint16_t *const mv0 = reinterpret_cast<uint16_t *>(cz0 + 2u * a.wcap);
+  uint16_t *const mv0 = reinterpret_cast<uint16_t *>(cz0 + a.wcap);
   auto ctl = [&](uint32_t set) {
     LevelCtl c;
-    c.cz = cz0 + set * a.wcap;
+    c.cz = cz0;
     c.mv = mv0 + set * a.tcap;
     c.m = &ctlm[0][0] + set * kTileCtlWords;
     return c;
@@ -347,8 +346,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
       const uint32_t rstep = kTileWarps / wpm;
       const uint32_t sw = warp % wpm;
       for (uint32_t rr = warp / wpm; rr < R; rr += rstep) {
-        const uint32_t Nr = ctl_N(c)[rr], Tr = ctl_T(c)[rr], ar = ctl_a(c)[rr],
-                       br = ctl_b(c)[rr], lbr = ctl_lb(c)[rr];
+        const uint32_t Nr = ctl_N(c)[rr], Tr = ctl_T(c)[rr], lbr = ctl_lb(c)[rr];
+        // (merge rr reads its halves at 2 rr Sin and 2 rr Sin + Sin, Sin the input stride)
+        const uint32_t Sin = lv ? s_S[lv - 1u] : a.P;
+        const uint32_t ar = 2u * rr * Sin, br = ar + Sin;
         const uint2 *const czr = c.cz + ctl_woff(c)[rr];
         uint16_t *const Yr = Y + rr * Sout;
         for (uint32_t t0 = 256u * sw; t0 < Nr; t0 += 256u * wpm) {
@@ -481,13 +482,38 @@ cudaError_t launch_t(const Plan &p, const void *in, void *out, uint64_t seed, cu
   auto kern = tile_kernel<E, kPerm>;
   cudaError_t err = allow_dynamic_smem(kern, p.tile_smem);
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, p.tile_smem);
-  if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return cudaErrorUnknown;
+  if constexpr (!kPerm) {
+    // A shuffle's tile ends by reading its input rows in a random order within the tile, which
+    // the L1 cache (the SM's unified memory less the shared memory of its resident CTAs) serves
+    // in part: keep at least kTileMinL1 bytes of it, with as many CTAs as fit in the rest
+    // (measured on GB300: at 79 KB a tile, three CTAs leave 28 KB and slow a 2^30 4-byte
+    // shuffle from 39.2 to 42.0 ms; the perm reads nothing and keeps every CTA that fits).
+    constexpr int kTileMinL1 = 56 * 1024;
+    int sm_bytes = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+      return cudaErrorUnknown;
+    const long per_cta = static_cast<long>(p.tile_smem) + static_cast<long>(fa.sharedSizeBytes) +
+                         reserved;
+    long k = (static_cast<long>(sm_bytes) - kTileMinL1) / per_cta;
+    if (k < 1) k = 1;
+    long pct = (100 * k * per_cta + sm_bytes - 1) / sm_bytes;
+    if (pct > 100) pct = 100;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               static_cast<int>(pct));
+    if (err != cudaSuccess) return err;
+  }
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, p.tile_smem);
+  if (err != cudaSuccess) return err;
   const uint64_t tiles = p.q >> p.d;
   const uint64_t resident = static_cast<uint64_t>(per_sm > 0 ? per_sm : 1) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
