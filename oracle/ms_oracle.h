@@ -13,7 +13,8 @@
  *     (q = 2^c blocks, c the smallest integer with floor(n / 2^c) <= cutoff, boundaries
  *     floor(n * i / q)),
  *   - Algorithm 3 (Merge): coin loop until one side is exhausted, then random insertion
- *     of every remaining position (the "Fisher-Yates to finish merging" loop).
+ *     of every remaining position (the second loop of the merge, Fisher-Yates steps over the
+ *     tail).
  *
  * Two merge placements are provided:
  *   MS_ORACLE_STABLE  -- the coin word interleaves the two halves in their order (output

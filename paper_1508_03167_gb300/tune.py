@@ -3,10 +3,12 @@ size bucket by timing the CUDA library on the GPU, and writes the table the libr
 lookup uses (``csrc/ms_tune_table.h``, built in) plus a JSON copy that can be installed at run
 time with ``ms_tune_install``.
 
-The paper leaves the cutoff open (Algorithm 2 splits into "blocks of roughly the same size"; the
-appendix listing takes the cutoff as a parameter). B is part of the result's definition, so the
-tuner only changes which B a call with B = 0 resolves to; every tuned choice is recorded in the
-table. The fusion depth and the level mode never change the result.
+The paper leaves the cutoff open: its driver (Algorithm 2) only needs 2^c nearly equal blocks,
+and the appendix listing takes the cutoff as a parameter. B is part of the result's definition,
+so the tuner only changes which B a call with B = 0 resolves to; every tuned choice is recorded
+in the table. The fusion depth and the level mode never change the result. A row's B is a block
+size: the library runs a call of n elements with the cutoff whose blocks are nearest to it
+(``row_cutoff``), and the tuner times each candidate the same way.
 
 Usage on a GPU:  python -m paper_1508_03167_gb300.tune [--quick] [--header] [--json PATH]
 Built-in table from a saved JSON table:  python -m paper_1508_03167_gb300.tune --from-json PATH
@@ -79,6 +81,18 @@ def parse_header(text: str) -> list[dict]:
         vals = [int(v) for v in line.strip("{},").split(",")]
         rows.append(dict(zip(("w", "batch", "log2n_max", "B", "fuse_depth", "flags"), vals)))
     return rows
+
+
+def row_cutoff(n: int, w: int, B: int) -> int:
+    """The cutoff a single call of n elements of width w runs with when the table's row holds
+    block size B: the library's own rule, read through a one-row table (host only)."""
+    from . import ms_tune_install, resolve
+
+    ms_tune_install([dict(w=w, batch=0, log2n_max=64, B=B, fuse_depth=-1, flags=0)])
+    try:
+        return resolve(n, w, B=0).B
+    finally:
+        ms_tune_install([])  # back to the built-in table
 
 
 # ------------------------------------------------------------------ GPU timing ----------------
@@ -181,7 +195,8 @@ def tune(quick: bool = False, reps: int = 5, log=print) -> list[dict]:
                 for fd, fl in MODE_CANDIDATES:
                     if fl in (0x80, 0x100) and lg < 20:
                         continue  # few global levels: nothing to fuse
-                    timings[(B, fd, fl)] = time_single(n, w, B, fd, fl, reps)
+                    timings[(B, fd, fl)] = time_single(n, w, row_cutoff(n, w, B), fd, fl,
+                                                       reps)
             B, fd, fl = pick(timings)
             log(f"single w={w:2d} n=2^{lg}: B={B} fuse_depth={fd} flags={fl:#x} "
                 f"({statistics.median(timings[(B, fd, fl)]):.3f} ms)")

@@ -78,6 +78,16 @@ def test_row_B_is_a_block_size():
     assert ms.resolve_batch([300_000_017] * 3, 16, B=0).B == 512
 
 
+def test_tuner_times_a_candidate_at_the_cutoff_its_row_gives():
+    # the 300,000,017-record size point: a row of 512 runs with blocks of 572, not the 286 that
+    # the cutoff 512 itself gives; at the other points (2^k, 2^k + 17) the two agree
+    assert tune.row_cutoff(300_000_017, 16, 512) == 572
+    assert tune.row_cutoff((1 << 26) + 17, 16, 512) == 512
+    assert tune.row_cutoff(1 << 30, 4, 256) == 256
+    # and the built-in table is back in place afterwards
+    assert ms.ms_tune_table() == tune.parse_header(open(tune.HEADER).read())
+
+
 def test_batch_resolves_by_the_median():
     ms.ms_tune_install([
         dict(w=4, batch=1, log2n_max=10, B=32, fuse_depth=-1, flags=0),
