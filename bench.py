@@ -30,6 +30,8 @@ N_PERM = 1 << 30
 N_REC = 300_000_017
 SEED = 7
 DEFAULT_B = {"perm": 0, "rec": 0}  # 0: the autotuner's table chooses (reported as resolved)
+SCALE_WORKLOAD = ("plain MergeShuffle at scale: perm of n=2^30 uint32 identity + shuffle of "
+                  "n=300000017 16-byte records {u32 key, 12-byte splitmix64 payload}, seed 7")
 
 
 def parse():
@@ -401,9 +403,8 @@ def run_ours(args, world, rank, local):
         "dtype": "u32",
         "data": "synthetic",
         "config": {
-            "workload": ("plain MergeShuffle at scale: perm of n=2^30 uint32 identity + shuffle of "
-                         "n=300000017 16-byte records {u32 key, 12-byte splitmix64 payload}, seed 7"
-                         if not args.small else "small profiling case: perm 2^26 + 2^24+17 records"),
+            "workload": (SCALE_WORKLOAD if not args.small
+                         else "small profiling case: perm 2^26 + 2^24+17 records"),
             "n_perm": n_perm, "n_rec": n_rec, "seed": SEED,
             "B_perm": p_perm.B, "B_rec": p_rec.B,
             "B_source": "autotuner table" if args.B_perm == 0 else "command line",
@@ -490,8 +491,10 @@ def run_reference(args, world, rank):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "plain MergeShuffle at scale (bounded CPU sample)",
-                   "n_perm_sample": n1, "n_rec_sample": n2, "seed": SEED},
+        # the GPU arm's workload; each timed step is the bounded sample stated below
+        "config": {"workload": SCALE_WORKLOAD, "n_perm": N_PERM, "n_rec": N_REC, "seed": SEED,
+                   "B_perm": B_perm, "B_rec": B_rec,
+                   "sample": {"n_perm": n1, "n_rec": n2}},
         "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
