@@ -126,6 +126,9 @@ typedef struct {
                                other hbm_levels - global_levels finish inside a CTA or a warp */
   uint32_t fused_pairs;     /* pairs of consecutive global levels sharing one data pass:
                                passes = 1 + hbm_levels - fused_pairs */
+  uint32_t tile_smem;       /* dynamic shared memory of one CTA of the 16-bit tile kernel (the
+                               base-block pass when fuse_depth > 0), bytes; 0 if that pass
+                               runs another kernel */
 } ms_plan;
 
 /* Per-kernel-class timing accumulated over calls made with MS_FLAG_PROFILE. */

@@ -51,7 +51,8 @@ class MsPlan(ctypes.Structure):
                 ("hbm_levels", ctypes.c_uint32), ("passes", ctypes.c_uint32),
                 ("tiles", ctypes.c_uint64), ("tile_max", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_uint32),
-                ("global_levels", ctypes.c_uint32), ("fused_pairs", ctypes.c_uint32)]
+                ("global_levels", ctypes.c_uint32), ("fused_pairs", ctypes.c_uint32),
+                ("tile_smem", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

@@ -958,6 +958,7 @@ ms_status ms_plan_info(uint64_t n, uint32_t w, const ms_params *params, ms_plan 
   uint32_t pairs = 0;
   for (uint32_t i = 0; i < p.nlevels && n > 1; ++i) pairs += p.levels[i].pair == 1 ? 1u : 0u;
   out->fused_pairs = pairs;
+  out->tile_smem = (n > 1 && p.tile_mode) ? static_cast<uint32_t>(p.tile_smem) : 0u;
   return MS_OK;
 }
 

@@ -92,6 +92,26 @@ def test_plan_fusion_depth_and_workspace():
     assert single.fuse_depth == 4 and single.fused_pairs == 0
 
 
+def test_tuned_tile_shapes_keep_their_occupancy():
+    """The tile kernel's shared memory at the tuned shapes: B = 512 at 2^30 (tiles of 16,384)
+    fits three CTAs in an SM's 228 KB (with 1 KB reserved and at most 2 KB of static shared
+    memory a CTA), B = 256 five (the registers allow four), the records' B = 572 two."""
+    perm = ms.MS_FLAG_PERM
+    per_sm = 228 * 1024
+
+    def ctas(t):
+        return per_sm // (t + 1024 + 2048)
+
+    t512 = ms.ms_plan_info(1 << 30, 4, ms.params(B=512, fuse_depth=5, flags=perm)).tile_smem
+    t256 = ms.ms_plan_info(1 << 30, 4, ms.params(B=256, fuse_depth=5, flags=perm)).tile_smem
+    t572 = ms.ms_plan_info(300_000_017, 16, ms.params(B=572, fuse_depth=5)).tile_smem
+    assert (ctas(t512), ctas(t256), ctas(t572)) == (3, 5, 2), (t512, t256, t572)
+    # no tile pass, no tile shared memory
+    assert ms.ms_plan_info(1 << 20, 4, ms.params(B=1024, fuse_depth=0)).tile_smem == 0
+    assert ms.ms_plan_info(1 << 30, 4, ms.params(B=512, fuse_depth=5,
+                                                 flags=perm | ms.MS_FLAG_CTA_TILES)).tile_smem == 0
+
+
 def test_plan_records():
     p = ms.ms_plan_info(300_000_017, 16, ms.params(B=1024))
     assert p.c == 19 and p.w == 16
