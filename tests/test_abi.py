@@ -158,3 +158,39 @@ def test_oracle_and_cuda_path_share_no_code():
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_1508_03167_gb300" not in text, f
             assert "mergeshuffle.h" not in text, f
+
+
+def test_plan_invariants_on_random_requests():
+    """Planner invariants over seeded random (n, w, B, fuse depth, mode flag) requests: the
+    cutoff of the appendix listing (c = min{c : floor(n / 2^c) <= B}), passes = 1 + HBM levels
+    - fused pairs, the fusion depth within c, the tile kernel's shared memory within its
+    budget, and a shuffle's tile pass never in place (an odd number of passes follows it, so
+    the last lands in the caller's array)."""
+    import random
+
+    rng = random.Random(5)
+    modes = [0, ms.MS_FLAG_PERM, ms.MS_FLAG_SINGLE_LEVELS, ms.MS_FLAG_PAIR_LEVELS,
+             ms.MS_FLAG_GLOBAL_LEVELS, ms.MS_FLAG_CTA_TILES]
+    tiled = 0
+    for _ in range(1500):
+        n = min(int(2 ** rng.uniform(1, 32)), 2**32 - 1)
+        fl = rng.choice(modes)
+        w = 4 if fl == ms.MS_FLAG_PERM else rng.choice([4, 8, 16])
+        B = rng.randint(1, ms.MS_MAX_B)
+        d = rng.choice([-1, 0, 1, 2, 3, 4, 5, 6])
+        p = ms.ms_plan_info(n, w, ms.params(B=B, fuse_depth=d, flags=fl))
+        c = 0
+        while (n >> c) > B:
+            c += 1
+        case = (n, w, B, d, fl)
+        assert p.c == c, case
+        if n <= 1:
+            continue
+        assert p.passes == 1 + p.hbm_levels - p.fused_pairs, case
+        assert p.fuse_depth <= c and p.hbm_levels == c - p.fuse_depth, case
+        if p.tile_smem:
+            tiled += 1
+            assert p.tile_smem <= 200 * 1024, case
+            if not fl & ms.MS_FLAG_PERM:
+                assert (p.passes - 1) % 2 == 1, case
+    assert tiled > 300  # the tile kernel's plans are well represented
