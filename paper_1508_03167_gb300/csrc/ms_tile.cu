@@ -13,7 +13,7 @@
 //     the stable interleave (a lane places eight consecutive positions, walking the two
 //     halves with one index each), the tail draws, and the random insertions of Algorithm 3's
 //     second loop in order, one lane per merge. The data-independent part of level l+1 (coins,
-//     prefixes, break steps by one warp, then the tail draws shared by the three warps that do
+//     prefixes, break steps by one warp, then the tail draws shared by the seven warps that do
 //     not run the tails) is built while the data warp runs level l's tails;
 //   * one store of the tile.
 // Block k of the tile sits at k*P in the first buffer (P = 2 mod 64, so the 32 lanes at one
@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
     const uint32_t role = (warp - static_cast<uint32_t>(tt)) & (kTileWarps - 1u);
     __syncthreads();
 
-    // ---- Algorithm 1's draws (warp w: quads w, w+4, ... of every block; lane: the block)
+    // ---- Algorithm 1's draws (warp w: quads w, w + kTileWarps, ... of every block; lane: the
+    // block)
     for (uint32_t kg = 0; kg < nb; kg += 32u) {
       const uint32_t k = kg + lane;
       const bool act = k < nb;
@@ -324,7 +325,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
       }
       for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
     } else {
-      // the other roles (1, 3, ...): level 0's control data (role 1), then its tail draws
+      // the other roles (1 and 3 .. kTileWarps-1): level 0's control data (role 1), then its
+      // tail draws
       const LevelCtl c0 = ctl(0u);
       if (role == 1u) level_setup(a.key, a.d, a.tcap, boff, k0, 0u, a.P, lane, c0.cz, c0.mv, c0.m);
       control_barrier((kTileWarps - 2u) * 32u);
@@ -340,8 +342,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
       const uint32_t Sout = s_S[lv];
       const uint32_t R = nb >> (lv + 1u);
       const LevelCtl c = ctl(lv & 1u);
-      // stable interleave: a thread places positions t .. t+7 of a merge. With R >= 4 merges a
-      // warp takes whole merges (r = w, w+4, ...); with fewer, 4/R warps share each merge
+      // stable interleave: a thread places positions t .. t+7 of a merge. With R >= kTileWarps
+      // merges a warp takes whole merges (r = w, w + kTileWarps, ...); with fewer, kTileWarps/R
+      // warps share each merge
       const uint32_t wpm = R >= kTileWarps ? 1u : kTileWarps / R;  // warps per merge
       const uint32_t rstep = kTileWarps / wpm;
       const uint32_t sw = warp % wpm;
@@ -443,8 +446,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
         for (; t < Lt; t += kTileThreads) o[t] = gb + Z[t];
       } else {
         // the tile's input rows in the order of the indices: eight independent row loads per
-        // thread are in flight before their stores (one at a time, each tile would wait out
-        // Lt / kTileThreads memory latencies in a row)
+        // thread (four of 16-byte rows) are in flight before their stores (one at a time, each
+        // tile would wait out Lt / kTileThreads memory latencies in a row)
         const E *const src = static_cast<const E *>(a.in) + g0;
         E *const o = static_cast<E *>(a.out) + g0;
         constexpr uint32_t kRows = sizeof(E) >= 16u ? 4u : 8u;
