@@ -88,9 +88,11 @@ typedef void *ms_stream_t;
 #define MS_FLAG_PAIR_LEVELS 0x100u   /* fuse consecutive global levels into one data pass for
                                         every element width (by default only 16-byte elements,
                                         where the pass is bound by memory rather than by its
-                                        instructions; the result is identical) */
+                                        instructions, and, for a shuffle of at least 2^28 bytes
+                                        whose tile pass needs an odd number of passes after it,
+                                        its last two global levels; the result is identical) */
 #define MS_FLAG_CTA_TILES 0x200u     /* fused merge levels (fuse_depth > 0) run on the CTA-wide
-                                        base-block kernel rather than the one-warp tile kernel
+                                        base-block kernel rather than the eight-warp tile kernel
                                         on 16-bit indices (the result is identical) */
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default

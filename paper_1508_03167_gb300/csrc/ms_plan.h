@@ -22,7 +22,7 @@ constexpr uint32_t kSmemLimit = 200u * 1024u; // dynamic shared memory budget of
 constexpr uint32_t kSpanBytes = 32u * 1024u;  // span buffer of the streamed small-merge levels
 constexpr uint32_t kSpanMaxMerges = 64u;      // merges per span at most
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kTileMaxDepth = 6u;        // one-warp tiles: at most 2^6 base blocks
+constexpr uint32_t kTileMaxDepth = 6u;        // tile kernel: at most 2^6 base blocks a tile
 constexpr uint64_t kPairParityBytes = 1ull << 28;  // arrays from which a shuffle fixes its pass
                                                    // parity with a fused pair of levels
 
@@ -95,7 +95,7 @@ struct Plan {
   uint32_t aux_w = 0;        // bytes of one warp's auxiliary shared-memory region
   uint32_t fy_per_cta = 0;   // d = 0: base blocks per one-warp CTA of the Fisher-Yates kernel
   size_t leaf_smem = 0;      // dynamic shared memory of the base-block kernel
-  // one-warp tile kernel (ms_tile.cu) for the base blocks and levels 0..d-1, if it fits:
+  // eight-warp tile kernel (ms_tile.cu) for the base blocks and levels 0..d-1, if it fits:
   // block stride of its Fisher-Yates layout, 16-bit entries of each of its two buffers, coin
   // words and tail draws of one level, output stride of one merge of level l, shared memory
   bool tile_mode = false;
@@ -172,7 +172,7 @@ cudaError_t allow_dynamic_smem(K kern, size_t smem) {
 // Kernel launchers (ms_leaf.cu, ms_level.cu). Return the launch error (cudaSuccess if none).
 cudaError_t launch_leaf(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s);
-// The one-warp tile kernel (ms_tile.cu): base blocks and levels 0..d-1; out of place unless perm.
+// The eight-warp tile kernel (ms_tile.cu): base blocks and levels 0..d-1; out of place unless perm.
 cudaError_t launch_tile(const Plan &p, const void *in, void *out, bool perm, uint64_t seed,
                         cudaStream_t s);
 // A global level in two parts: the data-independent plan (coin counts, prefixes, break steps,

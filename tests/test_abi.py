@@ -71,7 +71,7 @@ def test_plan_fusion_depth_and_workspace():
     assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=0)).fuse_depth == 0
     perm = ms.MS_FLAG_PERM
     assert ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2, flags=perm)).fuse_depth == 2
-    # a shuffle's one-warp tile pass must not run in place: with 1 span level and 7 global
+    # a shuffle's tile pass must not run in place: with 1 span level and 7 global
     # levels after it, it fuses one level less (an odd number of passes follows)
     sh = ms.ms_plan_info(2**20, 4, ms.params(B=1024, fuse_depth=2))
     assert sh.fuse_depth == 1 and (sh.passes - 1) % 2 == 1

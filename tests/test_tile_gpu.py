@@ -1,8 +1,9 @@
-"""The one-warp tile kernel (Fisher-Yates of the base blocks and the first d merge levels on
-16-bit tile-local indices, one warp per tile of 2^d blocks) against the oracle: every depth it
-takes, cutoffs that give base blocks of two sizes and uneven merge halves, all element widths,
-the per-level tail draws made in the loop when they overflow, and the same calls on the CTA-wide
-base-block kernel (MS_FLAG_CTA_TILES)."""
+"""The tile kernel (Fisher-Yates of the base blocks and the first d merge levels on 16-bit
+tile-local indices, one CTA of eight warps per tile of 2^d blocks) against the oracle: every
+depth it takes, cutoffs that give base blocks of two sizes and uneven merge halves, all element
+widths, the per-level tail draws made in the loop when they overflow, the tuned block sizes, the
+shuffle's parity pair, and the same calls on the CTA-wide base-block kernel
+(MS_FLAG_CTA_TILES)."""
 from __future__ import annotations
 
 import numpy as np
