@@ -56,7 +56,8 @@ typedef enum {
   MS_ERR_UNSUPPORTED = 2, /* valid request this build does not handle (e.g. B > MS_MAX_B) */
   MS_ERR_NOMEM = 3,       /* a host-side staging allocation failed */
   MS_ERR_CUDA = 4,        /* a CUDA call or launch failed */
-  MS_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up (batched form) */
+  MS_ERR_TIMEOUT = 5      /* reserved: no entry point returns it (no kernel of this library
+                             waits on another CTA, a flag or a peer) */
 } ms_status;
 
 /* Largest cutoff B the shared-memory base-block kernel accepts. */
@@ -237,10 +238,15 @@ ms_status ms_perm_host(uint32_t *h_out, uint64_t n, uint64_t seed, void *d_ws, s
  *
  * Instances of at most 2^22 elements run in one persistent launch: every CTA takes whole
  * instances, largest first, from an atomic queue and finishes each alone (no CTA waits for
- * another). Larger instances run the single-instance path one after another on the stream.
+ * another). Larger instances (and those above 2^16 that are large against the batch's share
+ * per CTA) run the single-instance path: one after another on the stream if there is one, else
+ * forked onto up to four side streams that belong to the caller's stream (created on its first
+ * batch with several such instances) and joined back into it before the call's work ends.
+ * Nothing of the batch fails asynchronously, so there is no per-instance status array.
  *   ms_batch_workspace_bytes  device workspace for the batch (ping-pong buffers of the engine
  *                             instances, per-CTA scratch, the instance table, and one
- *                             single-instance workspace for the largest large instance).
+ *                             single-instance workspace per side stream, sized for the largest
+ *                             large instance).
  *   ms_batch_prepare          writes the instance table into d_ws (a host-to-device copy from
  *                             pageable memory; call it again whenever pointers, sizes or seeds
  *                             change).

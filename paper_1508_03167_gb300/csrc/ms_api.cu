@@ -587,11 +587,9 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
   if (st != MS_OK) return st;
   if (n <= 1) {
     if (perm && n == 1) {
-      const uint32_t zero = 0;
-      if (failed(cudaMemcpyAsync(data, &zero, 4, cudaMemcpyHostToDevice, s)))
-        return MS_ERR_CUDA;
-      // the source lives on this stack frame: wait until the copy has consumed it
-      if (failed(cudaStreamSynchronize(s))) return MS_ERR_CUDA;
+      // the permutation of {0}: one zero word, stream-ordered (no host source, no sync)
+      if (data == nullptr || reinterpret_cast<uintptr_t>(data) % 4 != 0) return MS_ERR_INVALID;
+      if (failed(cudaMemsetAsync(data, 0, 4, s))) return MS_ERR_CUDA;
     }
     return MS_OK;
   }
@@ -761,33 +759,45 @@ ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_par
   return MS_OK;
 }
 
-// Side streams of the batch form (per device, created once): large instances fork off the
-// caller's stream onto them and join back before the call's work ends.
+// Side streams of the batch form, one set per (device, caller stream), created on first use:
+// large instances fork off the caller's stream onto them and join back before the call's work
+// ends. Keying them by the caller's stream keeps unrelated callers (and captures) from being
+// chained to each other; the set's mutex is held from the fork record to the last join wait,
+// so two host threads on the same caller stream cannot re-record the fork event in between.
 struct SideStreams {
+  int dev = -1;
+  cudaStream_t caller = nullptr;
   cudaStream_t s[kBatchSideStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kBatchSideStreams] = {};
-  bool ready = false;
+  std::mutex mu;
 };
 
-ms_status side_streams(SideStreams **out) {
+ms_status side_streams(cudaStream_t caller, SideStreams **out) {
   static std::mutex mu;
-  static SideStreams per_dev[64];
+  static SideStreams pool[64];
+  static uint32_t used = 0;
   int dev = 0;
-  if (failed(cudaGetDevice(&dev)) || dev < 0 || dev >= 64) return MS_ERR_CUDA;
+  if (failed(cudaGetDevice(&dev))) return MS_ERR_CUDA;
   std::lock_guard<std::mutex> g(mu);
-  SideStreams &S = per_dev[dev];
-  if (!S.ready) {
-    for (uint32_t i = 0; i < kBatchSideStreams; ++i) {
-      if (failed(cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking)))
-        return MS_ERR_CUDA;
-      if (failed(cudaEventCreateWithFlags(&S.join[i], cudaEventDisableTiming)))
-        return MS_ERR_CUDA;
+  for (uint32_t i = 0; i < used; ++i)
+    if (pool[i].dev == dev && pool[i].caller == caller) {
+      *out = &pool[i];
+      return MS_OK;
     }
-    if (failed(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming)))
-      return MS_ERR_CUDA;
-    S.ready = true;
+  if (used == 64) {
+    *out = nullptr;  // too many distinct caller streams: the large instances run in order
+    return MS_OK;
   }
+  SideStreams &S = pool[used];
+  for (uint32_t i = 0; i < kBatchSideStreams; ++i) {
+    if (failed(cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking))) return MS_ERR_CUDA;
+    if (failed(cudaEventCreateWithFlags(&S.join[i], cudaEventDisableTiming))) return MS_ERR_CUDA;
+  }
+  if (failed(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming))) return MS_ERR_CUDA;
+  S.dev = dev;
+  S.caller = caller;
+  ++used;
   *out = &S;
   return MS_OK;
 }
@@ -879,7 +889,9 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
       return MS_ERR_CUDA;
   }
   if (L.large.empty()) return MS_OK;
-  if (L.large_streams <= 1) {
+  SideStreams *S = nullptr;
+  if (L.large_streams > 1 && side_streams(s, &S) != MS_OK) return MS_ERR_CUDA;
+  if (S == nullptr) {
     for (uint32_t i : L.large) {
       const uint64_t seed = h_seeds ? h_seeds[i] : base_seed + i;
       const ms_status rs = run(h_ptrs[i], perm, h_n[i], w, seed, base + L.off_large, L.large_ws,
@@ -888,9 +900,8 @@ ms_status ms_batch_run(uint32_t k, void *const *h_ptrs, const uint64_t *h_n, uin
     }
     return MS_OK;
   }
-  // several large instances: fork onto side streams, one workspace each, join back
-  SideStreams *S = nullptr;
-  if (side_streams(&S) != MS_OK) return MS_ERR_CUDA;
+  // several large instances: fork onto this caller's side streams, one workspace each, join back
+  std::lock_guard<std::mutex> fork_lock(S->mu);
   if (failed(cudaEventRecord(S->fork, s))) return MS_ERR_CUDA;
   for (uint32_t j = 0; j < L.large_streams; ++j)
     if (failed(cudaStreamWaitEvent(S->s[j], S->fork, 0))) return MS_ERR_CUDA;

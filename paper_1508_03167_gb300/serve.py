@@ -124,6 +124,13 @@ class Server:
     def _large_ws(self, n):
         return self.ms.ms_workspace_bytes(n, 4, self.ms.params(B=self.B))
 
+    def _footprint(self, n):
+        """Arena bytes a request needs when admitted alone: its output, the batch workspace of
+        a one-request batch and the fixed per-batch estimate the admission test adds."""
+        extra = 4 * n if n <= self.ENGINE_MAX_N else self._large_ws(n)
+        ws = self.ms.ms_batch_workspace_bytes([n], 4, self.params)
+        return max(self.FIXED_WS + extra + 4 * n, Arena._round(4 * n) + Arena._round(ws))
+
     def _admit(self, group):
         """Allocate outputs for a prefix of `group` and the batch workspace; returns the admitted
         requests (possibly none). The workspace block is left in self._ws_blk."""
@@ -159,6 +166,8 @@ class Server:
         free_streams = list(range(self.max_inflight))
         nxt = 0
         done = []
+        rejected = []
+        timed_out = False
         start_evt = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         start_evt.record(self.streams[0])
@@ -166,8 +175,14 @@ class Server:
         while True:
             now = time.perf_counter() - t0
             while nxt < len(requests) and requests[nxt].arrival <= now:
-                pending.append(requests[nxt])
+                r = requests[nxt]
                 nxt += 1
+                # a request that would not fit even in an empty arena can never be admitted:
+                # reject it on arrival rather than leave it pending for ever
+                if self._footprint(r.n) > self.arena.capacity:
+                    rejected.append(r)
+                else:
+                    pending.append(r)
             # completions (host polls the batch events; the GPU timestamp is the completion)
             still = []
             for evt, si, reqs, wsb in inflight:
@@ -229,6 +244,7 @@ class Server:
             if nxt >= len(requests) and not pending and not inflight:
                 break
             if time.perf_counter() - t0 > time_limit:
+                timed_out = True
                 break
             if not (free_streams and pending):
                 time.sleep(20e-6)
@@ -247,6 +263,12 @@ class Server:
             "arena_peak_bytes": self.arena.peak,
             "arena_bytes": self.arena_bytes,
             "wall_s": wall,
+            "rejected": len(rejected),
+            "time_limit_hit": timed_out,
+            # requests still waiting (never admitted) or not yet arrived when the run ended;
+            # the latency percentiles cover completed requests only
+            "pending_at_end": len(pending) + (len(requests) - nxt),
+            "inflight_at_end": sum(len(reqs) for _, _, reqs, _ in inflight),
         }
         return stats
 

@@ -120,3 +120,47 @@ def test_autotuned_batch_runs_every_instance_at_the_batch_B():
     for i, n in enumerate(sizes):
         want, _ = oracle.perm(n, 40 + i, B)
         assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), want), (i, n)
+
+
+def test_two_threads_batches_with_several_large_instances():
+    """Two host threads each run, on their own stream, batches with several instances above the
+    engine's limit (forked onto side streams and joined back). Each thread's side streams belong
+    to its own stream, so each batch's large instances start only after that thread's earlier
+    work on its stream: every thread first fills its buffers with a marker on its stream, and the
+    results must equal the single calls bit for bit on every round."""
+    import threading
+
+    import torch
+
+    B = 256
+    jobs = {0: [(1 << 22) + 5, (1 << 22) + 1001, 70_001], 1: [(1 << 22) + 77, (1 << 22) + 3, 999]}
+    outs, errs = {}, []
+
+    def work(tid, sizes):
+        try:
+            s = torch.cuda.Stream()
+            p = ms.params(B=B, flags=ms.MS_FLAG_PERM)
+            ptrs_t = [torch.empty(n, dtype=torch.int32, device="cuda") for n in sizes]
+            nbytes = ms.ms_batch_workspace_bytes(sizes, 4, p)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            ptrs = [t.data_ptr() for t in ptrs_t]
+            for rnd in range(3):
+                with torch.cuda.stream(s):
+                    for t in ptrs_t:
+                        t.fill_(-1 - rnd)
+                assert ms.ms_shuffle_batch(ptrs, sizes, 4, None, 40 + 10 * tid, ws.data_ptr(),
+                                           nbytes, p, s.cuda_stream) == ms.MS_OK
+            s.synchronize()
+            outs[tid] = [t.clone() for t in ptrs_t]
+        except Exception as e:  # pragma: no cover - reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(i, j)) for i, j in jobs.items()]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for tid, sizes in jobs.items():
+        for i, n in enumerate(sizes):
+            assert torch.equal(outs[tid][i], ms.perm(n, 40 + 10 * tid + i, B=B)), (tid, i)

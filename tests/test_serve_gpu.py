@@ -37,3 +37,17 @@ def test_overload_run_terminates():
     stats = srv.run(reqs, time_limit=300)
     assert stats["completed"] == len(reqs)
     assert stats["arena_peak_bytes"] <= srv.arena_bytes
+
+
+def test_request_larger_than_the_arena_is_rejected_not_left_pending():
+    """A request whose buffers cannot fit even an empty arena is rejected on arrival; the rest
+    are served, and the run ends without hitting its time limit."""
+    reqs = serve.make_requests(rate_hz=20_000, duration_s=0.002, lo_log2=10, hi_log2=12,
+                               seed_base=3)
+    huge = serve.Request(rid=len(reqs), n=1 << 24, seed=99, arrival=reqs[-1].arrival)
+    srv = serve.Server(arena_bytes=192 << 20, B=128, max_inflight=2)
+    assert srv._footprint(huge.n) > srv.arena_bytes
+    stats = srv.run(reqs + [huge], time_limit=60)
+    assert stats["rejected"] == 1
+    assert stats["completed"] == len(reqs)
+    assert not stats["time_limit_hit"] and stats["pending_at_end"] == 0

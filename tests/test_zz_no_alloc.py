@@ -62,12 +62,29 @@ def test_static_entry_point_rejects_sizes_beyond_its_scratch():
 
 
 def test_static_entry_point_at_its_size_limit():
-    """n = MS_STATIC_MAX_N with the default cutoff: the entry point runs the plan whose scratch
-    fits the fixed array (one data pass per global level) and still matches ms_perm."""
+    """n = MS_STATIC_MAX_N with the default cutoff: the plan's scratch (one data pass per global
+    level, the default for 4-byte elements) fits the fixed array, and the result matches
+    ms_perm."""
     import torch
 
     n = ms.MS_STATIC_MAX_N
     p = ms.params(B=1024)
+    assert ms.ms_workspace_bytes(n, 4, p) <= ms.MS_STATIC_SCRATCH_BYTES
     want = _perm_with_workspace(torch, n, 3, p)
     got = _perm_static(torch, n, 3, p)
+    assert np.array_equal(got, want)
+
+
+def test_static_entry_point_drops_fused_pairs_that_do_not_fit():
+    """Fused pairs of levels need more plan scratch than the fixed array holds at
+    n = MS_STATIC_MAX_N; the entry point then runs one data pass per level instead, which gives
+    the same permutation as ms_perm with the pairs."""
+    import torch
+
+    n = ms.MS_STATIC_MAX_N
+    p = ms.params(B=1024, flags=ms.MS_FLAG_PAIR_LEVELS)
+    assert ms.ms_workspace_bytes(n, 4, p) > ms.MS_STATIC_SCRATCH_BYTES
+    assert ms.plan(n, 4, B=1024, flags=ms.MS_FLAG_PAIR_LEVELS)["fused_pairs"] > 0
+    want = _perm_with_workspace(torch, n, 11, p)
+    got = _perm_static(torch, n, 11, p)
     assert np.array_equal(got, want)
