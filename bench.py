@@ -58,7 +58,12 @@ def parse():
                     help="seconds of 20k/s arrivals in the serving overload run")
     ap.add_argument("--serve-sub-rate", type=float, default=1500.0)
     ap.add_argument("--serve-sub-window", type=float, default=2.0)
+    ap.add_argument("--serve-inflight", type=int, default=4,
+                    help="launches the server keeps on the GPU at once (one stream each)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="scale workload only: skip the batched, batched-large and serving "
+                         "sub-objects of the default line")
     ap.add_argument("--workload", choices=["scale", "batched", "batched-large", "serve"],
                     default="scale")
     ap.add_argument("--small", action="store_true",
@@ -172,6 +177,25 @@ def measured_peaks() -> dict:
 GATHER_TRAFFIC_PER_ELEM = {4: 7.182, 16: 28.71}
 
 
+# the cutoffs the built-in tuning table resolves the scale workload to (the GPU arm checks it;
+# the reference arm uses them without loading the CUDA library)
+TUNED_B = {"perm": 512, "rec": 572}
+
+# kernel classes whose CUDA-event spans measure their own duration (launched in order on the
+# caller's stream), and those launched on the paired plan stream, whose spans also cover the time
+# they wait for SMs held by the data pass they overlap
+DATA_STREAM_KINDS = ("leaf", "gather", "pair_gather", "patch_read", "patch_write",
+                     "tail_sequential", "local")
+PLAN_STREAM_KINDS = ("count", "scan", "kscan", "hash_clear", "tail_insert", "tail_resolve",
+                     "exceptions")
+
+
+def perm_bytes(n: int, passes: int) -> int:
+    """Algorithmic HBM bytes of a perm: its first pass only writes (4n), every later pass reads
+    and writes the array (2 * 4n)."""
+    return (2 * passes - 1) * 4 * n if passes > 0 else 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -186,14 +210,15 @@ def run_ours(args, world, rank, local):
     n_perm = (1 << 26) if args.small else N_PERM
     n_rec = (1 << 24) + 17 if args.small else N_REC
     seed = SEED + rank
-    flags = ms.MS_FLAG_PROFILE
     # B = 0 resolves through the autotuner's table; the resolved parameters define the result
     fd_perm = args.fuse_depth if args.fuse_depth_perm is None else args.fuse_depth_perm
     fd_rec = args.fuse_depth if args.fuse_depth_rec is None else args.fuse_depth_rec
-    p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=fd_perm,
-                        tile_bytes=args.tile_bytes, flags=flags)
-    p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=fd_rec,
-                       tile_bytes=args.tile_bytes, flags=flags)
+    p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=fd_perm, tile_bytes=args.tile_bytes)
+    p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=fd_rec, tile_bytes=args.tile_bytes)
+    prof_perm = ms.params(p_perm.B, p_perm.fuse_depth, p_perm.flags | ms.MS_FLAG_PROFILE,
+                          p_perm.tile_bytes)
+    prof_rec = ms.params(p_rec.B, p_rec.fuse_depth, p_rec.flags | ms.MS_FLAG_PROFILE,
+                         p_rec.tile_bytes)
     # (the perm's plan, not the 4-byte shuffle's: a shuffle whose first pass is the tile kernel
     # may fuse one level less so that this pass does not run in place)
     plan_perm = ms.ms_plan_info(n_perm, 4, ms.params(p_perm.B, p_perm.fuse_depth,
@@ -220,17 +245,19 @@ def run_ours(args, world, rank, local):
         fork = torch.cuda.Event()
         join = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def step():
+    def step(profiled: bool, mid=None):
         if fork is not None:
             fork.record(stream)
             st_perm.wait_event(fork)
             st_rec.wait_event(fork)
         st = ms.ms_perm(out.data_ptr(), n_perm, seed, ws_perm.data_ptr(), ws_perm.numel(),
-                        p_perm, s_perm)
+                        prof_perm if profiled else p_perm, s_perm)
         if st != ms.MS_OK:
             raise ms.MsError(st, "ms_perm")
+        if mid is not None:
+            mid.record(stream)
         st = ms.ms_shuffle(rec.data_ptr(), n_rec, 16, seed, ws_rec.data_ptr(), ws_rec.numel(),
-                           p_rec, s_rec)
+                           prof_rec if profiled else p_rec, s_rec)
         if st != ms.MS_OK:
             raise ms.MsError(st, "ms_shuffle")
         if fork is not None:
@@ -240,55 +267,88 @@ def run_ours(args, world, rank, local):
             stream.wait_event(join[1])
 
     for _ in range(args.warmup):
-        step()
+        step(False)
+    step(True)  # the profiled variant's first call (events created outside the timed regions)
     torch.cuda.synchronize(dev)
     ms.profile(reset=True)
 
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    # timed region 1 (the headline): the plain calls, an event between the perm and the records
+    # of every step (on one stream: the perm's and the records' shares of the step)
     barrier(world)
     torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step(False, mid=evs[k][1] if fork is None else None)
+        evs[k][2].record(stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
-    clk = clocks.stop()
     t_ms = e0.elapsed_time(e1) / args.steps
+    t_perm_ms = t_rec_ms = None
+    if fork is None:
+        t_perm_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
+        t_rec_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
     t_ms = allreduce_max(t_ms, world)
+    # timed region 2: the same steps with an event pair around every kernel (MS_FLAG_PROFILE),
+    # for the per-kernel figures; its step time against region 1 is the profiling overhead
+    torch.cuda.synchronize(dev)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    e3.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t_prof_ms = e2.elapsed_time(e3) / args.steps
     prof = ms.profile(reset=True)
 
     elems = n_perm + n_rec
     value = world * elems / (t_ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    bw = peaks["hbm_gbs"]
 
     # roofline of the dominant kernel, the streaming gather of a global merge level (one
     # launch per unfused level): algorithmic bytes per launch = read n*w + write n*w. Fused
-    # pairs of levels (a pair_gather launch each, also one read and one write of the array) are
-    # reported beside it.
-    g = prof["gather"]
+    # pairs of levels (a pair_gather launch each, also one read and one write of the array) and
+    # the tile kernel (first pass: the perm only writes 4n, a shuffle reads and writes n*w) are
+    # reported beside it. Kernel times: CUDA events around each launch on the caller's stream.
+    g = prof.get("gather", {"ms": 0.0, "launches": 0})
     pg = prof.get("pair_gather", {"ms": 0.0, "launches": 0})
+    lf = prof.get("leaf", {"ms": 0.0, "launches": 0})
     single_perm = plan_perm.global_levels - 2 * plan_perm.fused_pairs
     single_rec = plan_rec.global_levels - 2 * plan_rec.fused_pairs
     gather_bytes = args.steps * (single_perm * 2 * n_perm * 4 + single_rec * 2 * n_rec * 16)
     pair_bytes = args.steps * (plan_perm.fused_pairs * 2 * n_perm * 4 +
                                plan_rec.fused_pairs * 2 * n_rec * 16)
-    peaks = measured_peaks()
+    tile_bytes = args.steps * (4 * n_perm + 2 * 16 * n_rec)
     achieved = gather_bytes / (g["ms"] * 1e-3) / 1e9 if g["ms"] > 0 else 0.0
     nlaunch = single_perm + single_rec
     traffic = ((single_perm * GATHER_TRAFFIC_PER_ELEM[4] * n_perm +
                 single_rec * GATHER_TRAFFIC_PER_ELEM[16] * n_rec) / nlaunch) if nlaunch else None
+    path_perm = perm_bytes(n_perm, plan_perm.passes)
+    path_rec = plan_rec.passes * 2 * n_rec * 16
+    path_perm_unfused = perm_bytes(n_perm, plan_perm.passes + plan_perm.fused_pairs)
+    path_rec_unfused = (plan_rec.passes + plan_rec.fused_pairs) * 2 * n_rec * 16
+
+    def frac(nbytes, ms_):
+        return round(nbytes / 1e9 / (ms_ * 1e-3) / bw, 4) if ms_ else None
+
     roofline = {
         "bound": "hbm",
         "kernel": "gather (HBM merge level)",
         "achieved": round(achieved, 1),
-        "peak": peaks["hbm_gbs"],
+        "peak": bw,
         "peak_source": peaks["source"],
         "unit": "GB/s",
-        "frac": round(achieved / peaks["hbm_gbs"], 4),
+        "frac": round(achieved / bw, 4),
         "traffic": round(traffic) if traffic else None,
         "traffic_note": "bytes per gather launch (dram read+write), ncu on a smaller case "
                         "scaled by elements; the small case leaves ~50 MB of writes in L2",
@@ -298,18 +358,29 @@ def run_ours(args, world, rank, local):
         "pair_gather": {
             "launches_per_step": {"perm": plan_perm.fused_pairs, "rec": plan_rec.fused_pairs},
             "achieved_gbs": round(pair_bytes / (pg["ms"] * 1e-3) / 1e9, 1) if pg["ms"] else None,
+            "frac": frac(pair_bytes, pg["ms"]),
         },
-        "whole_path_frac": round(
-            (plan_perm.passes * 2 * n_perm * 4 + plan_rec.passes * 2 * n_rec * 16) / 1e9
-            / (t_ms * 1e-3) / peaks["hbm_gbs"], 4),
-        "whole_path_frac_unfused": round(
-            ((plan_perm.passes + plan_perm.fused_pairs) * 2 * n_perm * 4 +
-             (plan_rec.passes + plan_rec.fused_pairs) * 2 * n_rec * 16) / 1e9
-            / (t_ms * 1e-3) / peaks["hbm_gbs"], 4),
+        "tile": {
+            "kernel": "tile kernel (Fisher-Yates and the first d merge levels, one pass)",
+            "algorithmic_bytes_per_step": {"perm": 4 * n_perm, "rec": 2 * 16 * n_rec},
+            "ms_per_step": round(lf["ms"] / args.steps, 3),
+            "achieved_gbs": round(tile_bytes / (lf["ms"] * 1e-3) / 1e9, 1) if lf["ms"] else None,
+            "frac": frac(tile_bytes, lf["ms"]),
+        },
+        # whole path: (algorithmic bytes of all passes / peak) / time; the perm's first pass
+        # writes only. "fused" counts a fused pair (and the tile kernel's levels) as one pass,
+        # "unfused" every global level as a pass.
+        "whole_path_bytes_per_step": {"perm": path_perm, "rec": path_rec},
+        "whole_path_frac": frac(path_perm + path_rec, t_ms),
+        "whole_path_frac_unfused": frac(path_perm_unfused + path_rec_unfused, t_ms),
+        "whole_path_frac_perm": frac(path_perm, t_perm_ms),
+        "whole_path_frac_rec": frac(path_rec, t_rec_ms),
     }
-    kernel_ms = {k: round(v["ms"] / args.steps, 3) for k, v in prof.items() if v["launches"]}
+    kernel_ms = {k: round(prof[k]["ms"] / args.steps, 3) for k in DATA_STREAM_KINDS
+                 if k in prof and prof[k]["launches"]}
+    plan_ms = {k: round(prof[k]["ms"] / args.steps, 3) for k in PLAN_STREAM_KINDS
+               if k in prof and prof[k]["launches"]}
     launches = args.steps * (plan_perm.kernel_launches + plan_rec.kernel_launches)
-
     # end to end through the host-buffer entry points: H2D of the input, the shuffle, D2H of
     # the result, every step
     e2e = None
@@ -319,10 +390,8 @@ def run_ours(args, world, rank, local):
         hp = torch.empty(n_perm, dtype=torch.int32, pin_memory=True)
         hr = torch.empty((n_rec, 4), dtype=torch.int32, pin_memory=True)
         hr.copy_(rec_host)
-        q_perm = ms.params(B=p_perm.B, fuse_depth=p_perm.fuse_depth, tile_bytes=args.tile_bytes,
-                           flags=p_perm.flags & ~ms.MS_FLAG_PROFILE)
-        q_rec = ms.params(B=p_rec.B, fuse_depth=p_rec.fuse_depth, tile_bytes=args.tile_bytes,
-                          flags=p_rec.flags & ~ms.MS_FLAG_PROFILE)
+        q_perm = p_perm
+        q_rec = p_rec
         wsh_perm = torch.empty(ms.ms_host_workspace_bytes(n_perm, 4, q_perm), dtype=torch.uint8,
                                device=dev)
         wsh_rec = torch.empty(ms.ms_host_workspace_bytes(n_rec, 16, q_rec), dtype=torch.uint8,
@@ -397,6 +466,8 @@ def run_ours(args, world, rank, local):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(t_ms, 3),
+        "ms_per_step_perm": round(t_perm_ms, 3) if t_perm_ms else None,
+        "ms_per_step_rec": round(t_rec_ms, 3) if t_rec_ms else None,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -415,18 +486,43 @@ def run_ours(args, world, rank, local):
             "l2": "inputs larger than L2 (4.3 GB and 4.8 GB arrays), no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
             "overlap": args.overlap,
-            "profiled_events": "CUDA event pair around every kernel during the timed region",
+            "timed": "value and ms_per_step: the plain calls; the per-kernel figures come from "
+                     "a second timed region of the same steps with a CUDA event pair around "
+                     "every kernel (MS_FLAG_PROFILE)",
+            "ms_per_step_profiled": round(t_prof_ms, 3),
         },
         "roofline": roofline,
         "kernel_ms_per_step": kernel_ms,
+        "plan_stream_event_ms_per_step": plan_ms,
+        "plan_stream_note": "the plan kernels run on a second stream beside the data passes; "
+                            "their event spans include the time they wait for SMs, so they "
+                            "overlap the data-stream figures and do not add up with them",
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "random_bits": bits,
     }
+    if not args.small and args.B_perm == 0 and args.B_rec == 0:
+        line["config"]["B_matches_reference_arm"] = (p_perm.B == TUNED_B["perm"] and
+                                                     p_rec.B == TUNED_B["rec"])
+    if world == 1 and not args.small and not args.no_extra:
+        # the batched, batched-large and served forms, each against one launch per instance
+        # (one request at a time), on the same GPU after the scale workload's buffers are freed
+        del out, rec
+        if e2e is not None:
+            del hp, hr, wsh_perm, wsh_rec  # (the e2e leg already freed ws_perm and ws_rec)
+        else:
+            del ws_perm, ws_rec
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        ks, kw = max(3, min(args.steps, 10)), 3
+        line["batched"] = run_batched(args, large=False, steps=ks, warmup=kw)
+        line["batched_large"] = run_batched(args, large=True, steps=ks, warmup=kw)
+        line["serve"] = run_serve(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
 
 
 # ------------------------------------------------------------------ CPU oracle --------------
@@ -444,7 +540,7 @@ def cpu_baseline(B_perm: int, B_rec: int) -> dict:
     oracle.shuffle(rec, SEED, B_rec)
     dt = time.perf_counter() - t0
     return {"value": round((n1 + n2) / dt / 1e9, 6), "unit": "Gelem/s", "cores": 1,
-            "kind": "oracle",
+            "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"perm(2^26) u32 + shuffle(2^24) 16-byte records, B={B_perm}/{B_rec}, "
                       f"single-threaded C oracle, {dt:.1f} s"}
 
@@ -454,15 +550,15 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
-    import paper_1508_03167_gb300 as ms
     from paper_1508_03167_gb300 import inputs
 
     n1 = 1 << 21
     n2 = 1 << 19
     rec = inputs.records16(n2)
-    # the B the GPU arm runs the full-size workload with (host-side table lookup, no GPU)
-    B_perm = ms.resolve(N_PERM, 4, B=args.B_perm).B
-    B_rec = ms.resolve(N_REC, 16, B=args.B_rec).B
+    # the B the GPU arm runs the full-size workload with (the tuning table's choice, which the
+    # GPU arm checks); this arm never loads the CUDA library
+    B_perm = args.B_perm or TUNED_B["perm"]
+    B_rec = args.B_rec or TUNED_B["rec"]
 
     def step():
         oracle.perm(n1, SEED, B_perm)
@@ -496,7 +592,7 @@ def run_reference(args, world, rank):
                    "B_perm": B_perm, "B_rec": B_rec,
                    "sample": {"n_perm": n1, "n_rec": n2}},
         "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "cores": 1,
-                         "kind": "oracle", "sample": sample},
+                         "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -525,7 +621,7 @@ def _timed_graph(torch, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_batched(args, large: bool):
+def run_batched(args, large: bool, steps: int | None = None, warmup: int | None = None) -> dict:
     """4096 perm(n_i), n_i log-uniform in [2^6, 2^20], seed_i = 1 + i (batched), or 64 shuffles
     of uint64 arrays, n_i uniform in [10^6, 10^8] non-power-of-two (batched-large); one prepared
     batch replayed from a CUDA graph, against one launch sequence per instance."""
@@ -534,6 +630,8 @@ def run_batched(args, large: bool):
     import paper_1508_03167_gb300 as ms
     from paper_1508_03167_gb300 import inputs
 
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     if large:
         sizes = [int(x) for x in inputs.batch_sizes_uniform(64, 10**6, 10**8)]
         w, B, flags = 8, args.B_rec, 0
@@ -565,7 +663,7 @@ def run_batched(args, large: bool):
     with torch.cuda.stream(s0):
         prep(s0)
     s0.synchronize()
-    t_batch = _timed_graph(torch, run, args.steps, args.warmup)
+    t_batch = _timed_graph(torch, run, steps, warmup)
     # one launch sequence per instance (the same library, no batching)
     q = ms.params(B=B)
     wss = torch.empty(max(ms.ms_workspace_bytes(n, w, q) for n in sizes), dtype=torch.uint8,
@@ -591,9 +689,20 @@ def run_batched(args, large: bool):
     e1.record()
     torch.cuda.synchronize()
     t_single = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
-    line = {
+    # roofline: algorithmic bytes of the batch over its time and the measured copy peak; the
+    # one-pass bound moves each instance once (a perm only writes it), the pass-counted figure
+    # charges every instance the HBM passes of its single-call plan at the batch's B
+    bw = measured_peaks()["hbm_gbs"]
+    one_pass = sum((4 * n) if not large else (2 * w * n) for n in sizes)
+    passes = 0
+    for n in sizes:
+        pl = ms.ms_plan_info(n, w, ms.params(B=B, flags=flags))
+        passes += perm_bytes(n, pl.passes) if not large else pl.passes * 2 * w * n
+    del wss, ws, bufs
+    torch.cuda.empty_cache()
+    return {
         "metric": "Gelem/s", "value": round(total / (t_batch * 1e-3) / 1e9, 4),
-        "unit": "Gelem/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": "Gelem/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
         "ms_per_step": round(t_batch, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32" if not large else "u64", "data": "synthetic",
         "config": {
@@ -605,15 +714,21 @@ def run_batched(args, large: bool):
             "graph": "prepared batch replayed from one CUDA graph",
             "device_bytes": int(nbytes + sum(n * w for n in sizes)),
         },
+        "roofline": {
+            "bound": "hbm", "peak": bw, "unit": "GB/s",
+            "one_pass_bytes": one_pass,
+            "one_pass_frac": round(one_pass / 1e9 / (t_batch * 1e-3) / bw, 4),
+            "passes_bytes": passes,
+            "passes_frac": round(passes / 1e9 / (t_batch * 1e-3) / bw, 4),
+        },
         "per_launch": {"ms": round(t_single, 3),
                        "gelem_per_s": round(total / (t_single * 1e-3) / 1e9, 4),
                        "how": "one ms_perm / ms_shuffle launch sequence per instance"},
         "speedup_vs_per_launch": round(t_single / t_batch, 2),
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def run_serve(args) -> dict:
     """Poisson arrivals of perm(n) requests, n log-uniform in [2^10, 2^26], own seeds, under a
     40 GB device-memory cap: the offered 20k req/s (about 121 Gelem/s) overloads one GPU, so the
     window is short; a sub-saturation rate is served too, and one-at-a-time is the baseline."""
@@ -633,27 +748,38 @@ def run_serve(args):
     for tag, rate, dur in (("overload_20k_per_s", 20_000, args.serve_window),
                            ("sub_saturation", args.serve_sub_rate, args.serve_sub_window)):
         reqs = serve.make_requests(rate, dur, 10, 26, seed_base=1)
-        srv = serve.Server(arena_bytes=cap, B=B, max_inflight=4)
+        srv = serve.Server(arena_bytes=cap, B=B, max_inflight=args.serve_inflight)
         st = srv.run(reqs, time_limit=600)
         del srv
         torch.cuda.empty_cache()
         st["offered_rate_per_s"] = rate
         st["window_s"] = dur
+        st["limiter"] = ("device memory (the arena held its cap)"
+                         if st["arena_peak_bytes"] > 0.9 * cap else
+                         f"launch slots (max_inflight = {args.serve_inflight}; the arena peaked "
+                         f"at {st['arena_peak_bytes'] / 2**30:.2f} of "
+                         f"{cap / 2**30:.0f} GiB)")
         out[tag] = st
     reqs = serve.make_requests(args.serve_sub_rate, args.serve_sub_window, 10, 26, seed_base=1)
     out["one_at_a_time_sub_saturation"] = serve.one_at_a_time(reqs, B=B)
     reqs = serve.make_requests(20_000, args.serve_window, 10, 26, seed_base=1)
     out["one_at_a_time_overload_20k_per_s"] = serve.one_at_a_time(reqs, B=B)
-    line = {
-        "metric": "Gelem/s", "value": round(out["overload_20k_per_s"]["gelem_per_s"], 4),
+    ov, one = out["overload_20k_per_s"], out["one_at_a_time_overload_20k_per_s"]
+    return {
+        "metric": "Gelem/s", "value": round(ov["gelem_per_s"], 4),
         "unit": "Gelem/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "dtype": "u32",
         "config": {"workload": "serving: Poisson perm(n) requests, n log-uniform in "
                                "[2^10, 2^26], own seeds, 40 GB device-memory cap, continuous "
-                               "batching over 4 streams (small requests batched, large alone)", "B": B},
+                               f"batching over {args.serve_inflight} streams (small requests "
+                               "batched, large alone)", "B": B,
+                   "window_note": f"{args.serve_window} s of the 20k/s arrivals (the offered "
+                                  "load, about 121 Gelem/s, is above what one GPU serves, so "
+                                  "the queue and the tail latency grow with the window)"},
+        "p50_s": ov["latency_s"]["p50"], "p99_s": ov["latency_s"]["p99"],
+        "speedup_vs_one_at_a_time": round(ov["gelem_per_s"] / one["gelem_per_s"], 2),
         "serving": out,
     }
-    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -662,11 +788,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batched":
-        run_batched(args, large=False)
+        print(json.dumps(run_batched(args, large=False)), flush=True)
     elif args.workload == "batched-large":
-        run_batched(args, large=True)
+        print(json.dumps(run_batched(args, large=True)), flush=True)
     elif args.workload == "serve":
-        run_serve(args)
+        print(json.dumps(run_serve(args)), flush=True)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -8,8 +8,7 @@
 //     k; the warps split its positions). A draw whose first Philox word rejects all its slices
 //     is queued by its thread and finished after the loop, so no lane holds its warp up with a
 //     second Philox block inline;
-//   * Algorithm 1's swap chain per block, resolved from those draws without running it: one
-//     pipelined last-writer pass per block, then every position in parallel;
+//   * Algorithm 1's swap chain per block, reading those draws;
 //   * per merge level: coin words and their zero prefix, the break step T of every merge,
 //     the stable interleave (a lane places eight consecutive positions, walking the two
 //     halves with one index each), the tail draws, and the random insertions of Algorithm 3's
@@ -214,11 +213,6 @@ constexpr uint32_t kTileThreads = 32u * kTileWarps;
 constexpr uint32_t kTileMinBlocks = kTileWarps == 4u ? 5u : 4u;  // CTAs an SM the registers allow
 // queued second-word Fisher-Yates draws per thread and block group (4 KB of queues in all)
 constexpr uint32_t kFailPerThread = 32u / kTileWarps;
-// the Fisher-Yates resolution's 16-bit markers: an empty last-writer entry, and the flag of a
-// step with no later writer of its target (positions and steps stay below 2^15: a block of a
-// tile below 2^16 elements with d >= 1 holds at most 32,767)
-constexpr uint32_t kFyNone = 0xFFFFu;
-constexpr uint32_t kFyDirect = 0x8000u;
 
 template <typename E, bool kPerm>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(TileArgs a) {
@@ -261,15 +255,14 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
     __syncthreads();
 
     // ---- Algorithm 1's draws (warp w: quads w, w + kTileWarps, ... of every block; lane: the
-    // block). D[i] (the first buffer) receives the draw j_i of step i; the second buffer, the
-    // last-writer table of the resolution below, starts empty.
+    // block)
     for (uint32_t kg = 0; kg < nb; kg += 32u) {
       const uint32_t k = kg + lane;
       const bool act = k < nb;
       const uint32_t off = act ? boff[k] : 0u;
       const uint32_t L = act ? boff[k + 1u] - off : 0u;
-      uint16_t *const D = bufA + k * a.P;  // D[i]: the draw of position i
-      uint16_t *const W = bufB + k * a.P;  // last-writer table
+      uint16_t *const A = bufA + k * a.P;
+      uint16_t *const D = bufB + k * a.P;  // D[i]: the draw of position i
       uint32_t *const F = flist + tid * kFailPerThread;
       const uint32_t id = static_cast<uint32_t>(k0 + k);
       const uint32_t nq = L ? ((L - 1u) >> 2) + 1u : 0u;
@@ -284,7 +277,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
         for (uint32_t v = 0; v < 4u; ++v) {
           const uint32_t pos = 4u * qd + v;
           if (pos < L) {
-            W[pos] = kFyNone;
+            A[pos] = static_cast<uint16_t>(off + pos);
             if (pos >= 1u) {
               uint32_t x;
               const uint32_t word = pick_word(blk, v);
@@ -310,48 +303,27 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
     }
     __syncthreads();
 
-    // ---- Algorithm 1's swap chain, resolved without running it. Steps go i = L-1 .. 1 and step
-    // i swaps positions i and j_i <= i, so position i is final after step i and receives what
-    // position j_i held just before it. Let F(p) = min{k > p : j_k = p}, the last step to write
-    // position p before step p runs, and NX(i) = min{k > i : j_k = j_i}, the last step to write
-    // position j_i before step i. Then the value position p holds just before step p is
-    // g(p) = g(F(p)) if F(p) exists, else p (its own index), and
-    //   final[i] = g(NX(i)) if NX(i) exists, else j_i        (i >= 1)
-    //   final[0] = g(F(0))  if F(0) exists,  else 0.
-    // One descending pass per block (one lane per block: the data warp, and a helper for blocks
-    // 32..63) finds both with a last-writer table W: at step i, NX(i) = W[j_i] before W[j_i] = i
-    // (skipped when j_i = i: no later step can target position i), so at the end W[p] = F(p).
-    // The pass carries no register dependency from step to step (its loads and stores are
-    // ordered by shared memory itself), so eight steps are issued back to back. D[i] then holds
-    // NX(i), or j_i | kFyDirect when there is none. Meanwhile the control warp builds level 0's
-    // control data.
+    // ---- Algorithm 1's swaps, i = L-1 .. 1 (blocks 0..31: the data warp, 32..63: a helper; the
+    // draws are read four ahead of the chain and clamped to the block); meanwhile the control
+    // warp builds level 0's control data
     if (role == 0u || role == 2u) {
       const uint32_t k = (role == 0u ? 0u : 32u) + lane;
       const uint32_t L = k < nb ? boff[k + 1u] - boff[k] : 0u;
-      uint16_t *const D = bufA + k * a.P;
-      uint16_t *const W = bufB + k * a.P;
-      uint32_t i = L;  // steps i-1, i-2, ... remain (down to 1)
-      while (i >= 9u) {
-        uint32_t j[8], f[8];
-#pragma unroll
-        for (uint32_t u = 0; u < 8u; ++u) j[u] = min(static_cast<uint32_t>(D[i - 1u - u]), i - 1u - u);
-#pragma unroll
-        for (uint32_t u = 0; u < 8u; ++u) {
-          f[u] = W[j[u]];
-          if (j[u] != i - 1u - u) W[j[u]] = static_cast<uint16_t>(i - 1u - u);
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 8u; ++u)
-          D[i - 1u - u] = static_cast<uint16_t>(f[u] != kFyNone ? f[u] : (j[u] | kFyDirect));
-        i -= 8u;
+      uint16_t *const A = bufA + k * a.P;
+      const uint16_t *const D = bufB + k * a.P;
+      uint32_t i = L;
+      while (i >= 5u) {
+        const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
+        const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
+        const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
+        const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
+        swap_smem(A, i - 1u, j0);
+        swap_smem(A, i - 2u, j1);
+        swap_smem(A, i - 3u, j2);
+        swap_smem(A, i - 4u, j3);
+        i -= 4u;
       }
-      for (; i >= 2u; --i) {
-        const uint32_t s = i - 1u;
-        const uint32_t jj = min(static_cast<uint32_t>(D[s]), s);
-        const uint32_t ff = W[jj];
-        if (jj != s) W[jj] = static_cast<uint16_t>(s);
-        D[s] = static_cast<uint16_t>(ff != kFyNone ? ff : (jj | kFyDirect));
-      }
+      for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
     } else {
       // the other roles (1 and 3 .. kTileWarps-1): level 0's control data (role 1), then its
       // tail draws
@@ -360,35 +332,6 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
       control_barrier((kTileWarps - 2u) * 32u);
       tail_draws(a.key, a.d, 0u, k0, (role == 1u ? 0u : role - 2u) * 32u + lane,
                  (kTileWarps - 2u) * 32u, c0.mv, c0.m);
-    }
-    __syncthreads();
-    // every position of every block: walk F from NX(i) (or F(0)) to the end of its run and write
-    // the tile-local index (block start + position) over D. F(p) > p, so a walk ends within the
-    // block; it takes about one step on average.
-    for (uint32_t e = tid; e < nb * 32u; e += kTileThreads) {
-      const uint32_t k = e >> 5;
-      const uint32_t off = boff[k];
-      const uint32_t L = boff[k + 1u] - off;
-      uint16_t *const D = bufA + k * a.P;
-      const uint16_t *const W = bufB + k * a.P;
-      for (uint32_t pos = e & 31u; pos < L; pos += 32u) {
-        uint32_t x = pos ? static_cast<uint32_t>(D[pos]) : static_cast<uint32_t>(W[0]);
-        uint32_t val;
-        if (pos == 0u && x == kFyNone) {
-          val = 0u;
-        } else if (pos != 0u && (x & kFyDirect)) {
-          val = x & (kFyDirect - 1u);
-        } else {
-          x = min(x, L - 1u);
-          for (uint32_t h = 0; h < L; ++h) {
-            const uint32_t y = W[x];
-            if (y == kFyNone) break;
-            x = min(y, L - 1u);
-          }
-          val = x;
-        }
-        D[pos] = static_cast<uint16_t>(off + val);
-      }
     }
     __syncthreads();
 
