@@ -33,6 +33,8 @@ PLANT_NO_TAIL = 64
 TAG_COIN = 1
 TAG_TAIL = 2
 TAG_LEAF = 3
+TAG_RS_COIN = 4
+TAG_RS_LEAF = 5
 
 _lock = threading.Lock()
 _lib = None
@@ -107,6 +109,12 @@ def _load():
     lib.ms_oracle_enumerate.restype = i32
     lib.ms_oracle_enumerate_merge.argtypes = [u32, u32, i32, vp, vp, p64]
     lib.ms_oracle_enumerate_merge.restype = i32
+    lib.ms_oracle_rs_shuffle.argtypes = [vp, u64, u32, u64, u32, i32, ctypes.POINTER(Stats)]
+    lib.ms_oracle_rs_shuffle.restype = i32
+    lib.ms_oracle_rs_perm.argtypes = [vp, u64, u64, u32, i32, ctypes.POINTER(Stats)]
+    lib.ms_oracle_rs_perm.restype = i32
+    lib.ms_oracle_enumerate_rs.argtypes = [u32, u32, u32, i32, vp, vp, p64, vp]
+    lib.ms_oracle_enumerate_rs.restype = i32
     _lib = lib
     return lib
 
@@ -203,3 +211,46 @@ def enumerate_merge(a: int, b: int, mode: int = STABLE) -> tuple[list[int], int,
     if rc != 0:
         raise RuntimeError(f"ms_oracle_enumerate_merge failed with code {rc}")
     return _u128(num), _u128(den)[0], int(paths.value)
+
+
+# ------------------------------------------------------------------ splitting process --------
+def rs_shuffle(data: np.ndarray, seed: int, B: int, mode: int = PHILOX) -> tuple[np.ndarray, Stats]:
+    """Rao-Sandelius splitting process with Fisher-Yates cutoff B on a copy of `data` (first axis
+    = the n elements). Stats: coin_bits (bits of the splits), merges (number of splits), levels
+    (split levels), leaf_bits / leaf_draws (Fisher-Yates)."""
+    arr = np.ascontiguousarray(data).copy()
+    n = arr.shape[0]
+    w = arr.nbytes // n if n else 1
+    st = Stats()
+    rc = _load().ms_oracle_rs_shuffle(arr.ctypes.data, n, w, seed, B, mode, ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"ms_oracle_rs_shuffle failed with code {rc}")
+    return arr, st
+
+
+def rs_perm(n: int, seed: int, B: int, mode: int = PHILOX) -> tuple[np.ndarray, Stats]:
+    out = np.empty(n, dtype=np.uint32)
+    st = Stats()
+    rc = _load().ms_oracle_rs_perm(out.ctypes.data, n, seed, B, mode, ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"ms_oracle_rs_perm failed with code {rc}")
+    return out, st
+
+
+def enumerate_rs(n: int, B: int, max_levels: int, mode: int = 0
+                 ) -> tuple[list[int], int, int, int]:
+    """Exact walk of the splitting process on the identity of size n <= 6, cut at max_levels
+    split levels. Returns (numerators by Lehmer rank over paths that finish, denominator, leaves,
+    numerator of the cut-off paths)."""
+    import math
+
+    nf = math.factorial(n)
+    num = np.zeros(2 * nf, dtype=np.uint64)
+    den = np.zeros(2, dtype=np.uint64)
+    unres = np.zeros(2, dtype=np.uint64)
+    paths = ctypes.c_uint64(0)
+    rc = _load().ms_oracle_enumerate_rs(n, B, max_levels, mode, num.ctypes.data,
+                                        den.ctypes.data, ctypes.byref(paths), unres.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"ms_oracle_enumerate_rs failed with code {rc}")
+    return _u128(num), _u128(den)[0], int(paths.value), _u128(unres)[0]

@@ -23,6 +23,10 @@
  *   tags     : TAIL (2) for the random insertions of merge `id` on `level` (pos = position in
  *              the merged range); LEAF (3) for the Fisher-Yates draws of base block `id`
  *              (level 0, pos = the index i of Algorithm 1).
+ *   splitting process (Rao-Sandelius, below): RS_COIN (4), the bit of position p on split level
+ *              l is bit (p mod 32) of word ((p / 32) mod 4) of Philox((p / 128, 0, (4 << 16) | l,
+ *              0)); RS_LEAF (5), the Fisher-Yates draws of the final segment starting at s
+ *              (level 0, id = s, pos = i).
  * ---------------------------------------------------------------------------------------
  */
 #include "ms_oracle.h"
@@ -65,6 +69,8 @@ void ms_oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 typedef struct ms_src ms_src;
 struct ms_src {
   int (*coin)(ms_src *s, uint32_t level, uint32_t id, uint64_t t);
+  /* a coin of another stream than the merges' (the splitting process): tag, level, id, t */
+  int (*tcoin)(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t t);
   uint64_t (*uniform)(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t pos,
                       uint64_t R, uint64_t *bits);
   int failed;
@@ -97,6 +103,13 @@ static int philox_coin(ms_src *s, uint32_t level, uint32_t id, uint64_t t) {
   philox_src *p = (philox_src *)s;
   const uint32_t *blk = philox_block(p, (uint32_t)(t >> 7), id,
                                      ((uint32_t)MS_ORACLE_TAG_COIN << 16) | level, 0);
+  uint32_t word = blk[(t >> 5) & 3];
+  return (int)((word >> (t & 31)) & 1u);
+}
+
+static int philox_tcoin(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t t) {
+  philox_src *p = (philox_src *)s;
+  const uint32_t *blk = philox_block(p, (uint32_t)(t >> 7), id, (tag << 16) | level, 0);
   uint32_t word = blk[(t >> 5) & 3];
   return (int)((word >> (t & 31)) & 1u);
 }
@@ -154,6 +167,11 @@ static uint32_t seq_bit(seq_src *q) {
 static int seq_coin(ms_src *s, uint32_t level, uint32_t id, uint64_t t) {
   (void)level; (void)id; (void)t;
   return (int)seq_bit((seq_src *)s);
+}
+
+static int seq_tcoin(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t t) {
+  (void)tag;
+  return seq_coin(s, level, id, t);
 }
 
 /* Fast Dice Roller: keep c uniform on [0, v); each bit doubles v; once v >= R, return c if
@@ -332,9 +350,95 @@ static int run_mergeshuffle(ms_src *src, unsigned char *data, uint64_t n, uint32
   return src->failed ? 1 : 0;
 }
 
+/* ------------------------------------------------------------------ splitting process --- */
+/* The Rao-Sandelius splitting process (the introduction's passage on splitting processes, after
+ * Flajolet et al.; Table 1's third row), with R = 2 parts and a Fisher-Yates cutoff B (the
+ * paper names the cutoff idea for MergeShuffle; here it plays the same role):
+ *   start with the single segment [0, n); on level l = 0, 1, ..., every segment [s, e) with more
+ *   than B elements draws one fair bit per element, the bit of its current position p
+ *   (stream RS_COIN: bit p mod 32 of word (p / 32) mod 4 of Philox((p / 128, 0,
+ *   (RS_COIN << 16) | l, 0))), and is split stably: the elements with bit 0 keep their order
+ *   and come first, then those with bit 1. Segments of at most B elements no longer change. Once
+ *   no segment has more than B elements, each segment [s, e) is shuffled by Algorithm 1 with the
+ *   draws of stream (RS_LEAF, level 0, id = s, pos = i).
+ * Each element draws an independent fresh bit per level while its segment splits (its position
+ * is a function of earlier bits only), so the ordered partition into segments is exchangeable
+ * and the shuffled segments make a uniform permutation. Levels stop after max_levels with code
+ * 5 if a segment is still above B (the walk below bounds its depth that way). */
+static void rs_fisher_yates(ms_src *src, unsigned char *a, uint64_t len, uint32_t w, uint32_t id,
+                            ms_oracle_stats *st) {
+  for (uint64_t i = len; i-- > 1;) {
+    uint64_t bits = 0;
+    uint64_t R = (src->plant & MS_ORACLE_PLANT_FY_RANGE) ? i : i + 1;
+    uint64_t j = src->uniform(src, MS_ORACLE_TAG_RS_LEAF, 0, id, i, R, &bits);
+    st->leaf_bits += bits;
+    st->leaf_draws += 1;
+    swap_elems(a, i, j, w);
+  }
+}
+
+static int run_rao_sandelius(ms_src *src, unsigned char *data, uint64_t n, uint32_t w,
+                             uint32_t B, uint32_t max_levels, ms_oracle_stats *st) {
+  if (n <= 1) return 0;
+  /* segment boundaries in order: seg[0] = 0 < ... < seg[count] = n (empty segments dropped) */
+  uint64_t cap = 2, count = 1;
+  uint64_t *seg = (uint64_t *)malloc((cap + 1) * sizeof(uint64_t));
+  unsigned char *tmp = (unsigned char *)malloc(n * w);
+  unsigned char *bitv = (unsigned char *)malloc(n);
+  if (!seg || !tmp || !bitv) { free(seg); free(tmp); free(bitv); return 2; }
+  seg[0] = 0;
+  seg[1] = n;
+  int rc = 0;
+  for (uint32_t level = 0;; ++level) {
+    int active = 0;
+    for (uint64_t k = 0; k < count; ++k)
+      if (seg[k + 1] - seg[k] > B) active = 1;
+    if (!active) break;
+    if (level >= max_levels) { rc = 5; break; }
+    uint64_t *next = (uint64_t *)malloc((2 * count + 1) * sizeof(uint64_t));
+    if (!next) { rc = 2; break; }
+    uint64_t m = 0;
+    next[m] = 0;
+    for (uint64_t k = 0; k < count; ++k) {
+      uint64_t s = seg[k], e = seg[k + 1];
+      if (e - s > B) {
+        /* stable split by the bit of each position: zeros to the front, ones after them */
+        uint64_t z = 0;
+        for (uint64_t p = s; p < e; ++p) {  /* each bit drawn once, in position order */
+          bitv[p] = (unsigned char)src->tcoin(src, MS_ORACLE_TAG_RS_COIN, level, 0, p);
+          if (bitv[p] == 0) ++z;
+        }
+        uint64_t zi = s, oi = s + z;
+        for (uint64_t p = s; p < e; ++p)
+          memcpy(tmp + (bitv[p] ? oi++ : zi++) * w, data + p * w, w);
+        memcpy(data + s * w, tmp + s * w, (e - s) * w);
+        st->coin_bits += e - s;
+        st->merges += 1; /* splits */
+        if (z > 0) next[++m] = s + z;
+        if (z < e - s) next[++m] = e;
+      } else {
+        next[++m] = e;
+      }
+    }
+    free(seg);
+    seg = next;
+    count = m;
+    st->levels = level + 1;
+  }
+  if (rc == 0)
+    for (uint64_t k = 0; k < count; ++k)
+      rs_fisher_yates(src, data + seg[k] * w, seg[k + 1] - seg[k], w, (uint32_t)seg[k], st);
+  free(seg);
+  free(tmp);
+  free(bitv);
+  if (rc == 0 && src->failed) rc = 1;
+  return rc;
+}
+
 static void init_philox(philox_src *p, uint64_t seed) {
   memset(p, 0, sizeof *p);
   p->base.coin = philox_coin;
+  p->base.tcoin = philox_tcoin;
   p->base.uniform = philox_uniform;
   p->seed = seed;
 }
@@ -342,6 +446,7 @@ static void init_philox(philox_src *p, uint64_t seed) {
 static void init_seq(seq_src *q, uint64_t seed) {
   memset(q, 0, sizeof *q);
   q->base.coin = seq_coin;
+  q->base.tcoin = seq_tcoin;
   q->base.uniform = seq_uniform;
   q->seed = seed;
 }
@@ -410,6 +515,29 @@ int ms_oracle_merge(uint32_t *a, uint64_t n1, uint64_t n2, uint64_t seed, uint32
   return src->failed ? 1 : 0;
 }
 
+int ms_oracle_rs_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_t B, int mode,
+                         ms_oracle_stats *st) {
+  ms_oracle_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof *st);
+  if (w == 0 || w > 64 || B == 0) return 3;
+  if (n > 0xFFFFFFFFull) return 3;
+  if (mode & MS_ORACLE_SEQFDR) {
+    seq_src q;
+    init_seq(&q, seed);
+    return run_rao_sandelius(&q.base, (unsigned char *)data, n, w, B, 4096, st);
+  }
+  philox_src p;
+  init_philox(&p, seed);
+  return run_rao_sandelius(&p.base, (unsigned char *)data, n, w, B, 4096, st);
+}
+
+int ms_oracle_rs_perm(uint32_t *out, uint64_t n, uint64_t seed, uint32_t B, int mode,
+                      ms_oracle_stats *st) {
+  for (uint64_t i = 0; i < n; ++i) out[i] = (uint32_t)i;
+  return ms_oracle_rs_shuffle(out, n, 4, seed, B, mode, st);
+}
+
 /* ------------------------------------------------------------------ exhaustive walk ----- */
 /* A source that, instead of drawing, walks the decision tree depth first: every coin is a
  * 2-way choice and every uniform draw an R-way choice (rejection collapsed to its exact
@@ -445,6 +573,11 @@ static uint32_t enum_take(enum_src *e, uint32_t arity) {
 static int enum_coin(ms_src *s, uint32_t level, uint32_t id, uint64_t t) {
   (void)level; (void)id; (void)t;
   return (int)enum_take((enum_src *)s, 2);
+}
+
+static int enum_tcoin(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t t) {
+  (void)tag;
+  return enum_coin(s, level, id, t);
 }
 
 static uint64_t enum_uniform(ms_src *s, uint32_t tag, uint32_t level, uint32_t id, uint64_t pos,
@@ -495,6 +628,7 @@ int ms_oracle_enumerate(uint32_t n, uint32_t B, int mode, uint64_t *num, uint64_
   enum_src e;
   memset(&e, 0, sizeof e);
   e.base.coin = enum_coin;
+  e.base.tcoin = enum_tcoin;
   e.base.uniform = enum_uniform;
   e.base.plant = mode & (MS_ORACLE_PLANT_FY_RANGE | MS_ORACLE_PLANT_TAIL_RANGE |
                          MS_ORACLE_PLANT_NO_TAIL);
@@ -536,6 +670,7 @@ int ms_oracle_enumerate_merge(uint32_t a, uint32_t b, int mode, uint64_t *num, u
   enum_src e;
   memset(&e, 0, sizeof e);
   e.base.coin = enum_coin;
+  e.base.tcoin = enum_tcoin;
   e.base.uniform = enum_uniform;
   e.base.plant = mode & (MS_ORACLE_PLANT_FY_RANGE | MS_ORACLE_PLANT_TAIL_RANGE |
                          MS_ORACLE_PLANT_NO_TAIL);
@@ -569,6 +704,53 @@ int ms_oracle_enumerate_merge(uint32_t a, uint32_t b, int mode, uint64_t *num, u
   }
   den[0] = (uint64_t)(D >> 64);
   den[1] = (uint64_t)D;
+  if (paths) *paths = leaves;
+  free(acc);
+  return rc;
+}
+
+/* The same walk for the splitting process, cut at max_levels levels: paths that still have a
+ * segment above B after max_levels levels are not counted (their mass goes to *unres, as a
+ * numerator over the same denominator). The counted mass of every permutation must be the same. */
+int ms_oracle_enumerate_rs(uint32_t n, uint32_t B, uint32_t max_levels, int mode, uint64_t *num,
+                           uint64_t *den, uint64_t *paths, uint64_t *unres) {
+  if (n == 0 || n > 6 || B == 0) return 3;
+  uint64_t nfact = 1;
+  for (uint32_t i = 2; i <= n; ++i) nfact *= i;
+  unsigned __int128 D = enum_denominator();
+  unsigned __int128 *acc = (unsigned __int128 *)calloc(nfact, sizeof(unsigned __int128));
+  if (!acc) return 2;
+  unsigned __int128 lost = 0;
+  enum_src e;
+  memset(&e, 0, sizeof e);
+  e.base.coin = enum_coin;
+  e.base.tcoin = enum_tcoin;
+  e.base.uniform = enum_uniform;
+  e.base.plant = mode & MS_ORACLE_PLANT_FY_RANGE;
+  uint64_t leaves = 0;
+  int rc = 0;
+  for (;;) {
+    uint32_t perm[8];
+    ms_oracle_stats st;
+    memset(&st, 0, sizeof st);
+    for (uint32_t i = 0; i < n; ++i) perm[i] = i;
+    e.depth = 0;
+    e.prod = 1;
+    int r = run_rao_sandelius(&e.base, (unsigned char *)perm, n, 4, B, max_levels, &st);
+    if (e.overflow || D % e.prod != 0 || (r != 0 && r != 5)) { rc = 4; break; }
+    if (r == 5) lost += D / e.prod;
+    else acc[lehmer_rank(perm, n)] += D / e.prod;
+    ++leaves;
+    if (!enum_next(&e)) break;
+  }
+  for (uint64_t k = 0; k < nfact; ++k) {
+    num[2 * k] = (uint64_t)(acc[k] >> 64);
+    num[2 * k + 1] = (uint64_t)acc[k];
+  }
+  den[0] = (uint64_t)(D >> 64);
+  den[1] = (uint64_t)D;
+  unres[0] = (uint64_t)(lost >> 64);
+  unres[1] = (uint64_t)lost;
   if (paths) *paths = leaves;
   free(acc);
   return rc;

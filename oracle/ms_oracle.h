@@ -56,7 +56,13 @@ enum {
 };
 
 /* Stream tags of MS-Philox v1. */
-enum { MS_ORACLE_TAG_COIN = 1, MS_ORACLE_TAG_TAIL = 2, MS_ORACLE_TAG_LEAF = 3 };
+enum {
+  MS_ORACLE_TAG_COIN = 1,
+  MS_ORACLE_TAG_TAIL = 2,
+  MS_ORACLE_TAG_LEAF = 3,
+  MS_ORACLE_TAG_RS_COIN = 4, /* splitting process: the bit of position p on level l */
+  MS_ORACLE_TAG_RS_LEAF = 5  /* splitting process: Fisher-Yates of the final segment at s */
+};
 
 typedef struct {
   uint64_t coin_bits;   /* flips drawn by all coin loops, terminating flips included */
@@ -90,6 +96,18 @@ int ms_oracle_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_
 int ms_oracle_perm(uint32_t *out, uint64_t n, uint64_t seed, uint32_t B, int mode,
                    ms_oracle_stats *st);
 
+/* The Rao-Sandelius splitting process with a Fisher-Yates cutoff B (see ms_oracle.c): segments
+ * above B split stably by one fresh bit per element and level (stream RS_COIN) until every
+ * segment has at most B elements, then each segment [s, e) is shuffled by Algorithm 1 with the
+ * draws of stream (RS_LEAF, 0, s, i). Stats: coin_bits = bits drawn by the splits, merges = the
+ * number of splits, levels = split levels, leaf_* = the Fisher-Yates draws. mode: MS_ORACLE_PHILOX
+ * or MS_ORACLE_SEQFDR (one sequential stream, Fast Dice Roller draws; bit counts only).
+ * Returns 0 on success. */
+int ms_oracle_rs_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_t B, int mode,
+                         ms_oracle_stats *st);
+int ms_oracle_rs_perm(uint32_t *out, uint64_t n, uint64_t seed, uint32_t B, int mode,
+                      ms_oracle_stats *st);
+
 /* One Merge of the adjacent ranges a[0..n1) and a[n1..n1+n2), as merge `id` of `level`.
  * *T_out receives the break step (number of flips before the terminating one). */
 int ms_oracle_merge(uint32_t *a, uint64_t n1, uint64_t n2, uint64_t seed, uint32_t level,
@@ -109,6 +127,13 @@ int ms_oracle_enumerate(uint32_t n, uint32_t B, int mode, uint64_t *num, uint64_
  * positions holding first-half elements is `mask`. */
 int ms_oracle_enumerate_merge(uint32_t a, uint32_t b, int mode, uint64_t *num, uint64_t *den,
                               uint64_t *paths);
+
+/* Exhaustive walk of the splitting process on the identity of size n <= 6, cut at max_levels
+ * split levels: num[2*rank..] receives the probability numerator of each output permutation over
+ * paths that finish within max_levels levels, unres[0..1] the numerator of the paths cut off
+ * (high, low), den the common denominator. mode: 0, or MS_ORACLE_PLANT_FY_RANGE (tests only). */
+int ms_oracle_enumerate_rs(uint32_t n, uint32_t B, uint32_t max_levels, int mode, uint64_t *num,
+                           uint64_t *den, uint64_t *paths, uint64_t *unres);
 
 #ifdef __cplusplus
 }
