@@ -309,6 +309,38 @@ ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *p, void *d_
                          size_t ws_bytes, uint64_t *h_out, ms_stream_t stream);
 
 /*
+ * The Rao-Sandelius splitting process (the comparison workload of the paper: the introduction's
+ * passage on splitting processes and the third row of Table 1), with a Fisher-Yates cutoff B.
+ * Result definition "RS-Philox v1" (also implemented by the CPU oracle of the test suite):
+ *   start with the segment [0, n); on split level l = 0, 1, ... every segment [s, e) with more
+ *   than B elements takes the bit of each current position p -- bit p%32 of word (p/32)%4 of
+ *   Philox4x32-10((p/128, 0, 4<<16 | l, 0)) -- and is split stably, bit 0 first; segments of at
+ *   most B elements stay. Once none is above B, every segment [s, e) is shuffled by Algorithm 1
+ *   with the uniform draws of stream (tag 5, level 0, id = s, pos = i) defined above.
+ *   ms_rs_workspace_bytes  device workspace for (n, w, B): a second buffer of n*w bytes, the
+ *                          per-level bit counts (n/128 + n/1024 bytes), two lists of active
+ *                          segments (8 bytes each, at most n/(B+1)), 12 bytes of split data per
+ *                          active segment and a bitmap of the segment starts (n/8 bytes);
+ *                          0 for invalid arguments.
+ *   ms_rs_shuffle          permute d_data[0..n) (w in {4, 8, 16}, w-byte aligned) in place;
+ *                          1 <= B <= MS_MAX_B, n <= 2^32 - 1, d_ws 256-byte aligned.
+ *   ms_rs_perm             fill d_out[0..n) with the permutation ms_rs_shuffle applies to the
+ *                          identity (the first level generates it instead of reading it).
+ * Each split level is one pass over the array. The planned number of levels (c + 1 or c + 2,
+ * odd, c = min{c : floor(n / 2^c) <= B}) leaves a segment above B only rarely for large B;
+ * the call then synchronises the stream once to read whether one is left, and runs further
+ * pairs of levels if so (at most 4096 levels: MS_ERR_UNSUPPORTED beyond). So unlike ms_shuffle
+ * these calls wait for their stream and cannot be captured into a CUDA graph.
+ * Errors: MS_ERR_INVALID for bad arguments, MS_ERR_UNSUPPORTED for B > MS_MAX_B, MS_ERR_CUDA for
+ * a failed launch or copy.
+ */
+size_t ms_rs_workspace_bytes(uint64_t n, uint32_t w, uint32_t B);
+ms_status ms_rs_shuffle(void *d_data, uint64_t n, uint32_t w, uint64_t seed, uint32_t B,
+                        void *d_ws, size_t ws_bytes, ms_stream_t stream);
+ms_status ms_rs_perm(uint32_t *d_out, uint64_t n, uint64_t seed, uint32_t B, void *d_ws,
+                     size_t ws_bytes, ms_stream_t stream);
+
+/*
  * Collect the timings of every launch recorded since the last reset (waits for the recorded
  * events; process-wide state, not thread-safe) and optionally reset the record.
  */

@@ -22,6 +22,7 @@ __all__ = [
     "ms_status_string", "ms_version", "ms_last_cuda_error", "ms_perm_static", "MS_STATIC_MAX_N", "MS_STATIC_SCRATCH_BYTES", "params", "plan", "shuffle_", "perm", "shuffle_host",
     "perm_host", "workspace", "MsTuneEntry", "ms_resolve_params", "ms_resolve_batch_params",
     "ms_tune_install", "ms_tune_table", "resolve", "resolve_batch",
+    "ms_rs_workspace_bytes", "ms_rs_shuffle", "ms_rs_perm", "rs_perm", "rs_shuffle_",
 ]
 
 MS_OK, MS_ERR_INVALID, MS_ERR_UNSUPPORTED, MS_ERR_NOMEM, MS_ERR_CUDA, MS_ERR_TIMEOUT = range(6)
@@ -156,6 +157,12 @@ def lib() -> ctypes.CDLL:
         L.ms_random_bits_workspace.restype = sz
         L.ms_random_bits.argtypes = [u64, u64, P, vp, sz, pu64, vp]
         L.ms_random_bits.restype = i32
+        L.ms_rs_workspace_bytes.argtypes = [u64, u32, u32]
+        L.ms_rs_workspace_bytes.restype = sz
+        L.ms_rs_shuffle.argtypes = [vp, u64, u32, u64, u32, vp, sz, vp]
+        L.ms_rs_shuffle.restype = i32
+        L.ms_rs_perm.argtypes = [vp, u64, u64, u32, vp, sz, vp]
+        L.ms_rs_perm.restype = i32
         L.ms_last_cuda_error.argtypes = []
         L.ms_last_cuda_error.restype = i32
         L.ms_last_cuda_error_string.argtypes = []
@@ -480,3 +487,49 @@ def shuffle_batch(tensors, base_seed: int = 0, seeds=None, perm: bool = False, B
     if st != MS_OK:
         raise MsError(st, "ms_shuffle_batch")
     return tensors
+
+
+# ------------------------------------------------------------------ splitting process -------
+def ms_rs_workspace_bytes(n: int, w: int, B: int) -> int:
+    return int(lib().ms_rs_workspace_bytes(n, w, B))
+
+
+def ms_rs_shuffle(d_data: int, n: int, w: int, seed: int, B: int, d_ws: int, ws_bytes: int,
+                  stream: int = 0) -> int:
+    return int(lib().ms_rs_shuffle(d_data, n, w, seed, B, d_ws, ws_bytes, stream))
+
+
+def ms_rs_perm(d_out: int, n: int, seed: int, B: int, d_ws: int, ws_bytes: int,
+               stream: int = 0) -> int:
+    return int(lib().ms_rs_perm(d_out, n, seed, B, d_ws, ws_bytes, stream))
+
+
+def rs_perm(n: int, seed: int, B: int, device=None, out=None, stream=None):
+    """The Rao-Sandelius splitting process's permutation of 0..n-1 (int32 CUDA tensor)."""
+    import torch
+
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=device or "cuda")
+    nbytes = ms_rs_workspace_bytes(n, 4, B)
+    if nbytes == 0:
+        raise MsError(MS_ERR_INVALID, "ms_rs_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=out.device)
+    st = ms_rs_perm(out.data_ptr(), n, seed, B, ws.data_ptr(), nbytes, _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_rs_perm")
+    return out
+
+
+def rs_shuffle_(x, seed: int, B: int, stream=None):
+    """Shuffle a contiguous CUDA tensor in place along its first axis by the splitting process."""
+    import torch
+
+    n, w = _width(x)
+    nbytes = ms_rs_workspace_bytes(n, w, B)
+    if nbytes == 0:
+        raise MsError(MS_ERR_INVALID, "ms_rs_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    st = ms_rs_shuffle(x.data_ptr(), n, w, seed, B, ws.data_ptr(), nbytes, _stream_handle(stream))
+    if st != MS_OK:
+        raise MsError(st, "ms_rs_shuffle")
+    return x

@@ -1,0 +1,575 @@
+// ms_rs.cu -- the Rao-Sandelius splitting process on the GPU (arXiv 1508.03167, the
+// introduction's passage on splitting processes and the third row of Table 1), with a
+// Fisher-Yates cutoff B: the comparison workload of MergeShuffle.
+//
+// Result definition (RS-Philox v1, implemented independently by the CPU oracle of the tests):
+//   start with the single segment [0, n); on split level l = 0, 1, ... every segment [s, e) with
+//   more than B elements draws the bit of each current position p (bit p mod 32 of word
+//   (p / 32) mod 4 of Philox((p / 128, 0, (4 << 16) | l, 0))) and is split stably, the elements
+//   with bit 0 first; segments of at most B elements keep their place. Once no segment has more
+//   than B elements, each segment [s, e) is shuffled by Algorithm 1 with the uniform draws of
+//   stream (tag 5, level 0, id = s, pos = i).
+//
+// One split level is one streaming pass over the array (read n*w, write n*w):
+//   count   zeros among the bits of every 128-position block and 4096-position chunk (Philox
+//           only, no array traffic), then an exclusive scan of the chunk counts;
+//   split   per active segment its zero count z (from the prefix) and its children: a child
+//           larger than B joins the next level's active list (an ordered compaction: count,
+//           single-CTA scan, write), and a split point s + z is marked in the boundary bitmap;
+//           the data pass then sends position p of an active segment to s + (Z_p - Z_s) if its
+//           bit is 0, else to s + z + (p - s) - (Z_p - Z_s); every other position is copied.
+// After the planned levels (an odd number, so that the last one writes the workspace buffer)
+// the host reads whether a segment above B is left and runs further pairs of levels if so.
+// The Fisher-Yates pass takes the final segments from the boundary bitmap: one lane per
+// segment shuffles its 16-bit local indices in shared memory, then the warp writes the segment
+// to the caller's buffer through them.
+#include <algorithm>
+
+#include "mergeshuffle.h"
+#include "ms_common.cuh"
+#include "ms_device.cuh"
+#include "ms_plan.h"
+
+namespace msk {
+namespace {
+
+constexpr uint32_t kTagRsCoin = 4u;
+constexpr uint32_t kTagRsLeaf = 5u;
+constexpr uint32_t kRsChunk = 4096u;                 // positions per chunk (32 Philox blocks)
+constexpr uint32_t kRsChunkBlocks = kRsChunk / 128u;
+constexpr uint32_t kRsThreads = 256u;
+constexpr uint32_t kRsScanThreads = 1024u;
+constexpr uint32_t kRsSegCap = 512u;  // active segments of one chunk staged at a time
+
+struct RsArgs {
+  uint64_t n;
+  uint2 key;
+  uint32_t level;
+  uint32_t B;
+  uint32_t nchunks;
+  uint32_t *zc;        // nchunks + 1: zeros per chunk, then their exclusive prefix (total last)
+  uint8_t *zb;         // 32 per chunk: zeros per 128-position block
+  const uint2 *act;    // active segments (s, e) of this level, sorted by s
+  const uint32_t *act_n;
+  uint2 *nxt;          // next level's active segments
+  uint32_t *nxt_n;
+  uint32_t *zseg;      // per active segment: zeros among its bits
+  uint32_t *zs;        // per active segment: zeros before its first position (Z_s)
+  uint32_t *cnt;       // per active segment: children above B, then their exclusive prefix
+  uint32_t *bnd;       // boundary bitmap: bit p set iff a final segment starts at p
+};
+
+__device__ __forceinline__ uint4 rs_block(uint2 key, uint32_t level, uint32_t blk) {
+  return philox10(make_uint4(blk, 0u, (kTagRsCoin << 16) | level, 0u), key);
+}
+
+// zeros among the bits of positions [128*blk, min(128*blk + 128, limit))
+__device__ __forceinline__ uint32_t rs_block_zeros(const uint4 &c, uint64_t base, uint64_t limit) {
+  if (base >= limit) return 0u;
+  const uint32_t valid = static_cast<uint32_t>(limit - base < 128ull ? limit - base : 128ull);
+  uint32_t z = 0;
+  z += __popc(~c.x & low_mask(min(valid, 32u)));
+  z += __popc(~c.y & low_mask(valid > 32u ? min(valid - 32u, 32u) : 0u));
+  z += __popc(~c.z & low_mask(valid > 64u ? min(valid - 64u, 32u) : 0u));
+  z += __popc(~c.w & low_mask(valid > 96u ? valid - 96u : 0u));
+  return z;
+}
+
+// Z_p: zeros among the bits of positions [0, p), p <= n (after the chunk scan)
+__device__ uint32_t rs_zeros_before(const RsArgs &a, uint64_t p) {
+  const uint64_t chunk = p / kRsChunk;
+  uint32_t Z = a.zc[chunk];
+  if (chunk >= a.nchunks) return Z;
+  const uint32_t blk_in = static_cast<uint32_t>((p / 128u) % kRsChunkBlocks);
+  const uint8_t *zb = a.zb + chunk * kRsChunkBlocks;
+  for (uint32_t b = 0; b < blk_in; ++b) Z += zb[b];
+  const uint32_t q = static_cast<uint32_t>(p & 127u);
+  if (q) {
+    const uint4 c = rs_block(a.key, a.level, static_cast<uint32_t>(p / 128u));
+    const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 4u; ++k) {
+      const uint32_t lo = 32u * k;
+      if (q > lo) Z += __popc(~w[k] & low_mask(min(q - lo, 32u)));
+    }
+  }
+  return Z;
+}
+
+// zeros per 128-block and per chunk: one warp per chunk, one lane per block
+__global__ void __launch_bounds__(kRsThreads) rs_count_kernel(RsArgs a) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (kRsThreads / 32u);
+  for (uint32_t ch = (blockIdx.x * kRsThreads + threadIdx.x) >> 5; ch < a.nchunks; ch += warps) {
+    const uint32_t blk = ch * kRsChunkBlocks + lane;
+    const uint4 c = rs_block(a.key, a.level, blk);
+    const uint32_t z = rs_block_zeros(c, 128ull * blk, a.n);
+    a.zb[blk] = static_cast<uint8_t>(z);
+    const uint32_t tot = warp_sum(z);
+    if (lane == 0) a.zc[ch] = tot;
+  }
+}
+
+// In-place exclusive scan of v[0..count) by one CTA, the total stored at *total (may alias
+// v + count). Each thread sums a contiguous run, then a CTA scan of the run sums.
+__device__ void cta_exclusive_scan(uint32_t *v, uint32_t count, uint32_t *total) {
+  __shared__ uint32_t scratch[33];
+  const uint32_t per = (count + kRsScanThreads - 1u) / kRsScanThreads;
+  const uint32_t lo = min(threadIdx.x * per, count);
+  const uint32_t hi = min(lo + per, count);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; ++i) s += v[i];
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(s, scratch, &tot);
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void __launch_bounds__(kRsScanThreads) rs_chunk_scan_kernel(RsArgs a) {
+  cta_exclusive_scan(a.zc, a.nchunks, a.zc + a.nchunks);
+}
+
+__global__ void __launch_bounds__(kRsScanThreads) rs_list_scan_kernel(RsArgs a) {
+  cta_exclusive_scan(a.cnt, *a.act_n, a.nxt_n);
+}
+
+// per active segment: its zeros, Z_s, its children above B; the split point joins the bitmap
+__global__ void __launch_bounds__(kRsThreads) rs_children_kernel(RsArgs a) {
+  const uint32_t na = *a.act_n;
+  for (uint32_t k = blockIdx.x * kRsThreads + threadIdx.x; k < na; k += gridDim.x * kRsThreads) {
+    const uint2 sg = a.act[k];
+    const uint32_t Zs = rs_zeros_before(a, sg.x);
+    const uint32_t z = rs_zeros_before(a, sg.y) - Zs;
+    const uint32_t len = sg.y - sg.x;
+    a.zs[k] = Zs;
+    a.zseg[k] = z;
+    a.cnt[k] = (z > a.B ? 1u : 0u) + (len - z > a.B ? 1u : 0u);
+    if (z > 0u && z < len) {
+      const uint32_t p = sg.x + z;
+      atomicOr(&a.bnd[p >> 5], 1u << (p & 31u));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_list_write_kernel(RsArgs a) {
+  const uint32_t na = *a.act_n;
+  for (uint32_t k = blockIdx.x * kRsThreads + threadIdx.x; k < na; k += gridDim.x * kRsThreads) {
+    const uint2 sg = a.act[k];
+    const uint32_t z = a.zseg[k];
+    uint32_t o = a.cnt[k];
+    if (z > a.B) a.nxt[o++] = make_uint2(sg.x, sg.x + z);
+    if (sg.y - sg.x - z > a.B) a.nxt[o] = make_uint2(sg.x + z, sg.y);
+  }
+}
+
+// The data pass of one split level. A CTA takes a chunk of 4096 positions: warp 0 makes the
+// chunk's bits and the zeros before each word, the active segments that overlap the chunk are
+// staged in shared memory (in rounds of kRsSegCap), and every position goes to its place in its
+// segment's split, or stays if no active segment holds it. Level 0 of a perm writes the
+// positions themselves (nothing is read).
+template <typename E, bool kPerm>
+__global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E *in, E *out) {
+  __shared__ uint32_t cw[kRsChunk / 32u];
+  __shared__ uint32_t zw[kRsChunk / 32u];
+  __shared__ uint4 sg[kRsSegCap];  // (s, e, z, Z_s)
+  __shared__ uint32_t s_first, s_count;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t na = *a.act_n;
+  for (uint32_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+    const uint64_t c0 = static_cast<uint64_t>(ch) * kRsChunk;
+    const uint64_t c1 = min(c0 + kRsChunk, a.n);
+    if (tid < 32u) {
+      const uint4 c = rs_block(a.key, a.level, ch * kRsChunkBlocks + lane);
+      cw[4u * lane + 0u] = c.x;
+      cw[4u * lane + 1u] = c.y;
+      cw[4u * lane + 2u] = c.z;
+      cw[4u * lane + 3u] = c.w;
+      const uint32_t z4 = __popc(~c.x) + __popc(~c.y) + __popc(~c.z) + __popc(~c.w);
+      uint32_t ex = warp_inclusive_scan(z4) - z4;
+      zw[4u * lane + 0u] = ex;
+      ex += __popc(~c.x);
+      zw[4u * lane + 1u] = ex;
+      ex += __popc(~c.y);
+      zw[4u * lane + 2u] = ex;
+      ex += __popc(~c.z);
+      zw[4u * lane + 3u] = ex;
+      if (lane == 0) {
+        // first active segment ending after c0 (segments are disjoint and sorted)
+        uint32_t lo = 0, hi = na;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (a.act[mid].y <= c0) lo = mid + 1;
+          else hi = mid;
+        }
+        s_first = lo;
+      }
+    }
+    __syncthreads();
+    const uint32_t Zc = a.zc[ch];
+    uint32_t k = s_first;
+    uint64_t span_lo = c0;
+    for (;;) {
+      // stage the next round of segments that start before c1
+      if (tid == 0) {
+        uint32_t m = 0;
+        while (m < kRsSegCap && k + m < na && a.act[k + m].x < c1) ++m;
+        s_count = m;
+      }
+      __syncthreads();
+      const uint32_t m = s_count;
+      for (uint32_t j = tid; j < m; j += kRsThreads) {
+        const uint2 e = a.act[k + j];
+        sg[j] = make_uint4(e.x, e.y, a.zseg[k + j], a.zs[k + j]);
+      }
+      __syncthreads();
+      const bool last = (m < kRsSegCap) || (k + m >= na) || (a.act[k + m].x >= c1);
+      const uint64_t span_hi = last ? c1 : min(static_cast<uint64_t>(sg[m - 1u].y), c1);
+      uint32_t j = 0;
+      for (uint64_t p = span_lo + tid; p < span_hi; p += kRsThreads) {
+        while (j < m && sg[j].y <= p) ++j;
+        E v;
+        if constexpr (kPerm) v = static_cast<E>(p);
+        else v = in[p];
+        uint64_t dst = p;
+        if (j < m && sg[j].x <= p) {
+          const uint4 g = sg[j];
+          const uint32_t q = static_cast<uint32_t>(p - c0);
+          const uint32_t wv = cw[q >> 5];
+          const uint32_t Zp = Zc + zw[q >> 5] + __popc(~wv & low_mask(q & 31u));
+          const uint32_t zin = Zp - g.w;  // zeros of the segment before p
+          dst = ((wv >> (q & 31u)) & 1u) ? g.x + g.z + static_cast<uint32_t>(p - g.x) - zin
+                                         : g.x + zin;
+        }
+        out[min(dst, a.n - 1u)] = v;
+      }
+      if (last) break;
+      k += m;
+      span_lo = span_hi;
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// Algorithm 1 on every final segment (at most B elements each; a segment starts at every set
+// bit of the boundary bitmap and ends at the next one, or at n). One warp per CTA takes windows
+// of `lanes` bitmap words; lane j owns word j of the window and takes the segments that start in
+// it, one per round, lowest first. It shuffles the local indices 0..L-1 of its segment in shared
+// memory (stride P = 2 mod 64: the lanes' entries at one index sit in distinct banks) with the
+// draws of stream (5, 0, s, i); the warp then writes each segment of the round through its
+// indices: out[s + i] = in[s + idx[i]].
+template <typename E>
+__global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t n, uint2 key,
+                                                  const uint32_t *bnd, uint32_t P,
+                                                  uint32_t lanes) {
+  extern __shared__ __align__(16) uint16_t idx[];
+  const uint32_t lane = threadIdx.x;
+  const uint64_t nwords = (n + 31u) >> 5;
+  uint16_t *const A = idx + lane * P;
+  for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * lanes; w0 < nwords;
+       w0 += static_cast<uint64_t>(gridDim.x) * lanes) {
+    const uint64_t wi = w0 + lane;
+    uint32_t word = (lane < lanes && wi < nwords) ? bnd[wi] : 0u;
+    while (__any_sync(kFullMask, word != 0u)) {
+      uint32_t s_pos = 0u, L = 0u;
+      if (word) {
+        const uint32_t b = static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
+        word &= word - 1u;
+        s_pos = static_cast<uint32_t>(wi << 5) + b;
+        // the segment ends at the next start (a later bit of this word, else a later word)
+        uint64_t e = n;
+        if (word) {
+          e = (wi << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
+        } else {
+          for (uint64_t q = wi + 1u; q < nwords; ++q) {
+            const uint32_t bw = bnd[q];
+            if (bw) {
+              e = (q << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(bw)) - 1);
+              break;
+            }
+          }
+        }
+        L = static_cast<uint32_t>(min(e, n) - s_pos);
+        L = min(L, P - 2u);  // (a final segment never exceeds B <= P - 2)
+        for (uint32_t i = 0; i < L; ++i) A[i] = static_cast<uint16_t>(i);
+        DrawMemo memo;
+        for (uint32_t i = L; i-- > 1u;) {
+          const uint32_t j = min(draw_uniform(key, kTagRsLeaf, 0u, s_pos, i, i + 1u, memo), i);
+          const uint16_t t = A[i];
+          A[i] = A[j];
+          A[j] = t;
+        }
+      }
+      __syncwarp();
+      for (uint32_t r = 0; r < lanes; ++r) {
+        const uint32_t sr = __shfl_sync(kFullMask, s_pos, r);
+        const uint32_t Lr = __shfl_sync(kFullMask, L, r);
+        const uint16_t *const Ar = idx + r * P;
+        for (uint32_t i = lane; i < Lr; i += 32u) {
+          const uint32_t src = min(static_cast<uint32_t>(Ar[i]), Lr - 1u);
+          out[static_cast<uint64_t>(sr) + i] = in[static_cast<uint64_t>(sr) + src];
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void rs_init_kernel(RsArgs a, uint2 *act0, uint32_t *act0_n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    a.bnd[0] |= 1u;
+    const bool split = a.n > a.B;
+    if (split) act0[0] = make_uint2(0u, static_cast<uint32_t>(a.n));
+    *act0_n = split ? 1u : 0u;
+  }
+}
+
+}  // namespace
+}  // namespace msk
+
+namespace msk {
+namespace {
+
+__global__ void rs_iota_kernel(uint32_t *out, uint64_t n) {
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull)
+    out[i] = static_cast<uint32_t>(i);
+}
+
+size_t up256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
+
+// Workspace of one call: the ping-pong partner, the per-level bit counts, two active lists with
+// their counts, the per-segment split data, and the boundary bitmap.
+struct RsLayout {
+  uint32_t nchunks = 0, maxact = 0;
+  size_t buf = 0, zc = 0, zb = 0, act0 = 0, act1 = 0, ctl = 0, zseg = 0, zs = 0, cnt = 0,
+         bnd = 0, total = 0;
+};
+
+RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
+  RsLayout L;
+  L.nchunks = static_cast<uint32_t>((n + kRsChunk - 1u) / kRsChunk);
+  L.maxact = static_cast<uint32_t>(n / (static_cast<uint64_t>(B) + 1u) + 2u);
+  size_t off = 0;
+  L.buf = off;
+  off += up256(n * w);
+  L.zc = off;
+  off += up256((L.nchunks + 1ull) * 4u);
+  L.zb = off;
+  off += up256(static_cast<size_t>(L.nchunks) * kRsChunkBlocks);
+  L.act0 = off;
+  off += up256(L.maxact * 8ull);
+  L.act1 = off;
+  off += up256(L.maxact * 8ull);
+  L.ctl = off;
+  off += 256;
+  L.zseg = off;
+  off += up256(L.maxact * 4ull);
+  L.zs = off;
+  off += up256(L.maxact * 4ull);
+  L.cnt = off;
+  off += up256(L.maxact * 4ull);
+  L.bnd = off;
+  off += up256(((n + 31u) / 32u + 1u) * 4u);
+  L.total = off;
+  return L;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+
+template <typename E>
+cudaError_t rs_launch_split(const RsArgs &a, const void *in, void *out, bool perm, int sms,
+                            cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(a.nchunks, 8ull * sms));
+  if constexpr (sizeof(E) == 4) {
+    if (perm) {
+      rs_split_kernel<E, true><<<grid, kRsThreads, 0, s>>>(a, static_cast<const E *>(in),
+                                                            static_cast<E *>(out));
+      return cudaGetLastError();
+    }
+  }
+  rs_split_kernel<E, false><<<grid, kRsThreads, 0, s>>>(a, static_cast<const E *>(in),
+                                                         static_cast<E *>(out));
+  return cudaGetLastError();
+}
+
+// one split level: bit counts and their scan, the segments' splits and the next active list,
+// then the data pass from `in` to `out`
+cudaError_t rs_level(RsArgs a, uint32_t maxact, const void *in, void *out, uint32_t w,
+                     bool perm, int sms, cudaStream_t s) {
+  const unsigned g_chunks =
+      static_cast<unsigned>(std::min<uint64_t>((a.nchunks * 32ull + kRsThreads - 1) / kRsThreads,
+                                               8ull * sms));
+  const unsigned g_segs = static_cast<unsigned>(
+      std::min<uint64_t>((maxact + kRsThreads - 1ull) / kRsThreads, 8ull * sms));
+  rs_count_kernel<<<g_chunks, kRsThreads, 0, s>>>(a);
+  rs_chunk_scan_kernel<<<1, kRsScanThreads, 0, s>>>(a);
+  rs_children_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
+  rs_list_scan_kernel<<<1, kRsScanThreads, 0, s>>>(a);
+  rs_list_write_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (w) {
+    case 4: return rs_launch_split<uint32_t>(a, in, out, perm, sms, s);
+    case 8: return rs_launch_split<uint2>(a, in, out, perm, sms, s);
+    default: return rs_launch_split<uint4>(a, in, out, perm, sms, s);
+  }
+}
+
+template <typename E>
+cudaError_t rs_launch_fy(const void *in, void *out, uint64_t n, uint2 key, const uint32_t *bnd,
+                         uint32_t B, int sms, cudaStream_t s) {
+  uint32_t P = B + 2u;
+  while (P % 64u != 2u) ++P;
+  constexpr uint32_t kBudget = 96u * 1024u;
+  const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (2u * P)));
+  const size_t smem = static_cast<size_t>(lanes) * P * 2u;
+  auto kern = rs_fy_kernel<E>;
+  cudaError_t e = allow_dynamic_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t windows = ((n + 31u) / 32u + lanes - 1u) / lanes;
+  const uint64_t resident = static_cast<uint64_t>(std::max(per_sm, 1)) * sms;
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1u, std::min(windows, resident)));
+  kern<<<grid, 32, smem, s>>>(static_cast<const E *>(in), static_cast<E *>(out), n, key, bnd, P,
+                              lanes);
+  return cudaGetLastError();
+}
+
+thread_local cudaError_t g_rs_last_error = cudaSuccess;
+
+bool rs_failed(cudaError_t e) {
+  if (e != cudaSuccess) g_rs_last_error = e;
+  return e != cudaSuccess;
+}
+
+ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, uint32_t B,
+                 void *ws, size_t ws_bytes, cudaStream_t s) {
+  if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
+  if (perm && w != 4) return MS_ERR_INVALID;
+  if (B == 0 || n > 0xFFFFFFFFull) return MS_ERR_INVALID;
+  if (B > MS_MAX_B) return MS_ERR_UNSUPPORTED;
+  if (n <= 1) {
+    if (perm && n == 1) {
+      if (data == nullptr || reinterpret_cast<uintptr_t>(data) % 4 != 0) return MS_ERR_INVALID;
+      if (rs_failed(cudaMemsetAsync(data, 0, 4, s))) return MS_ERR_CUDA;
+    }
+    return MS_OK;
+  }
+  const RsLayout L = rs_layout(n, w, B);
+  if (data == nullptr || reinterpret_cast<uintptr_t>(data) % w != 0) return MS_ERR_INVALID;
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < L.total)
+    return MS_ERR_INVALID;
+  const int sms = sm_count();
+  if (sms <= 0) return MS_ERR_CUDA;
+  char *base = static_cast<char *>(ws);
+  void *W = base + L.buf;
+  uint32_t *ctl = reinterpret_cast<uint32_t *>(base + L.ctl);
+  uint2 *act[2] = {reinterpret_cast<uint2 *>(base + L.act0), reinterpret_cast<uint2 *>(base + L.act1)};
+  RsArgs a;
+  a.n = n;
+  a.key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  a.level = 0;
+  a.B = B;
+  a.nchunks = L.nchunks;
+  a.zc = reinterpret_cast<uint32_t *>(base + L.zc);
+  a.zb = reinterpret_cast<uint8_t *>(base + L.zb);
+  a.zseg = reinterpret_cast<uint32_t *>(base + L.zseg);
+  a.zs = reinterpret_cast<uint32_t *>(base + L.zs);
+  a.cnt = reinterpret_cast<uint32_t *>(base + L.cnt);
+  a.bnd = reinterpret_cast<uint32_t *>(base + L.bnd);
+  if (rs_failed(cudaMemsetAsync(a.bnd, 0, ((n + 31u) / 32u + 1u) * 4u, s)) ||
+      rs_failed(cudaMemsetAsync(ctl, 0, 256, s)))
+    return MS_ERR_CUDA;
+  rs_init_kernel<<<1, 32, 0, s>>>(a, act[0], ctl);
+  if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
+  // planned levels: c + 1 (segments then average at most B/2, so one above B is rare), made
+  // odd so that the last one writes W
+  uint32_t levels = 0;
+  if (n > B) {
+    uint32_t c = 0;
+    while ((n >> c) > B) ++c;
+    levels = c + 1u;
+    if (levels % 2u == 0u) ++levels;
+  }
+  uint32_t lv = 0;
+  auto run_levels = [&](uint32_t upto) -> bool {
+    for (; lv < upto; ++lv) {
+      RsArgs l = a;
+      l.level = lv;
+      l.act = act[lv % 2u];
+      l.act_n = ctl + (lv % 2u);
+      l.nxt = act[(lv + 1u) % 2u];
+      l.nxt_n = ctl + ((lv + 1u) % 2u);
+      const void *in = (lv % 2u == 0u) ? data : W;
+      void *out = (lv % 2u == 0u) ? W : data;
+      if (rs_failed(rs_level(l, L.maxact, in, out, w, perm && lv == 0u, sms, s))) return false;
+    }
+    return true;
+  };
+  if (!run_levels(levels)) return MS_ERR_CUDA;
+  if (levels > 0) {
+    // segments still above B after the planned levels: read the count and run pairs of levels
+    for (;;) {
+      uint32_t left = 0;
+      if (rs_failed(cudaMemcpyAsync(&left, ctl + (lv % 2u), 4, cudaMemcpyDeviceToHost, s)) ||
+          rs_failed(cudaStreamSynchronize(s)))
+        return MS_ERR_CUDA;
+      if (left == 0u) break;
+      if (lv + 2u > 4096u) return MS_ERR_UNSUPPORTED;
+      if (!run_levels(lv + 2u)) return MS_ERR_CUDA;
+    }
+  } else if (perm) {
+    rs_iota_kernel<<<static_cast<unsigned>(std::min<uint64_t>((n + 255u) / 256u, 8ull * sms)),
+                     256, 0, s>>>(static_cast<uint32_t *>(W), n);
+    if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
+  } else if (rs_failed(cudaMemcpyAsync(W, data, n * w, cudaMemcpyDeviceToDevice, s))) {
+    return MS_ERR_CUDA;
+  }
+  // the data now sits in W (an odd number of levels, or the copy above): Algorithm 1 on every
+  // final segment, from W into the caller's buffer
+  cudaError_t e;
+  switch (w) {
+    case 4: e = rs_launch_fy<uint32_t>(W, data, n, a.key, a.bnd, B, sms, s); break;
+    case 8: e = rs_launch_fy<uint2>(W, data, n, a.key, a.bnd, B, sms, s); break;
+    default: e = rs_launch_fy<uint4>(W, data, n, a.key, a.bnd, B, sms, s); break;
+  }
+  return rs_failed(e) ? MS_ERR_CUDA : MS_OK;
+}
+
+}  // namespace
+}  // namespace msk
+
+extern "C" {
+
+size_t ms_rs_workspace_bytes(uint64_t n, uint32_t w, uint32_t B) {
+  if ((w != 4 && w != 8 && w != 16) || B == 0 || B > MS_MAX_B || n > 0xFFFFFFFFull) return 0;
+  if (n <= 1) return 256;
+  return msk::rs_layout(n, w, B).total;
+}
+
+ms_status ms_rs_shuffle(void *d_data, uint64_t n, uint32_t w, uint64_t seed, uint32_t B,
+                        void *d_ws, size_t ws_bytes, ms_stream_t stream) {
+  return msk::rs_run(d_data, false, n, w, seed, B, d_ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+ms_status ms_rs_perm(uint32_t *d_out, uint64_t n, uint64_t seed, uint32_t B, void *d_ws,
+                     size_t ws_bytes, ms_stream_t stream) {
+  return msk::rs_run(d_out, true, n, 4, seed, B, d_ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
