@@ -24,6 +24,7 @@ STABLE = 0
 LITERAL = 1
 PHILOX = 0
 SEQFDR = 2
+FDR = 4
 
 # planted mistakes (exhaustive-walk tests only)
 PLANT_FY_RANGE = 16
@@ -97,6 +98,8 @@ def _load():
     lib.ms_oracle_coin.restype = i32
     lib.ms_oracle_draw.argtypes = [u64, u32, u32, u32, u64, u64, p64]
     lib.ms_oracle_draw.restype = u64
+    lib.ms_oracle_draw_fdr.argtypes = [u64, u32, u32, u32, u64, u64, p64]
+    lib.ms_oracle_draw_fdr.restype = u64
     lib.ms_oracle_levels.argtypes = [u64, u32]
     lib.ms_oracle_levels.restype = u32
     lib.ms_oracle_shuffle.argtypes = [vp, u64, u32, u64, u32, i32, ctypes.POINTER(Stats)]
@@ -137,6 +140,14 @@ def draw(seed: int, tag: int, level: int, stream_id: int, pos: int, R: int) -> t
     """(value, bits) of the uniform draw in [0, R) of stream (tag, level, id, pos)."""
     bits = ctypes.c_uint64(0)
     v = _load().ms_oracle_draw(seed, tag, level, stream_id, pos, R, ctypes.byref(bits))
+    return int(v), int(bits.value)
+
+
+def draw_fdr(seed: int, tag: int, level: int, stream_id: int, pos: int, R: int
+             ) -> tuple[int, int]:
+    """(value, bits) of the Fast Dice Roller draw in [0, R) on stream (tag, level, id, pos)."""
+    bits = ctypes.c_uint64(0)
+    v = _load().ms_oracle_draw_fdr(seed, tag, level, stream_id, pos, R, ctypes.byref(bits))
     return int(v), int(bits.value)
 
 

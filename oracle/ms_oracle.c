@@ -142,6 +142,35 @@ static uint64_t philox_uniform(ms_src *s, uint32_t tag, uint32_t level, uint32_t
   return 0;
 }
 
+/* Fast Dice Roller (Lumbroso 2013, the optimal uniform draw Section 1 cites) on each draw's own
+ * stream: the bits of word j of stream (tag, level, id, pos) -- word (pos mod 4) of
+ * Philox(ctr = (pos / 4, id, (tag << 16) | level, j)) -- are read least significant first,
+ * j = 0, 1, ...; v doubles and c takes the next bit with each read; once v >= R, c < R is the
+ * value, else c - R is uniform on [0, v - R) and the loop continues with v - R. (The coins are
+ * MS-Philox v1's; only the uniform draws change.) */
+static uint64_t philox_fdr_uniform(ms_src *s, uint32_t tag, uint32_t level, uint32_t id,
+                                   uint64_t pos, uint64_t R, uint64_t *bits) {
+  philox_src *p = (philox_src *)s;
+  if (R <= 1) return 0;
+  uint64_t v = 1, c = 0;
+  for (uint32_t j = 0; j < (1u << 20); ++j) {
+    const uint32_t *blk = philox_block(p, (uint32_t)(pos >> 2), id, (tag << 16) | level, j);
+    uint32_t word = blk[pos & 3];
+    for (uint32_t u = 0; u < 32; ++u) {
+      v <<= 1;
+      c = (c << 1) | ((word >> u) & 1u);
+      if (bits) *bits += 1;
+      if (v >= R) {
+        if (c < R) return c;
+        v -= R;
+        c -= R;
+      }
+    }
+  }
+  s->failed = 1;
+  return 0;
+}
+
 /* Sequential bit stream + Fast Dice Roller (Lumbroso 2013), for bit counts only. */
 typedef struct {
   ms_src base;
@@ -466,6 +495,14 @@ uint64_t ms_oracle_draw(uint64_t seed, uint32_t tag, uint32_t level, uint32_t id
   return philox_uniform(&p.base, tag, level, id, pos, R, bits);
 }
 
+uint64_t ms_oracle_draw_fdr(uint64_t seed, uint32_t tag, uint32_t level, uint32_t id,
+                            uint64_t pos, uint64_t R, uint64_t *bits) {
+  philox_src p;
+  init_philox(&p, seed);
+  if (bits) *bits = 0;
+  return philox_fdr_uniform(&p.base, tag, level, id, pos, R, bits);
+}
+
 int ms_oracle_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_t B, int mode,
                       ms_oracle_stats *st) {
   ms_oracle_stats local;
@@ -481,6 +518,7 @@ int ms_oracle_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_
   }
   philox_src p;
   init_philox(&p, seed);
+  if (mode & MS_ORACLE_FDR) p.base.uniform = philox_fdr_uniform;
   return run_mergeshuffle(&p.base, (unsigned char *)data, n, w, B, literal, st);
 }
 
@@ -499,7 +537,11 @@ int ms_oracle_merge(uint32_t *a, uint64_t n1, uint64_t n2, uint64_t seed, uint32
   seq_src q;
   ms_src *src;
   if (mode & MS_ORACLE_SEQFDR) { init_seq(&q, seed); src = &q.base; }
-  else { init_philox(&p, seed); src = &p.base; }
+  else {
+    init_philox(&p, seed);
+    if (mode & MS_ORACLE_FDR) p.base.uniform = philox_fdr_uniform;
+    src = &p.base;
+  }
   uint64_t T;
   if (mode & MS_ORACLE_LITERAL) {
     T = merge_literal(src, (unsigned char *)a, n1, n2, 4, level, id, st);

@@ -34,6 +34,8 @@
  *   MS_ORACLE_SEQFDR  -- one sequential bit stream; uniform integers by Lumbroso's Fast Dice
  *                        Roller (Section 1, "optimal way of drawing discrete uniform
  *                        variables"). Used only to compare bit counts with Table 1.
+ *   MS_ORACLE_FDR     -- the Philox streams, but every uniform draw by the Fast Dice Roller on
+ *                        its own stream ("MS-Philox-FDR"); the GPU's MS_FLAG_FDR mode.
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H
@@ -48,6 +50,8 @@ enum {
   MS_ORACLE_LITERAL = 1,
   MS_ORACLE_PHILOX = 0,
   MS_ORACLE_SEQFDR = 2,
+  MS_ORACLE_FDR = 4, /* Philox streams, uniform draws by the Fast Dice Roller on each draw's
+                        own stream (MS-Philox-FDR; coins unchanged) */
   /* Planted mistakes, for tests that show the pins catch them (never used otherwise):
    * Sattolo-style off-by-one ranges in Algorithm 1 or in the merge tail, or no tail at all. */
   MS_ORACLE_PLANT_FY_RANGE = 16,
@@ -84,6 +88,10 @@ int ms_oracle_coin(uint64_t seed, uint32_t level, uint32_t id, uint64_t t);
 /* Uniform integer in [0, R) of stream (tag, level, id, pos); *bits receives the bits used. */
 uint64_t ms_oracle_draw(uint64_t seed, uint32_t tag, uint32_t level, uint32_t id, uint64_t pos,
                         uint64_t R, uint64_t *bits);
+
+/* The same draw by the Fast Dice Roller on the draw's own stream (mode MS_ORACLE_FDR). */
+uint64_t ms_oracle_draw_fdr(uint64_t seed, uint32_t tag, uint32_t level, uint32_t id,
+                            uint64_t pos, uint64_t R, uint64_t *bits);
 
 /* Number of base-block levels c for n elements and cutoff B (B >= 1). */
 uint32_t ms_oracle_levels(uint64_t n, uint32_t B);
