@@ -520,6 +520,7 @@ def run_ours(args, world, rank, local):
         line["batched"] = run_batched(args, large=False, steps=ks, warmup=kw)
         line["batched_large"] = run_batched(args, large=True, steps=ks, warmup=kw)
         line["serve"] = run_serve(args)
+        line["rao_sandelius"] = run_rs(args, t_perm_ms)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -725,6 +726,61 @@ def run_batched(args, large: bool, steps: int | None = None, warmup: int | None 
                        "gelem_per_s": round(total / (t_single * 1e-3) / 1e9, 4),
                        "how": "one ms_perm / ms_shuffle launch sequence per instance"},
         "speedup_vs_per_launch": round(t_single / t_batch, 2),
+    }
+
+
+def run_rs(args, t_ms_mergeshuffle=None, steps: int = 5, warmup: int = 2) -> dict:
+    """The comparison workload: the Rao-Sandelius splitting process (Fisher-Yates cutoff B)
+    filling a perm of 2^30 uint32 with seed 7 and B = 512 (the MergeShuffle perm's tuned cutoff),
+    timed like the scale step's perm, beside that perm's own time."""
+    import torch
+
+    import paper_1508_03167_gb300 as ms
+
+    n = (1 << 26) if args.small else N_PERM
+    B = TUNED_B["perm"]
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    nbytes = ms.ms_rs_workspace_bytes(n, 4, B)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def call():
+        st = ms.ms_rs_perm(out.data_ptr(), n, SEED, B, ws.data_ptr(), nbytes, s.cuda_stream)
+        if st != ms.MS_OK:
+            raise ms.MsError(st, "ms_rs_perm")
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record(s)
+        call()  # (the call waits once for its stream: the host reads the unfinished count)
+        b.record(s)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ev) / steps
+    c = 0
+    while (n >> c) > B:
+        c += 1
+    levels = c + 1 + ((c + 1) % 2 == 0)
+    # algorithmic bytes: the first split level only writes (4n), every other split level and the
+    # Fisher-Yates pass read and write the array
+    nb = 4 * n + (levels - 1) * 8 * n + 8 * n
+    bw = measured_peaks()["hbm_gbs"]
+    del out, ws
+    torch.cuda.empty_cache()
+    return {
+        "metric": "Gelem/s", "value": round(n / (t * 1e-3) / 1e9, 4), "unit": "Gelem/s",
+        "ms_per_call": round(t, 3), "steps": steps, "warmup": warmup, "dtype": "u32",
+        "config": {"workload": f"Rao-Sandelius splitting process, perm of n={n} uint32, seed "
+                               f"{SEED}, Fisher-Yates cutoff B={B}", "n": n, "B": B,
+                   "split_levels_planned": levels},
+        "roofline": {"bound": "hbm", "bytes_per_call": nb, "peak": bw, "unit": "GB/s",
+                     "achieved": round(nb / 1e9 / (t * 1e-3), 1),
+                     "frac": round(nb / 1e9 / (t * 1e-3) / bw, 4)},
+        "mergeshuffle_perm_ms": round(t_ms_mergeshuffle, 3) if t_ms_mergeshuffle else None,
+        "mergeshuffle_speedup": (round(t / t_ms_mergeshuffle, 3) if t_ms_mergeshuffle else None),
     }
 
 

@@ -19,6 +19,7 @@
 //   patch    two small kernels apply the patches (read all sources, then write).
 // If a level's tails exceed the planned capacity, a sequential per-merge tail (in place on the
 // output) runs instead of insert/resolve/patch; the result is the same.
+#include "mergeshuffle.h"
 #include "ms_common.cuh"
 #include "ms_device.cuh"
 #include "ms_plan.h"
@@ -56,6 +57,8 @@ struct LevelArgs {
   uint32_t gate_on;
   void *out_alt;           // optional: tails and patches act on out_alt when *alt_sel != 0
   const uint32_t *alt_sel;
+  uint2 *laps;             // literal merge: per merge, lcap entries (lap start, zeros before it)
+  uint32_t lcap;
 };
 
 __device__ __forceinline__ bool gated_off(const LevelArgs &a) {
@@ -286,7 +289,13 @@ __global__ void __launch_bounds__(kThreads) tail_insert_kernel(LevelArgs a) {
     const uint32_t r = owner_merge(a, g);
     const uint4 mi = a.minfo[r];
     const uint32_t i = mi.x + (g - mi.z);
-    const uint32_t m = draw_uniform(a.key, kTagTail, a.level, r, i, i + 1u);
+    uint32_t m;
+    if (a.flags & MS_FLAG_FDR) {
+      uint32_t nb;
+      m = draw_fdr(a.key, kTagTail, a.level, r, i, i + 1u, &nb);
+    } else {
+      m = draw_uniform(a.key, kTagTail, a.level, r, i, i + 1u);
+    }
     a.mv[g] = m;
     const unsigned long long key = tail_key(r, m);
     uint32_t h = hash_slot(key, a.hbits);
@@ -404,7 +413,9 @@ __global__ void __launch_bounds__(kThreads) tail_sequential_kernel(LevelArgs a) 
     E *c = out + mb.s;
     DrawMemo memo;
     for (uint32_t i = mi.x; i < N; ++i) {
-      const uint32_t m = draw_uniform(a.key, kTagTail, a.level, r, i, i + 1u, memo);
+      uint32_t m, nb;
+      if (a.flags & MS_FLAG_FDR) m = draw_fdr(a.key, kTagTail, a.level, r, i, i + 1u, &nb);
+      else m = draw_uniform(a.key, kTagTail, a.level, r, i, i + 1u, memo);
       const E t = c[i];
       c[i] = c[m];
       c[m] = t;
@@ -1019,6 +1030,153 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
   }
 }
 
+// ---------------------------------------------------------- literal merge (flag) --------
+// Algorithm 3 as printed merges in place: i walks the output, and a 1-coin swaps T[i] with the
+// next second-half element T[j], so the front of the first half's unconsumed part moves to its
+// back. The second-half elements land exactly where the stable interleave puts them; the first
+// half behaves as a queue visited in rounds ("laps"): every step, 0- or 1-coin, visits the next
+// remaining first-half element in its original cyclic order, and a 0-coin takes the element it
+// visits. Lap 0 visits A[k] at step k; the elements a lap does not take (its 1-coin steps) are
+// visited again, in order, in the next lap, which starts where the previous one ends:
+//   S_0 = 0, m_0 = n1, S_{j+1} = S_j + m_j, m_{j+1} = ones among coins [S_j, S_{j+1}).
+// So first-half element k lands at its first visit step x that has a 0-coin, or, if the loop
+// breaks first (the second half ran out at T), at its first visit step x >= T: the leftover part
+// [T, N) holds the queue from its front, which is exactly the order of those visits. The gather
+// of the stable interleave writes every position first; this pass then overwrites the
+// first-half positions with their literal elements. The tails follow unchanged.
+
+// zeros among the coins of steps [0, x) of merge r, x <= N (zb and the scanned zc)
+__device__ uint32_t zeros_before(const LevelArgs &a, uint32_t r, uint32_t x) {
+  uint32_t chunk = x / kChunk;
+  if (chunk >= a.J) chunk = a.J - 1u;  // x = N on a chunk boundary: the whole last chunk
+  const uint64_t cid = static_cast<uint64_t>(r) * a.J + chunk;
+  uint32_t Z = a.zc[cid];
+  const uint32_t rel = min(x - chunk * kChunk, kChunk);
+  const uint32_t nb = rel >> 7;  // whole 128-step blocks before x
+  const uint8_t *zb = a.zb + cid * 32u;
+  for (uint32_t b = 0; b < nb; ++b) Z += zb[b];
+  const uint32_t q = rel & 127u;
+  if (q != 0u && nb < 32u) {
+    const uint4 c = coin_block(a.key, a.level, r, chunk * 32u + nb);
+    const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 4u; ++k) {
+      const uint32_t lo = 32u * k;
+      if (q > lo) Z += __popc(~w4[k] & low_mask(min(q - lo, 32u)));
+    }
+  }
+  return Z;
+}
+
+// the lap starts S_j and Z(S_j) of every merge, while S_j < T (one thread per merge)
+__global__ void __launch_bounds__(kThreads) lap_kernel(LevelArgs a) {
+  for (uint32_t r = blockIdx.x * kThreads + threadIdx.x; r < a.M; r += gridDim.x * kThreads) {
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t T = a.minfo[r].x;
+    uint2 *const L = a.laps + static_cast<uint64_t>(r) * a.lcap;
+    uint32_t S = 0, Z = 0, m = n1;
+    L[0] = make_uint2(0u, 0u);
+    for (uint32_t j = 1; j < a.lcap; ++j) {
+      if (S >= T || m == 0u) break;
+      const uint32_t S2 = min(S + m, N);  // (S_j + m_j <= N: the rest of both halves)
+      const uint32_t Z2 = zeros_before(a, r, S2);
+      m = (S2 - Z2) - (S - Z);
+      S = S2;
+      Z = Z2;
+      L[j] = make_uint2(S, Z);
+    }
+  }
+}
+
+// every first-half element of every merge to its literal position (one chunk of 4096
+// first-half elements per CTA; lap 0's coins come from shared memory)
+template <typename E>
+__global__ void __launch_bounds__(kThreads) literal_scatter_kernel(LevelArgs a) {
+  __shared__ uint32_t cw[kChunk / 32u];
+  __shared__ uint32_t zw[kChunk / 32u];
+  const E *__restrict__ in = static_cast<const E *>(a.in);
+  E *__restrict__ out = static_cast<E *>(a.out);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t r = static_cast<uint32_t>(cid / a.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(r) * a.J);
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t k0 = j * kChunk;
+    if (k0 >= n1) continue;  // uniform across the CTA
+    const uint32_t k1 = min(k0 + kChunk, n1);
+    const uint32_t T = a.minfo[r].x;
+    if (tid < 32u) {
+      const uint4 c = coin_block(a.key, a.level, r, j * (kChunk / 128u) + lane);
+      cw[4u * lane + 0u] = c.x;
+      cw[4u * lane + 1u] = c.y;
+      cw[4u * lane + 2u] = c.z;
+      cw[4u * lane + 3u] = c.w;
+      const uint32_t z4 = __popc(~c.x) + __popc(~c.y) + __popc(~c.z) + __popc(~c.w);
+      uint32_t ex = warp_inclusive_scan(z4) - z4;
+      zw[4u * lane + 0u] = ex;
+      ex += __popc(~c.x);
+      zw[4u * lane + 1u] = ex;
+      ex += __popc(~c.y);
+      zw[4u * lane + 2u] = ex;
+      ex += __popc(~c.z);
+      zw[4u * lane + 3u] = ex;
+    }
+    __syncthreads();
+    const uint32_t Zc = a.zc[cid];
+    const uint2 *const L = a.laps + static_cast<uint64_t>(r) * a.lcap;
+    for (uint32_t k = k0 + tid; k < k1; k += kThreads) {
+      uint32_t P;
+      // lap 0: visited at step k (coin and zeros before it from shared memory)
+      const uint32_t q = k - k0;
+      const uint32_t w0 = cw[q >> 5];
+      if (k >= T || ((w0 >> (q & 31u)) & 1u) == 0u) {
+        P = k;
+      } else {
+        uint32_t Zx = Zc + zw[q >> 5] + __popc(~w0 & low_mask(q & 31u));
+        uint32_t x = k, S = 0, Z = 0, m = n1, lap = 0;
+        P = N - 1u;  // (only if the walk below were cut short: an inconsistent plan)
+        for (uint32_t h = 0; h <= N; ++h) {
+          // x survives lap `lap`: its rank among the lap's survivors, then its next visit
+          const uint32_t rk = (x - Zx) - (S - Z);
+          uint32_t S2, Z2;
+          if (lap + 1u < a.lcap) {
+            const uint2 e = L[lap + 1u];
+            S2 = e.x;
+            Z2 = e.y;
+          } else {
+            S2 = min(S + m, N);
+            Z2 = zeros_before(a, r, S2);
+          }
+          m = (S2 - Z2) - (S - Z);
+          S = S2;
+          Z = Z2;
+          ++lap;
+          x = S + rk;
+          if (x >= T) {
+            P = x;
+            break;
+          }
+          const uint4 c = coin_block(a.key, a.level, r, x >> 7);
+          const uint32_t wx = pick_word(c, (x >> 5) & 3u);
+          if (((wx >> (x & 31u)) & 1u) == 0u) {
+            P = x;
+            break;
+          }
+          Zx = zeros_before(a, r, x);
+        }
+      }
+      out[mb.s + min(P, N - 1u)] = in[mb.s + k];
+    }
+    __syncthreads();  // cw / zw are reused by the next chunk
+  }
+}
+
 // ---------------------------------------------------------- staged fused pair (w = 4) ----
 // Two levels l, l+1 in one pass for 4-byte elements. A CTA takes 4096 outputs of level l+1;
 // they read one range of each of its halves (merges 2R and 2R+1 of level l), and each range is
@@ -1389,6 +1547,9 @@ LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.gate_on = 0;
   a.out_alt = nullptr;
   a.alt_sel = nullptr;
+  a.laps = b.laps;
+  a.lcap = lv.lcap;
+  if (p.flags & MS_FLAG_LITERAL) a.zb = b.zb;  // the literal merge's rank queries read it
   return a;
 }
 
@@ -1412,6 +1573,11 @@ cudaError_t launch_data_t(const Plan &p, const LevelPlan &lv, const void *in, vo
     else
       gather_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(a);
   });
+  if (p.flags & MS_FLAG_LITERAL) {
+    timed(p.prof, kKindGather, s, [&] {
+      literal_scatter_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(a);
+    });
+  }
   timed(p.prof, kKindTailSeq, s, [&] {
     tail_sequential_kernel<E><<<grid_for(lv.M, kThreads, 1u << 16), kThreads, 0, s>>>(a);
   });
@@ -1435,6 +1601,8 @@ cudaError_t plan_kernels(const Plan &p, const LevelArgs &a, const LevelPlan &lv,
   timed(p.prof, kKindScan, s,
         [&] { scan_kernel<<<grid_for(lv.M, 1, 1u << 20), kThreads, 0, s>>>(a); });
   timed(p.prof, kKindKscan, s, [&] { kscan_kernel<<<1, 1024, 0, s>>>(a); });
+  if (p.flags & MS_FLAG_LITERAL)
+    lap_kernel<<<grid_for(lv.M, kThreads, 1u << 16), kThreads, 0, s>>>(a);
   cudaError_t err = cudaSuccess;
   timed(p.prof, kKindHashClear, s, [&] {
     err = cudaMemsetAsync(b.hkeys, 0xFF, sizeof(unsigned long long) << lv.hbits, s);

@@ -76,6 +76,7 @@ struct LevelPlan {
   // of the pair's single data pass), 2 = second level of a pair, 0 = unpaired
   uint32_t pair;
   uint32_t xhbits;  // exception hash of a pair's first level: 2^xhbits slots
+  uint32_t lcap;    // literal merge (MS_FLAG_LITERAL): laps cached per merge
 };
 
 struct Plan {
@@ -117,6 +118,9 @@ struct Plan {
   // plan sets): per-block zero counts (one byte per 128 coins), the exception bitmap (one bit
   // per element) and the exception hash (keys, values)
   size_t off_zb = 0, off_xbits = 0, off_xkeys = 0, off_xvals = 0, exc_base = 0, exc_bytes = 0;
+  // literal merge (MS_FLAG_LITERAL): per merge, the first step of each lap of the first half's
+  // rotating queue and the zero coins before it (uint2), lcap entries a merge (same copies)
+  size_t off_laps = 0;
   uint32_t units = 0;         // global-level units: single levels and fused pairs
   uint32_t hbm_passes = 0;    // data passes after the base-block pass
   uint32_t zc_cap = 0, minfo_cap = 0, kcap_max = 0, hbits_max = 0;
@@ -144,6 +148,7 @@ struct Buffers {
   uint32_t *psrc;
   void *ptmp;
   uint32_t *ostart;  // first merge of every 1024 tail steps of a level (kscan), + one sentinel
+  uint2 *laps;       // literal merge: lap table (see Plan::off_laps)
 };
 
 // Lets `kern` launch with `smem` bytes of dynamic shared memory. The attribute is process-wide,

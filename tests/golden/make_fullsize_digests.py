@@ -17,8 +17,11 @@ table still resolves them so, so the digests stay tied to what the benchmark run
                  seed_i = 1 + i), B = 256: one digest over the instances' outputs in order
   c4_u64_<i>     instance i of the batched-large workload (uint64 splitmix64 values, n_i uniform
                  in [10^6, 10^8]), seed 1 + i, B = 256: the largest instance and a small one
+  rs_perm        the splitting process (Rao-Sandelius, Fisher-Yates cutoff B) on 2^30 positions,
+                 seed 7, B = 512: the comparison workload's perm
 
-Run:  python tests/golden/make_fullsize_digests.py   (about 10 minutes on one core; ~20 GB RAM)
+Run:  python tests/golden/make_fullsize_digests.py [name ...]   (all rows: about 16 minutes on
+one core, ~20 GB RAM; with names, only those rows are recomputed and the others kept)
 """
 from __future__ import annotations
 
@@ -53,44 +56,59 @@ C2A = dict(name="c2a_perm", n=1 << 30, w=4, seed=7, B=512)
 C2B = dict(name="c2b_records", n=300_000_017, w=16, seed=7, B=572)
 C3_B = 256
 C4_B = 256
+RS = dict(name="rs_perm", n=1 << 30, w=4, seed=7, B=512)
 
 
 def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
 
 
-def main() -> None:
-    rows = []
+def main(only: set[str]) -> None:
+    rows = {}
+    if only and os.path.exists(OUT):
+        with open(OUT) as f:
+            for line in f:
+                if line.strip() and not line.startswith("#"):
+                    rows[line.split()[0]] = line.strip()
+
+    def want(name):
+        return not only or name in only or (name.startswith("c4_u64_") and "c4" in only)
 
     def emit(name, n, w, seed, B, digest, dt):
-        rows.append(f"{name} {n} {w} {seed} {B} {digest}")
+        rows[name] = f"{name} {n} {w} {seed} {B} {digest}"
         print(f"{name}: n={n} w={w} seed={seed} B={B} {digest} ({dt:.1f} s)", flush=True)
 
     for cfg in (C1, C2A):
+        if not want(cfg["name"]):
+            continue
         t = time.time()
         out, _ = oracle.perm(cfg["n"], cfg["seed"], cfg["B"])
         emit(cfg["name"], cfg["n"], 4, cfg["seed"], cfg["B"], sha(out), time.time() - t)
         del out
 
-    t = time.time()
-    rec = inputs.records16(C2B["n"])
-    out, _ = oracle.shuffle(rec, C2B["seed"], C2B["B"])
-    del rec
-    emit(C2B["name"], C2B["n"], 16, C2B["seed"], C2B["B"], sha(out), time.time() - t)
-    del out
+    if want(C2B["name"]):
+        t = time.time()
+        rec = inputs.records16(C2B["n"])
+        out, _ = oracle.shuffle(rec, C2B["seed"], C2B["B"])
+        del rec
+        emit(C2B["name"], C2B["n"], 16, C2B["seed"], C2B["B"], sha(out), time.time() - t)
+        del out
 
     # batched: every instance's permutation, concatenated in instance order
-    t = time.time()
-    sizes = [int(x) for x in inputs.batch_sizes_log_uniform(4096, 6, 20)]
-    h = hashlib.sha256()
-    for i, n in enumerate(sizes):
-        out, _ = oracle.perm(n, 1 + i, C3_B)
-        h.update(out.tobytes())
-    emit("c3_batch", sum(sizes), 4, 1, C3_B, h.hexdigest(), time.time() - t)
+    if want("c3_batch"):
+        t = time.time()
+        sizes = [int(x) for x in inputs.batch_sizes_log_uniform(4096, 6, 20)]
+        h = hashlib.sha256()
+        for i, n in enumerate(sizes):
+            out, _ = oracle.perm(n, 1 + i, C3_B)
+            h.update(out.tobytes())
+        emit("c3_batch", sum(sizes), 4, 1, C3_B, h.hexdigest(), time.time() - t)
 
     # batched large: the largest instance, and the smallest (which the batch engine takes)
     big = [int(x) for x in inputs.batch_sizes_uniform(64, 10**6, 10**8)]
     for i in (max(range(64), key=lambda j: big[j]), min(range(64), key=lambda j: big[j])):
+        if not want(f"c4_u64_{i}"):
+            continue
         t = time.time()
         vals = inputs.values_u64(big[i], i)
         out, _ = oracle.shuffle(vals, 1 + i, C4_B)
@@ -98,15 +116,21 @@ def main() -> None:
         emit(f"c4_u64_{i}", big[i], 8, 1 + i, C4_B, sha(out), time.time() - t)
         del out
 
+    if want(RS["name"]):
+        t = time.time()
+        out, _ = oracle.rs_perm(RS["n"], RS["seed"], RS["B"])
+        emit(RS["name"], RS["n"], 4, RS["seed"], RS["B"], sha(out), time.time() - t)
+        del out
+
     with open(OUT, "w") as f:
         f.write("# SHA-256 of the CPU oracle's output (little-endian element bytes), written by\n"
                 "# make_fullsize_digests.py from the oracle alone. Columns: name n w seed B digest.\n"
                 "# c3_batch: n is the total of the 4096 instances, seed the first instance's\n"
                 "# (instance i takes seed 1 + i); the digest covers the outputs in instance order.\n")
-        for r in rows:
+        for r in rows.values():
             f.write(r + "\n")
     print("wrote", OUT)
 
 
 if __name__ == "__main__":
-    main()
+    main(set(sys.argv[1:]))

@@ -144,3 +144,22 @@ def test_c4_batched_large_instances_digest():
         assert _sha_device(bufs[i]) == v["digest"], i
     del bufs
     torch.cuda.empty_cache()
+
+
+def test_rao_sandelius_perm_2p30_digest():
+    """The comparison workload the benchmark times: the splitting process's perm of 2^30
+    positions, seed 7, cutoff 512."""
+    import torch
+
+    g = _digests()["rs_perm"]
+    out = torch.empty(g["n"], dtype=torch.int32, device="cuda")
+    nbytes = ms.ms_rs_workspace_bytes(g["n"], 4, g["B"])
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_rs_perm(out.data_ptr(), g["n"], g["seed"], g["B"], ws.data_ptr(), nbytes,
+                       torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    del ws
+    assert _sha_device(out) == g["digest"]
+    del out
+    torch.cuda.empty_cache()
