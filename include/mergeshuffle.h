@@ -95,6 +95,22 @@ typedef void *ms_stream_t;
 #define MS_FLAG_CTA_TILES 0x200u     /* fused merge levels (fuse_depth > 0) run on the CTA-wide
                                         base-block kernel rather than the eight-warp tile kernel
                                         on 16-bit indices (the result is identical) */
+#define MS_FLAG_LITERAL 0x400u       /* Algorithm 3 as printed: the in-place swapping merge, whose
+                                        first-half elements leave in a rotated order (the
+                                        result differs from the default stable interleave; same
+                                        coins, break steps and insertions, so the same random
+                                        bits). Single calls only (the batched form returns
+                                        MS_ERR_UNSUPPORTED); runs every level through HBM
+                                        (fuse_depth 0, one global pass per level). The oracle's
+                                        literal mode gives the same permutation. */
+#define MS_FLAG_FDR 0x800u           /* uniform draws (Algorithm 1's and the merge tails') by the
+                                        Fast Dice Roller on each draw's own stream instead of
+                                        rejection on ceil(log2 R)-bit slices: fewer random bits
+                                        a draw, a different result ("MS-Philox-FDR", the
+                                        oracle's FDR mode). ms_random_bits counts its bits.
+                                        Single calls only (the batched form returns
+                                        MS_ERR_UNSUPPORTED); runs with fuse_depth 0 and one
+                                        global pass per level. */
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level
@@ -297,7 +313,8 @@ ms_status ms_perm_static(uint32_t *d_out, uint64_t n, uint64_t seed, const ms_pa
  * equal the CPU oracle's for the same (n, seed, B).
  *   h_out   host array of 8 uint64: [0] coin bits (T + 1 per merge: the coin that asks for an
  *           exhausted half is drawn and counted), [1] bits of Algorithm 1's draws, [2] bits of
- *           the merge tails' draws (a draw costs its tested slices times b = ceil(log2 R)),
+ *           the merge tails' draws (a draw costs its tested slices times b = ceil(log2 R); with
+ *           MS_FLAG_FDR in p->flags, the bits the Fast Dice Roller reads from its stream),
  *           [3] Algorithm 1's draws, [4] tail draws, [5] merges, [6] leftover positions
  *           (sum of N - T), [7] levels c.
  *   d_ws    device workspace of ms_random_bits_workspace(n, p) bytes, 256-byte aligned.

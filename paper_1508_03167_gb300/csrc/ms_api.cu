@@ -133,6 +133,12 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   if (B == 0) return 1;
   if (n > 0xFFFFFFFFull) return 1;
   if (B > kMaxB) return 2;
+  if (flags & (MS_FLAG_LITERAL | MS_FLAG_FDR)) {
+    // the literal merge and the FDR draws run on the global levels only: no fused levels, no
+    // fused pairs
+    fuse_depth = 0;
+    flags |= MS_FLAG_GLOBAL_LEVELS | MS_FLAG_SINGLE_LEVELS | MS_FLAG_CTA_TILES;
+  }
   p.n = n;
   p.w = w;
   p.B = B;
@@ -365,6 +371,14 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   p.units = units;
   p.hbm_passes = nlocal + units;
   const bool pairs = xhbits_max > 0;
+  const bool literal = (flags & MS_FLAG_LITERAL) != 0;
+  uint32_t lcap_max = 0;
+  for (uint32_t i = 0; i < p.nlevels; ++i) {
+    uint32_t lg = 0;
+    while ((1ull << lg) < p.levels[i].Nmax) ++lg;
+    p.levels[i].lcap = literal ? std::min(lg + 12u, 64u) : 0u;
+    lcap_max = std::max(lcap_max, static_cast<uint32_t>(p.levels[i].M) * p.levels[i].lcap);
+  }
 
   size_t off = 0;
   p.off_buf = off;
@@ -387,12 +401,17 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     p.plan_sets = units >= 2 ? 4u : 2u;
     off += (p.plan_sets - 1) * p.plan_set_bytes;
     // exception structures of a pair's first level, one copy per live unit (after the sets)
-    if (pairs) {
+    if (pairs || literal) {
       const size_t ebase = off;
       p.off_zb = off - ebase;     off += round_up(zc_cap * 32ull, 256);
-      p.off_xbits = off - ebase;  off += round_up((n + 31) / 32 * 4, 256);
-      p.off_xkeys = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
-      p.off_xvals = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+      if (pairs) {
+        p.off_xbits = off - ebase;  off += round_up((n + 31) / 32 * 4, 256);
+        p.off_xkeys = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+        p.off_xvals = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+      }
+      if (literal) {
+        p.off_laps = off - ebase;   off += round_up(static_cast<size_t>(lcap_max) * 8u, 256);
+      }
       p.exc_base = ebase;
       p.exc_bytes = off - ebase;
       off += (p.plan_sets / 2 - 1) * p.exc_bytes;
@@ -510,6 +529,7 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   b.xbits = reinterpret_cast<uint32_t *>(es + p.off_xbits);
   b.xkeys = reinterpret_cast<uint32_t *>(es + p.off_xkeys);
   b.xvals = reinterpret_cast<uint32_t *>(es + p.off_xvals);
+  b.laps = reinterpret_cast<uint2 *>(es + p.off_laps);
   b.zc = reinterpret_cast<uint32_t *>(ps + p.off_zc);
   b.minfo = reinterpret_cast<uint4 *>(ps + p.off_minfo);
   b.ctrl = reinterpret_cast<uint32_t *>(ps + p.off_ctrl);
@@ -706,6 +726,7 @@ ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_par
   const ms_params r = msk::resolve_batch(k, h_n, w, params);
   if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
   if ((r.flags & MS_FLAG_PERM) && w != 4) return MS_ERR_INVALID;
+  if (r.flags & (MS_FLAG_LITERAL | MS_FLAG_FDR)) return MS_ERR_UNSUPPORTED;
   if (r.B == 0) return MS_ERR_INVALID;
   if (r.B > MS_MAX_B) return MS_ERR_UNSUPPORTED;
   if (k > 0 && h_n == nullptr) return MS_ERR_INVALID;

@@ -1,7 +1,8 @@
 // ms_bits.cu -- random-bit accounting of one MergeShuffle run (the random-bit model of
 // Section 1 of arXiv 1508.03167; the count the paper's Table 1 reports): coin bits (T + 1 per
 // merge, the terminating coin included), and for every uniform draw its tested slices times
-// their width b = ceil(log2 R), for Algorithm 1's draws and for the merge tails. The counts are a
+// their width b = ceil(log2 R), for Algorithm 1's draws and for the merge tails -- or, with
+// MS_FLAG_FDR, the bits the Fast Dice Roller reads from the draw's stream. The counts are a
 // pure function of (n, seed, B): no data is permuted.
 #include <algorithm>
 
@@ -41,7 +42,7 @@ __device__ __forceinline__ void add_warp(unsigned long long *dst, unsigned long 
 // Algorithm 1's draws: one thread per (base block, quad of positions). out[1] += bits,
 // out[3] += draws.
 __global__ void __launch_bounds__(kBitThreads) leaf_bits_kernel(uint64_t n, uint32_t c, uint2 key,
-                                                               uint32_t nq,
+                                                               uint32_t nq, bool fdr,
                                                                unsigned long long *out) {
   const uint64_t q = 1ull << c;
   unsigned long long bits = 0, draws = 0;
@@ -58,9 +59,15 @@ __global__ void __launch_bounds__(kBitThreads) leaf_bits_kernel(uint64_t n, uint
       const uint32_t pos = 4u * qd + v;
       if (pos >= 1u && pos < L) {
         const uint32_t R = pos + 1u;
-        bits += static_cast<unsigned long long>(
-                    draw_attempts(key, kTagLeaf, 0u, static_cast<uint32_t>(k), pos, R,
-                                  pick_word(blk, v))) * (32u - __clz(R - 1u));
+        if (fdr) {
+          uint32_t nb;
+          draw_fdr(key, kTagLeaf, 0u, static_cast<uint32_t>(k), pos, R, &nb);
+          bits += nb;
+        } else {
+          bits += static_cast<unsigned long long>(
+                      draw_attempts(key, kTagLeaf, 0u, static_cast<uint32_t>(k), pos, R,
+                                    pick_word(blk, v))) * (32u - __clz(R - 1u));
+        }
         ++draws;
       }
     }
@@ -74,6 +81,7 @@ __global__ void __launch_bounds__(kBitThreads) leaf_bits_kernel(uint64_t n, uint
 __global__ void __launch_bounds__(kBitThreads) tail_bits_kernel(uint64_t n, uint32_t c,
                                                                uint32_t level, uint32_t M,
                                                                const uint4 *minfo, uint2 key,
+                                                               bool fdr,
                                                                unsigned long long *out) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kBitThreads / 32);
@@ -90,10 +98,16 @@ __global__ void __launch_bounds__(kBitThreads) tail_bits_kernel(uint64_t n, uint
     }
     for (uint32_t i = T + lane; i < N; i += 32u) {
       const uint32_t R = i + 1u;
-      const uint4 blk = philox10(make_uint4(i >> 2, static_cast<uint32_t>(r), (kTagTail << 16) | level, 0u), key);
-      bits += static_cast<unsigned long long>(
-                  draw_attempts(key, kTagTail, level, static_cast<uint32_t>(r), i, R,
-                                pick_word(blk, i & 3u))) * (32u - __clz(R - 1u));
+      if (fdr) {
+        uint32_t nb;
+        draw_fdr(key, kTagTail, level, static_cast<uint32_t>(r), i, R, &nb);
+        bits += nb;
+      } else {
+        const uint4 blk = philox10(make_uint4(i >> 2, static_cast<uint32_t>(r), (kTagTail << 16) | level, 0u), key);
+        bits += static_cast<unsigned long long>(
+                    draw_attempts(key, kTagTail, level, static_cast<uint32_t>(r), i, R,
+                                  pick_word(blk, i & 3u))) * (32u - __clz(R - 1u));
+      }
       ++draws;
     }
   }
@@ -150,7 +164,8 @@ ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *params, voi
   if (cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return MS_ERR_CUDA;
   const uint32_t lmax = static_cast<uint32_t>((n + (1ull << c) - 1) >> c);
   const uint32_t nq = (lmax + 3u) / 4u;
-  msk::leaf_bits_kernel<<<152u * 8u, msk::kBitThreads, 0, s>>>(n, c, key, nq, cnt);
+  const bool fdr = (r.flags & MS_FLAG_FDR) != 0;
+  msk::leaf_bits_kernel<<<152u * 8u, msk::kBitThreads, 0, s>>>(n, c, key, nq, fdr, cnt);
   if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   msk::Plan p;
   p.n = n;
@@ -172,7 +187,7 @@ ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *params, voi
     if (msk::launch_level_breaks(p, lv, b, seed, s) != cudaSuccess) return MS_ERR_CUDA;
     const uint64_t grid = std::min<uint64_t>((lv.M + 7) / 8, 152u * 16u);
     msk::tail_bits_kernel<<<static_cast<unsigned>(grid), msk::kBitThreads, 0, s>>>(
-        n, c, l, lv.M, b.minfo, key, cnt);
+        n, c, l, lv.M, b.minfo, key, fdr, cnt);
     if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   }
   unsigned long long host[8];

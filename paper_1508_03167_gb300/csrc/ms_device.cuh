@@ -94,6 +94,32 @@ __device__ __forceinline__ uint32_t draw_uniform(uint2 key, uint32_t tag, uint32
   return draw_uniform(key, tag, level, id, pos, R, memo);
 }
 
+// Uniform integer in [0, R) by the Fast Dice Roller (Lumbroso 2013) on the stream's bits: word
+// j of the stream (as above) read least significant bit first, j = 0, 1, ...; v doubles and c
+// takes the next bit with each read; once v >= R, c < R is the value, else c - R is uniform on
+// [0, v - R) and the loop goes on with v - R. *bits receives the bits read (MS_FLAG_FDR).
+__device__ __forceinline__ uint32_t draw_fdr(uint2 key, uint32_t tag, uint32_t level, uint32_t id,
+                                             uint32_t pos, uint32_t R, uint32_t *bits) {
+  *bits = 0u;
+  if (R <= 1u) return 0u;
+  uint64_t v = 1u, c = 0u;
+  const uint32_t c2 = (tag << 16) | level;
+  for (uint32_t j = 0; j < (1u << 20); ++j) {
+    const uint32_t word = pick_word(philox10(make_uint4(pos >> 2, id, c2, j), key), pos & 3u);
+    for (uint32_t u = 0; u < 32u; ++u) {
+      v <<= 1;
+      c = (c << 1) | ((word >> u) & 1u);
+      ++*bits;
+      if (v >= R) {
+        if (c < R) return static_cast<uint32_t>(c);
+        v -= R;
+        c -= R;
+      }
+    }
+  }
+  return 0u;  // 2^25 bits without a value: probability far below 2^-(2^20); kept finite
+}
+
 // ----------------------------------------------------------------------------- merge tree --
 // Block boundary floor(n * i / 2^c) (appendix listing; n < 2^32 and i <= 2^c keep the product
 // inside 64 bits).

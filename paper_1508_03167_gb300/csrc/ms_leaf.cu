@@ -18,6 +18,9 @@
 // issues several words' loads before their stores; every merge tail (the random insertions) has
 // its draws and the final positions of the elements it moves computed in parallel, then the
 // moved values are read into the level's dead input buffer and written back.
+#include <algorithm>
+
+#include "mergeshuffle.h"
 #include "ms_merge.cuh"
 
 namespace msk {
@@ -277,9 +280,46 @@ __global__ void __launch_bounds__(32) fy_perm16_kernel(LeafArgs a, uint32_t per_
   }
 }
 
+// Algorithm 1 on every base block with uniform draws by the Fast Dice Roller (MS_FLAG_FDR): one
+// thread per block copies it to the output (a perm writes its positions) and swaps there, in
+// order, i = L-1 .. 1 with j from stream (LEAF, 0, block, i). The output is out of place or the
+// input itself; a thread touches only its own block.
+template <typename E, bool kPerm>
+__global__ void __launch_bounds__(128) fy_fdr_kernel(const E *in, E *out, uint64_t n, uint32_t c,
+                                                    uint2 key) {
+  const uint64_t q = 1ull << c;
+  for (uint64_t k = static_cast<uint64_t>(blockIdx.x) * 128u + threadIdx.x; k < q;
+       k += static_cast<uint64_t>(gridDim.x) * 128u) {
+    const uint64_t s0 = boundary(n, c, k);
+    const uint32_t L = static_cast<uint32_t>(boundary(n, c, k + 1) - s0);
+    E *const o = out + s0;
+    for (uint32_t i = 0; i < L; ++i) {
+      if constexpr (kPerm) o[i] = static_cast<E>(s0 + i);
+      else if (in != out) o[i] = in[s0 + i];
+    }
+    for (uint32_t i = L; i-- > 1u;) {
+      uint32_t nb;
+      const uint32_t j = min(draw_fdr(key, kTagLeaf, 0u, static_cast<uint32_t>(k), i, i + 1u, &nb), i);
+      const E t = o[i];
+      o[i] = o[j];
+      o[j] = t;
+    }
+  }
+}
+
 template <typename E, bool kPerm>
 cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t seed,
                           cudaStream_t s) {
+  if (p.flags & MS_FLAG_FDR) {
+    // Algorithm 1 with the Fast Dice Roller draws: one thread per base block
+    const uint64_t grid = std::min<uint64_t>((p.q + 127u) / 128u, 1048576ull);
+    if (p.prof) p.prof->begin(kKindLeaf, s);
+    fy_fdr_kernel<E, kPerm><<<static_cast<unsigned>(grid), 128, 0, s>>>(
+        static_cast<const E *>(in), static_cast<E *>(out), p.n, p.c,
+        make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+    if (p.prof) p.prof->end(s);
+    return cudaGetLastError();
+  }
   LeafArgs a;
   a.in = in;
   a.out = out;
