@@ -521,6 +521,7 @@ def run_ours(args, world, rank, local):
         line["batched_large"] = run_batched(args, large=True, steps=ks, warmup=kw)
         line["serve"] = run_serve(args)
         line["rao_sandelius"] = run_rs(args, t_perm_ms)
+        line["literal_and_fdr"] = run_literal_fdr(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -782,6 +783,62 @@ def run_rs(args, t_ms_mergeshuffle=None, steps: int = 5, warmup: int = 2) -> dic
         "mergeshuffle_perm_ms": round(t_ms_mergeshuffle, 3) if t_ms_mergeshuffle else None,
         "mergeshuffle_speedup": (round(t / t_ms_mergeshuffle, 3) if t_ms_mergeshuffle else None),
     }
+
+
+def run_literal_fdr(args, steps: int = 3, warmup: int = 1) -> dict:
+    """Algorithm 3 as printed (MS_FLAG_LITERAL) and Fast Dice Roller draws (MS_FLAG_FDR) on the
+    scale workload's perm (2^30, seed 7, B = 512), timed beside the default plan with the same
+    forced shape (fuse_depth 0, one global pass per level); and Table 1's measure, the random bits
+    consumed, counted on the GPU for n = 10^5 .. 10^8 with rejection draws and with FDR draws."""
+    import torch
+
+    import paper_1508_03167_gb300 as ms
+
+    n = (1 << 26) if args.small else N_PERM
+    B = TUNED_B["perm"]
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    res = {}
+    for tag, flags in (("single_levels", ms.MS_FLAG_GLOBAL_LEVELS | ms.MS_FLAG_SINGLE_LEVELS),
+                       ("literal", ms.MS_FLAG_LITERAL), ("fdr", ms.MS_FLAG_FDR),
+                       ("literal_fdr", ms.MS_FLAG_LITERAL | ms.MS_FLAG_FDR)):
+        p = ms.params(B=B, fuse_depth=0, flags=flags)
+        ws = torch.empty(ms.ms_workspace_bytes(n, 4, p), dtype=torch.uint8, device="cuda")
+
+        def call():
+            st = ms.ms_perm(out.data_ptr(), n, SEED, ws.data_ptr(), ws.numel(), p, s.cuda_stream)
+            if st != ms.MS_OK:
+                raise ms.MsError(st, "ms_perm")
+
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            call()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / steps
+        res[tag] = {"ms": round(t, 3), "gelem_per_s": round(n / (t * 1e-3) / 1e9, 4)}
+        del ws
+        torch.cuda.empty_cache()
+    del out
+    table = []
+    for nn in (10**5, 10**6, 10**7, 10**8):
+        rej = ms.random_bits(nn, 1, B=1024)
+        fdr = ms.random_bits(nn, 1, B=1024, flags=ms.MS_FLAG_FDR)
+        table.append({"n": nn, "bits_rejection": rej["total_bits"], "bits_fdr": fdr["total_bits"],
+                      "fdr_over_log2_n_factorial": round(
+                          fdr["total_bits"] / (math.lgamma(nn + 1) / math.log(2)), 5)})
+    return {"config": {"workload": f"perm of n={n} uint32, seed {SEED}, B={B}, fuse_depth 0, "
+                                   "every level one global pass", "n": n, "B": B},
+            "times": res,
+            "random_bits_B1024_seed1": table,
+            "note": "Table 1 (paper): Fisher-Yates 1,631,434 / 19,550,941 / 229,329,728 / "
+                    "2,628,248,831 and MergeShuffle 1,636,560 / 19,686,051 / 231,641,075 / "
+                    "2,650,387,993 bits for n = 1e5 .. 1e8 (its cutoff is not stated)"}
 
 
 def run_serve(args) -> dict:

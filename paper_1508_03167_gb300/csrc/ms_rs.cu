@@ -57,6 +57,7 @@ struct RsArgs {
   uint32_t *zs;        // per active segment: zeros before its first position (Z_s)
   uint32_t *cnt;       // per active segment: children above B, then their exclusive prefix
   uint32_t *bnd;       // boundary bitmap: bit p set iff a final segment starts at p
+  uint32_t *tsum;      // scan scratch: one sum per tile of kRsScanTile values
 };
 
 __device__ __forceinline__ uint4 rs_block(uint2 key, uint32_t level, uint32_t blk) {
@@ -129,12 +130,71 @@ __device__ void cta_exclusive_scan(uint32_t *v, uint32_t count, uint32_t *total)
   if (threadIdx.x == 0) *total = tot;
 }
 
-__global__ void __launch_bounds__(kRsScanThreads) rs_chunk_scan_kernel(RsArgs a) {
-  cta_exclusive_scan(a.zc, a.nchunks, a.zc + a.nchunks);
+// Exclusive scan of v[0..count) over the whole grid, in three kernels: every CTA sums a tile of
+// kRsScanTile values (tile_sums), one CTA scans the tile sums (the total goes to *total), then
+// every CTA rescans its tile from its offset. count is *count_dev if given, else count_host.
+constexpr uint32_t kRsScanTile = 16u * kRsThreads;
+
+__device__ __forceinline__ uint32_t scan_count(const uint32_t *count_dev, uint32_t count_host) {
+  return count_dev ? *count_dev : count_host;
 }
 
-__global__ void __launch_bounds__(kRsScanThreads) rs_list_scan_kernel(RsArgs a) {
-  cta_exclusive_scan(a.cnt, *a.act_n, a.nxt_n);
+__global__ void __launch_bounds__(kRsThreads) rs_scan_reduce_kernel(const uint32_t *v,
+                                                                    const uint32_t *count_dev,
+                                                                    uint32_t count_host,
+                                                                    uint32_t *tile_sums) {
+  __shared__ uint32_t red[kRsThreads / 32u];
+  const uint32_t count = scan_count(count_dev, count_host);
+  const uint32_t ntiles = (count + kRsScanTile - 1u) / kRsScanTile;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t sum = 0;
+    for (uint32_t i = t * kRsScanTile + threadIdx.x; i < min((t + 1u) * kRsScanTile, count);
+         i += kRsThreads)
+      sum += v[i];
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31u) == 0u) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x < 32u) {
+      uint32_t x = threadIdx.x < kRsThreads / 32u ? red[threadIdx.x] : 0u;
+      x = warp_sum(x);
+      if (threadIdx.x == 0u) tile_sums[t] = x;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRsScanThreads) rs_scan_tiles_kernel(uint32_t *tile_sums,
+                                                                       const uint32_t *count_dev,
+                                                                       uint32_t count_host,
+                                                                       uint32_t *total) {
+  const uint32_t count = scan_count(count_dev, count_host);
+  cta_exclusive_scan(tile_sums, (count + kRsScanTile - 1u) / kRsScanTile, total);
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_scan_down_kernel(uint32_t *v,
+                                                                  const uint32_t *count_dev,
+                                                                  uint32_t count_host,
+                                                                  const uint32_t *tile_sums) {
+  __shared__ uint32_t scratch[33];
+  const uint32_t count = scan_count(count_dev, count_host);
+  const uint32_t ntiles = (count + kRsScanTile - 1u) / kRsScanTile;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // thread i takes the 16 consecutive values [16 i, 16 i + 16) of the tile
+    const uint32_t lo = t * kRsScanTile + 16u * threadIdx.x;
+    uint32_t x[16], sum = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < 16u; ++u) {
+      x[u] = lo + u < count ? v[lo + u] : 0u;
+      sum += x[u];
+    }
+    uint32_t tot;
+    uint32_t run = tile_sums[t] + block_exclusive_scan(sum, scratch, &tot);
+#pragma unroll
+    for (uint32_t u = 0; u < 16u; ++u) {
+      if (lo + u < count) v[lo + u] = run;
+      run += x[u];
+    }
+  }
 }
 
 // per active segment: its zeros, Z_s, its children above B; the split point joins the bitmap
@@ -229,23 +289,36 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
       __syncthreads();
       const bool last = (m < kRsSegCap) || (k + m >= na) || (a.act[k + m].x >= c1);
       const uint64_t span_hi = last ? c1 : min(static_cast<uint64_t>(sg[m - 1u].y), c1);
+      // eight positions a thread per round (their loads in flight together), each to its place
+      constexpr uint32_t kU = 8u;
       uint32_t j = 0;
-      for (uint64_t p = span_lo + tid; p < span_hi; p += kRsThreads) {
-        while (j < m && sg[j].y <= p) ++j;
-        E v;
-        if constexpr (kPerm) v = static_cast<E>(p);
-        else v = in[p];
-        uint64_t dst = p;
-        if (j < m && sg[j].x <= p) {
-          const uint4 g = sg[j];
-          const uint32_t q = static_cast<uint32_t>(p - c0);
-          const uint32_t wv = cw[q >> 5];
-          const uint32_t Zp = Zc + zw[q >> 5] + __popc(~wv & low_mask(q & 31u));
-          const uint32_t zin = Zp - g.w;  // zeros of the segment before p
-          dst = ((wv >> (q & 31u)) & 1u) ? g.x + g.z + static_cast<uint32_t>(p - g.x) - zin
-                                         : g.x + zin;
+      for (uint64_t p0 = span_lo + tid; p0 < span_hi; p0 += kU * kRsThreads) {
+        E v[kU];
+#pragma unroll
+        for (uint32_t u = 0; u < kU; ++u) {
+          const uint64_t p = p0 + static_cast<uint64_t>(u) * kRsThreads;
+          if (p < span_hi) {
+            if constexpr (kPerm) v[u] = static_cast<E>(p);
+            else v[u] = in[p];
+          }
         }
-        out[min(dst, a.n - 1u)] = v;
+#pragma unroll
+        for (uint32_t u = 0; u < kU; ++u) {
+          const uint64_t p = p0 + static_cast<uint64_t>(u) * kRsThreads;
+          if (p >= span_hi) break;
+          while (j < m && sg[j].y <= p) ++j;
+          uint64_t dst = p;
+          if (j < m && sg[j].x <= p) {
+            const uint4 g = sg[j];
+            const uint32_t q = static_cast<uint32_t>(p - c0);
+            const uint32_t wv = cw[q >> 5];
+            const uint32_t Zp = Zc + zw[q >> 5] + __popc(~wv & low_mask(q & 31u));
+            const uint32_t zin = Zp - g.w;  // zeros of the segment before p
+            dst = ((wv >> (q & 31u)) & 1u) ? g.x + g.z + static_cast<uint32_t>(p - g.x) - zin
+                                           : g.x + zin;
+          }
+          out[min(dst, a.n - 1u)] = v[u];
+        }
       }
       if (last) break;
       k += m;
@@ -257,66 +330,107 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 }
 
 // Algorithm 1 on every final segment (at most B elements each; a segment starts at every set
-// bit of the boundary bitmap and ends at the next one, or at n). One warp per CTA takes windows
-// of `lanes` bitmap words; lane j owns word j of the window and takes the segments that start in
-// it, one per round, lowest first. It shuffles the local indices 0..L-1 of its segment in shared
-// memory (stride P = 2 mod 64: the lanes' entries at one index sit in distinct banks) with the
-// draws of stream (5, 0, s, i); the warp then writes each segment of the round through its
-// indices: out[s + i] = in[s + idx[i]].
+// bit of the boundary bitmap and ends at the next one, or at n). One warp per CTA walks windows
+// of kRsFyWinWords bitmap words, collecting the starts in order into a shared list; each batch
+// of `lanes` starts goes to the lanes, one segment a lane: the lane shuffles the local indices
+// 0..L-1 of its segment in shared memory (stride P = 2 mod 64: the lanes' entries at one index
+// sit in distinct banks) with the draws of stream (5, 0, s, i), then the warp writes each
+// segment of the batch through its indices: out[s + i] = in[s + idx[i]].
+constexpr uint32_t kRsFyWinWords = 1024u;
+
+template <typename E>
+__device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const uint32_t *bnd,
+                            uint32_t P, const uint32_t *list, uint32_t k, uint16_t *idx) {
+  const uint32_t lane = threadIdx.x;
+  const uint64_t nwords = (n + 31u) >> 5;
+  uint32_t s_pos = 0u, L = 0u;
+  if (lane < k) {
+    s_pos = list[lane];
+    uint64_t e = n;
+    if (lane + 1u < k) {
+      e = list[lane + 1u];
+    } else {
+      // the next start after s_pos in the bitmap (a later bit of its word, else a later word)
+      const uint64_t w = static_cast<uint64_t>(s_pos) >> 5;
+      uint32_t bw = bnd[w] & ~low_mask((s_pos & 31u) + 1u);
+      uint64_t q = w;
+      while (bw == 0u && ++q < nwords) bw = bnd[q];
+      if (bw) e = (q << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(bw)) - 1);
+    }
+    L = static_cast<uint32_t>(min(e, n) - s_pos);
+    L = min(L, P - 2u);  // (a final segment never exceeds B <= P - 2)
+    uint16_t *const A = idx + lane * P;
+    for (uint32_t i = 0; i < L; ++i) A[i] = static_cast<uint16_t>(i);
+    DrawMemo memo;
+    for (uint32_t i = L; i-- > 1u;) {
+      const uint32_t j = min(draw_uniform(key, kTagRsLeaf, 0u, s_pos, i, i + 1u, memo), i);
+      const uint16_t t = A[i];
+      A[i] = A[j];
+      A[j] = t;
+    }
+  }
+  __syncwarp();
+  // write the batch through the indices: eight independent row loads a lane in flight before
+  // their stores (one segment's rows at a time would wait out a load latency per 32 rows)
+  constexpr uint32_t kRows = 8u;
+  for (uint32_t r = 0; r < k; ++r) {
+    const uint32_t sr = __shfl_sync(kFullMask, s_pos, r);
+    const uint32_t Lr = __shfl_sync(kFullMask, L, r);
+    const uint16_t *const Ar = idx + r * P;
+    const E *const src = in + sr;
+    E *const dst = out + sr;
+    for (uint32_t i0 = 0; i0 < Lr; i0 += 32u * kRows) {
+      E v[kRows];
+#pragma unroll
+      for (uint32_t u = 0; u < kRows; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        if (i < Lr) v[u] = src[min(static_cast<uint32_t>(Ar[i]), Lr - 1u)];
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kRows; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        if (i < Lr) dst[i] = v[u];
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <typename E>
 __global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t n, uint2 key,
                                                   const uint32_t *bnd, uint32_t P,
                                                   uint32_t lanes) {
   extern __shared__ __align__(16) uint16_t idx[];
+  uint32_t *const list = reinterpret_cast<uint32_t *>(idx + ((lanes * P + 1u) & ~1u));
   const uint32_t lane = threadIdx.x;
   const uint64_t nwords = (n + 31u) >> 5;
-  uint16_t *const A = idx + lane * P;
-  for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * lanes; w0 < nwords;
-       w0 += static_cast<uint64_t>(gridDim.x) * lanes) {
-    const uint64_t wi = w0 + lane;
-    uint32_t word = (lane < lanes && wi < nwords) ? bnd[wi] : 0u;
-    while (__any_sync(kFullMask, word != 0u)) {
-      uint32_t s_pos = 0u, L = 0u;
-      if (word) {
-        const uint32_t b = static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
+  for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * kRsFyWinWords; w0 < nwords;
+       w0 += static_cast<uint64_t>(gridDim.x) * kRsFyWinWords) {
+    uint32_t cnt = 0;  // starts waiting in the list (uniform across the warp)
+    for (uint32_t cw = 0; cw < kRsFyWinWords && w0 + cw < nwords; cw += 32u) {
+      const uint64_t wi = w0 + cw + lane;
+      uint32_t word = wi < nwords ? bnd[wi] : 0u;
+      const uint32_t c = static_cast<uint32_t>(__popc(word));
+      const uint32_t incl = warp_inclusive_scan(c);
+      uint32_t pos = cnt + incl - c;
+      while (word) {
+        list[pos++] = static_cast<uint32_t>(wi << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
         word &= word - 1u;
-        s_pos = static_cast<uint32_t>(wi << 5) + b;
-        // the segment ends at the next start (a later bit of this word, else a later word)
-        uint64_t e = n;
-        if (word) {
-          e = (wi << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
-        } else {
-          for (uint64_t q = wi + 1u; q < nwords; ++q) {
-            const uint32_t bw = bnd[q];
-            if (bw) {
-              e = (q << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(bw)) - 1);
-              break;
-            }
-          }
-        }
-        L = static_cast<uint32_t>(min(e, n) - s_pos);
-        L = min(L, P - 2u);  // (a final segment never exceeds B <= P - 2)
-        for (uint32_t i = 0; i < L; ++i) A[i] = static_cast<uint16_t>(i);
-        DrawMemo memo;
-        for (uint32_t i = L; i-- > 1u;) {
-          const uint32_t j = min(draw_uniform(key, kTagRsLeaf, 0u, s_pos, i, i + 1u, memo), i);
-          const uint16_t t = A[i];
-          A[i] = A[j];
-          A[j] = t;
-        }
       }
+      cnt += __shfl_sync(kFullMask, incl, 31);
       __syncwarp();
-      for (uint32_t r = 0; r < lanes; ++r) {
-        const uint32_t sr = __shfl_sync(kFullMask, s_pos, r);
-        const uint32_t Lr = __shfl_sync(kFullMask, L, r);
-        const uint16_t *const Ar = idx + r * P;
-        for (uint32_t i = lane; i < Lr; i += 32u) {
-          const uint32_t src = min(static_cast<uint32_t>(Ar[i]), Lr - 1u);
-          out[static_cast<uint64_t>(sr) + i] = in[static_cast<uint64_t>(sr) + src];
+      while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
+        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, idx);
+        for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
+          const uint32_t v = list[i + lanes];
+          __syncwarp(__activemask());
+          list[i] = v;
         }
+        __syncwarp();
+        cnt -= lanes;
       }
-      __syncwarp();
     }
+    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, idx);
   }
 }
 
@@ -347,7 +461,7 @@ size_t up256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 struct RsLayout {
   uint32_t nchunks = 0, maxact = 0;
   size_t buf = 0, zc = 0, zb = 0, act0 = 0, act1 = 0, ctl = 0, zseg = 0, zs = 0, cnt = 0,
-         bnd = 0, total = 0;
+         bnd = 0, tsum = 0, total = 0;
 };
 
 RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
@@ -375,6 +489,8 @@ RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   off += up256(L.maxact * 4ull);
   L.bnd = off;
   off += up256(((n + 31u) / 32u + 1u) * 4u);
+  L.tsum = off;
+  off += up256((std::max<uint64_t>(L.maxact, L.nchunks) / kRsScanTile + 2u) * 4u);
   L.total = off;
   return L;
 }
@@ -412,10 +528,19 @@ cudaError_t rs_level(RsArgs a, uint32_t maxact, const void *in, void *out, uint3
                                                8ull * sms));
   const unsigned g_segs = static_cast<unsigned>(
       std::min<uint64_t>((maxact + kRsThreads - 1ull) / kRsThreads, 8ull * sms));
+  const unsigned g_tiles = static_cast<unsigned>(std::min<uint64_t>(
+      (std::max<uint64_t>(maxact, a.nchunks) + kRsScanTile - 1u) / kRsScanTile, 8ull * sms));
   rs_count_kernel<<<g_chunks, kRsThreads, 0, s>>>(a);
-  rs_chunk_scan_kernel<<<1, kRsScanThreads, 0, s>>>(a);
+  // exclusive prefix of the chunk zeros (the total after the last chunk)
+  rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
+  rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, nullptr, a.nchunks,
+                                                    a.zc + a.nchunks);
+  rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
   rs_children_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
-  rs_list_scan_kernel<<<1, kRsScanThreads, 0, s>>>(a);
+  // the next active list: exclusive prefix of the children kept, its total is the list size
+  rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.cnt, a.act_n, 0u, a.tsum);
+  rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, a.act_n, 0u, a.nxt_n);
+  rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.cnt, a.act_n, 0u, a.tsum);
   rs_list_write_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -431,16 +556,18 @@ cudaError_t rs_launch_fy(const void *in, void *out, uint64_t n, uint2 key, const
                          uint32_t B, int sms, cudaStream_t s) {
   uint32_t P = B + 2u;
   while (P % 64u != 2u) ++P;
-  constexpr uint32_t kBudget = 96u * 1024u;
+  constexpr uint32_t kBudget = 96u * 1024u;  // (index regions; the start list adds ~4.3 KB)
   const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (2u * P)));
-  const size_t smem = static_cast<size_t>(lanes) * P * 2u;
+  // the lanes' index regions, then the window's list of segment starts
+  const size_t smem = ((static_cast<size_t>(lanes) * P + 1u) & ~static_cast<size_t>(1u)) * 2u +
+                      (lanes + 32u * 32u + 32u) * 4u;  // (lanes waiting + one read of 32 words)
   auto kern = rs_fy_kernel<E>;
   cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
   if (e != cudaSuccess) return e;
-  const uint64_t windows = ((n + 31u) / 32u + lanes - 1u) / lanes;
+  const uint64_t windows = ((n + 31u) / 32u + kRsFyWinWords - 1u) / kRsFyWinWords;
   const uint64_t resident = static_cast<uint64_t>(std::max(per_sm, 1)) * sms;
   const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1u, std::min(windows, resident)));
   kern<<<grid, 32, smem, s>>>(static_cast<const E *>(in), static_cast<E *>(out), n, key, bnd, P,
@@ -490,6 +617,7 @@ ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, u
   a.zs = reinterpret_cast<uint32_t *>(base + L.zs);
   a.cnt = reinterpret_cast<uint32_t *>(base + L.cnt);
   a.bnd = reinterpret_cast<uint32_t *>(base + L.bnd);
+  a.tsum = reinterpret_cast<uint32_t *>(base + L.tsum);
   if (rs_failed(cudaMemsetAsync(a.bnd, 0, ((n + 31u) / 32u + 1u) * 4u, s)) ||
       rs_failed(cudaMemsetAsync(ctl, 0, 256, s)))
     return MS_ERR_CUDA;
