@@ -28,6 +28,7 @@
 #include "mergeshuffle.h"
 #include "ms_common.cuh"
 #include "ms_device.cuh"
+#include "ms_merge.cuh"
 #include "ms_plan.h"
 
 namespace msk {
@@ -58,6 +59,7 @@ struct RsArgs {
   uint32_t *cnt;       // per active segment: children above B, then their exclusive prefix
   uint32_t *bnd;       // boundary bitmap: bit p set iff a final segment starts at p
   uint32_t *tsum;      // scan scratch: one sum per tile of kRsScanTile values
+  uint32_t *cfirst;    // per chunk: the first active segment that ends after the chunk's start
 };
 
 __device__ __forceinline__ uint4 rs_block(uint2 key, uint32_t level, uint32_t blk) {
@@ -226,6 +228,23 @@ __global__ void __launch_bounds__(kRsThreads) rs_list_write_kernel(RsArgs a) {
   }
 }
 
+// per chunk: the first active segment that ends after the chunk's first position (one thread per
+// chunk; the active segments are disjoint and sorted)
+__global__ void __launch_bounds__(kRsThreads) rs_chunk_first_kernel(RsArgs a) {
+  const uint32_t na = *a.act_n;
+  for (uint32_t ch = blockIdx.x * kRsThreads + threadIdx.x; ch < a.nchunks;
+       ch += gridDim.x * kRsThreads) {
+    const uint64_t c0 = static_cast<uint64_t>(ch) * kRsChunk;
+    uint32_t lo = 0, hi = na;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a.act[mid].y <= c0) lo = mid + 1;
+      else hi = mid;
+    }
+    a.cfirst[ch] = lo;
+  }
+}
+
 // The data pass of one split level. A CTA takes a chunk of 4096 positions: warp 0 makes the
 // chunk's bits and the zeros before each word, the active segments that overlap the chunk are
 // staged in shared memory (in rounds of kRsSegCap), and every position goes to its place in its
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
   __shared__ uint32_t cw[kRsChunk / 32u];
   __shared__ uint32_t zw[kRsChunk / 32u];
   __shared__ uint4 sg[kRsSegCap];  // (s, e, z, Z_s)
-  __shared__ uint32_t s_first, s_count;
+  __shared__ uint32_t s_first;
   const uint32_t tid = threadIdx.x;
   const uint32_t lane = tid & 31u;
   const uint32_t na = *a.act_n;
@@ -258,35 +277,27 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
       zw[4u * lane + 2u] = ex;
       ex += __popc(~c.z);
       zw[4u * lane + 3u] = ex;
-      if (lane == 0) {
-        // first active segment ending after c0 (segments are disjoint and sorted)
-        uint32_t lo = 0, hi = na;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (a.act[mid].y <= c0) lo = mid + 1;
-          else hi = mid;
-        }
-        s_first = lo;
-      }
     }
+    if (tid == 0) s_first = a.cfirst[ch];
     __syncthreads();
     const uint32_t Zc = a.zc[ch];
     uint32_t k = s_first;
     uint64_t span_lo = c0;
     for (;;) {
-      // stage the next round of segments that start before c1
-      if (tid == 0) {
-        uint32_t m = 0;
-        while (m < kRsSegCap && k + m < na && a.act[k + m].x < c1) ++m;
-        s_count = m;
+      // stage the next round of segments that start before c1 (sorted: those form a prefix)
+      uint32_t m = 0;
+      for (uint32_t j0 = 0; j0 < kRsSegCap; j0 += kRsThreads) {
+        const uint32_t j = j0 + tid;
+        bool in_chunk = false;
+        if (j < kRsSegCap && k + j < na) {
+          const uint2 e = a.act[k + j];
+          in_chunk = e.x < c1;
+          if (in_chunk) sg[j] = make_uint4(e.x, e.y, a.zseg[k + j], a.zs[k + j]);
+        }
+        const uint32_t got = static_cast<uint32_t>(__syncthreads_count(in_chunk));
+        m += got;
+        if (got < kRsThreads) break;  // (uniform: every thread sees the same count)
       }
-      __syncthreads();
-      const uint32_t m = s_count;
-      for (uint32_t j = tid; j < m; j += kRsThreads) {
-        const uint2 e = a.act[k + j];
-        sg[j] = make_uint4(e.x, e.y, a.zseg[k + j], a.zs[k + j]);
-      }
-      __syncthreads();
       const bool last = (m < kRsSegCap) || (k + m >= na) || (a.act[k + m].x >= c1);
       const uint64_t span_hi = last ? c1 : min(static_cast<uint64_t>(sg[m - 1u].y), c1);
       // eight positions a thread per round (their loads in flight together), each to its place
@@ -340,7 +351,8 @@ constexpr uint32_t kRsFyWinWords = 1024u;
 
 template <typename E>
 __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const uint32_t *bnd,
-                            uint32_t P, const uint32_t *list, uint32_t k, uint16_t *idx) {
+                            uint32_t P, const uint32_t *list, uint32_t k, uint16_t *idx,
+                            uint32_t *pre) {
   const uint32_t lane = threadIdx.x;
   const uint64_t nwords = (n + 31u) >> 5;
   uint32_t s_pos = 0u, L = 0u;
@@ -361,37 +373,66 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
     L = min(L, P - 2u);  // (a final segment never exceeds B <= P - 2)
     uint16_t *const A = idx + lane * P;
     for (uint32_t i = 0; i < L; ++i) A[i] = static_cast<uint16_t>(i);
-    DrawMemo memo;
-    for (uint32_t i = L; i-- > 1u;) {
-      const uint32_t j = min(draw_uniform(key, kTagRsLeaf, 0u, s_pos, i, i + 1u, memo), i);
-      const uint16_t t = A[i];
-      A[i] = A[j];
-      A[j] = t;
+    // i = L-1 .. 1 by quads of positions (one Philox block draws four of them); the next quad's
+    // block is computed while the current one's swaps run
+    if (L >= 2u) {
+      uint32_t quad = (L - 1u) >> 2;
+      uint4 cur = philox10(make_uint4(quad, s_pos, kTagRsLeaf << 16, 0u), key);
+      for (;;) {
+        const uint4 nxt =
+            quad > 0 ? philox10(make_uint4(quad - 1u, s_pos, kTagRsLeaf << 16, 0u), key) : cur;
+        const uint32_t lo = quad << 2;
+#pragma unroll
+        for (uint32_t v = 4; v-- > 0;) {
+          const uint32_t pos = lo + v;
+          if (pos < L && pos >= 1u) {
+            const uint32_t j = min(draw_with_word0_flat(key, kTagRsLeaf, 0u, s_pos, pos, pos + 1u,
+                                                        pick_word(cur, v)),
+                                   pos);
+            const uint16_t t = A[pos];
+            A[pos] = A[j];
+            A[j] = t;
+          }
+        }
+        if (quad == 0) break;
+        --quad;
+        cur = nxt;
+      }
     }
   }
+  // the batch's rows through the indices, flattened over its segments (pre: exclusive prefix of
+  // the lengths): sixteen independent row loads a lane in flight before their stores
+  const uint32_t incl = warp_inclusive_scan(L);
+  pre[lane] = incl - L;
+  const uint32_t total = __shfl_sync(kFullMask, incl, 31);
   __syncwarp();
-  // write the batch through the indices: eight independent row loads a lane in flight before
-  // their stores (one segment's rows at a time would wait out a load latency per 32 rows)
-  constexpr uint32_t kRows = 8u;
-  for (uint32_t r = 0; r < k; ++r) {
-    const uint32_t sr = __shfl_sync(kFullMask, s_pos, r);
-    const uint32_t Lr = __shfl_sync(kFullMask, L, r);
-    const uint16_t *const Ar = idx + r * P;
-    const E *const src = in + sr;
-    E *const dst = out + sr;
-    for (uint32_t i0 = 0; i0 < Lr; i0 += 32u * kRows) {
-      E v[kRows];
+  constexpr uint32_t kRows = sizeof(E) >= 16u ? 8u : 16u;
+  for (uint32_t e0 = 0; e0 < total; e0 += 32u * kRows) {
+    E v[kRows];
+    uint32_t dst[kRows];
 #pragma unroll
-      for (uint32_t u = 0; u < kRows; ++u) {
-        const uint32_t i = i0 + 32u * u + lane;
-        if (i < Lr) v[u] = src[min(static_cast<uint32_t>(Ar[i]), Lr - 1u)];
-      }
-#pragma unroll
-      for (uint32_t u = 0; u < kRows; ++u) {
-        const uint32_t i = i0 + 32u * u + lane;
-        if (i < Lr) dst[i] = v[u];
+    for (uint32_t t = 0; t < kRows; ++t) {
+      const uint32_t e = e0 + 32u * t + lane;
+      dst[t] = 0xFFFFFFFFu;
+      if (e < total) {
+        // the segment of flat index e: the last r < k with pre[r] <= e
+        uint32_t lo = 0, hi = k;
+        while (hi - lo > 1u) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (pre[mid] <= e) lo = mid;
+          else hi = mid;
+        }
+        const uint32_t i = e - pre[lo];
+        const uint32_t base = list[lo];
+        const uint16_t *const Ar = idx + lo * P;
+        const uint32_t Lr = (lo + 1u < k ? pre[lo + 1u] : total) - pre[lo];
+        v[t] = in[static_cast<uint64_t>(base) + min(static_cast<uint32_t>(Ar[i]), Lr - 1u)];
+        dst[t] = base + i;
       }
     }
+#pragma unroll
+    for (uint32_t t = 0; t < kRows; ++t)
+      if (dst[t] != 0xFFFFFFFFu) out[dst[t]] = v[t];
   }
   __syncwarp();
 }
@@ -401,6 +442,7 @@ __global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t
                                                   const uint32_t *bnd, uint32_t P,
                                                   uint32_t lanes) {
   extern __shared__ __align__(16) uint16_t idx[];
+  __shared__ uint32_t pre[32];
   uint32_t *const list = reinterpret_cast<uint32_t *>(idx + ((lanes * P + 1u) & ~1u));
   const uint32_t lane = threadIdx.x;
   const uint64_t nwords = (n + 31u) >> 5;
@@ -420,7 +462,7 @@ __global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t
       cnt += __shfl_sync(kFullMask, incl, 31);
       __syncwarp();
       while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
-        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, idx);
+        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, idx, pre);
         for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
           const uint32_t v = list[i + lanes];
           __syncwarp(__activemask());
@@ -430,7 +472,7 @@ __global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t
         cnt -= lanes;
       }
     }
-    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, idx);
+    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, idx, pre);
   }
 }
 
@@ -461,7 +503,7 @@ size_t up256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 struct RsLayout {
   uint32_t nchunks = 0, maxact = 0;
   size_t buf = 0, zc = 0, zb = 0, act0 = 0, act1 = 0, ctl = 0, zseg = 0, zs = 0, cnt = 0,
-         bnd = 0, tsum = 0, total = 0;
+         bnd = 0, tsum = 0, cfirst = 0, total = 0;
 };
 
 RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
@@ -491,6 +533,8 @@ RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   off += up256(((n + 31u) / 32u + 1u) * 4u);
   L.tsum = off;
   off += up256((std::max<uint64_t>(L.maxact, L.nchunks) / kRsScanTile + 2u) * 4u);
+  L.cfirst = off;
+  off += up256(L.nchunks * 4ull);
   L.total = off;
   return L;
 }
@@ -542,6 +586,9 @@ cudaError_t rs_level(RsArgs a, uint32_t maxact, const void *in, void *out, uint3
   rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, a.act_n, 0u, a.nxt_n);
   rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.cnt, a.act_n, 0u, a.tsum);
   rs_list_write_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
+  rs_chunk_first_kernel<<<static_cast<unsigned>(std::min<uint64_t>(
+                              (a.nchunks + kRsThreads - 1u) / kRsThreads, 8ull * sms)),
+                          kRsThreads, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   switch (w) {
@@ -618,6 +665,7 @@ ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, u
   a.cnt = reinterpret_cast<uint32_t *>(base + L.cnt);
   a.bnd = reinterpret_cast<uint32_t *>(base + L.bnd);
   a.tsum = reinterpret_cast<uint32_t *>(base + L.tsum);
+  a.cfirst = reinterpret_cast<uint32_t *>(base + L.cfirst);
   if (rs_failed(cudaMemsetAsync(a.bnd, 0, ((n + 31u) / 32u + 1u) * 4u, s)) ||
       rs_failed(cudaMemsetAsync(ctl, 0, 256, s)))
     return MS_ERR_CUDA;
