@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
         if (j < kRsSegCap && k + j < na) {
           const uint2 e = a.act[k + j];
           in_chunk = e.x < c1;
-          if (in_chunk) sg[j] = make_uint4(e.x, e.y, a.zseg[k + j], a.zs[k + j]);
+          // (s, e, A0 = s - Z_s, B1 = z + Z_s): bit 0 goes to A0 + Z_p, bit 1 to B1 + p - Z_p
+          if (in_chunk) {
+            const uint32_t Zs = a.zs[k + j];
+            sg[j] = make_uint4(e.x, e.y, e.x - Zs, a.zseg[k + j] + Zs);
+          }
         }
         const uint32_t got = static_cast<uint32_t>(__syncthreads_count(in_chunk));
         m += got;
@@ -300,35 +304,40 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
       }
       const bool last = (m < kRsSegCap) || (k + m >= na) || (a.act[k + m].x >= c1);
       const uint64_t span_hi = last ? c1 : min(static_cast<uint64_t>(sg[m - 1u].y), c1);
-      // eight positions a thread per round (their loads in flight together), each to its place
+      // eight positions a thread per round (their loads in flight together), each to its place;
+      // positions are 32-bit (n < 2^32), the thread's current segment is kept in registers
       constexpr uint32_t kU = 8u;
+      const uint32_t lo32 = static_cast<uint32_t>(span_lo), hi32 = static_cast<uint32_t>(span_hi);
+      const uint32_t cbase = static_cast<uint32_t>(c0);
+      const uint32_t nlast = static_cast<uint32_t>(a.n - 1u);
       uint32_t j = 0;
-      for (uint64_t p0 = span_lo + tid; p0 < span_hi; p0 += kU * kRsThreads) {
+      uint4 g = m ? sg[0] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+      for (uint32_t p0 = lo32 + tid; p0 < hi32; p0 += kU * kRsThreads) {
         E v[kU];
 #pragma unroll
         for (uint32_t u = 0; u < kU; ++u) {
-          const uint64_t p = p0 + static_cast<uint64_t>(u) * kRsThreads;
-          if (p < span_hi) {
+          const uint32_t p = p0 + u * kRsThreads;
+          if (p < hi32) {
             if constexpr (kPerm) v[u] = static_cast<E>(p);
             else v[u] = in[p];
           }
         }
 #pragma unroll
         for (uint32_t u = 0; u < kU; ++u) {
-          const uint64_t p = p0 + static_cast<uint64_t>(u) * kRsThreads;
-          if (p >= span_hi) break;
-          while (j < m && sg[j].y <= p) ++j;
-          uint64_t dst = p;
-          if (j < m && sg[j].x <= p) {
-            const uint4 g = sg[j];
-            const uint32_t q = static_cast<uint32_t>(p - c0);
+          const uint32_t p = p0 + u * kRsThreads;
+          if (p >= hi32) break;
+          while (g.y <= p && j < m) {
+            ++j;
+            g = j < m ? sg[j] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+          }
+          uint32_t dst = p;
+          if (g.x <= p) {
+            const uint32_t q = p - cbase;
             const uint32_t wv = cw[q >> 5];
             const uint32_t Zp = Zc + zw[q >> 5] + __popc(~wv & low_mask(q & 31u));
-            const uint32_t zin = Zp - g.w;  // zeros of the segment before p
-            dst = ((wv >> (q & 31u)) & 1u) ? g.x + g.z + static_cast<uint32_t>(p - g.x) - zin
-                                           : g.x + zin;
+            dst = ((wv >> (q & 31u)) & 1u) ? g.w + p - Zp : g.z + Zp;
           }
-          out[min(dst, a.n - 1u)] = v[u];
+          out[min(dst, nlast)] = v[u];
         }
       }
       if (last) break;
