@@ -25,6 +25,7 @@ LITERAL = 1
 PHILOX = 0
 SEQFDR = 2
 FDR = 4
+BALANCED = 8
 
 # planted mistakes (exhaustive-walk tests only)
 PLANT_FY_RANGE = 16

@@ -332,11 +332,35 @@ static uint64_t merge_literal(ms_src *src, unsigned char *a, uint64_t n1, uint64
   return T;
 }
 
+/* Merge driven by a balanced word (Section 3's idea; its correctness lemma: a uniform word in
+ * C(n1 + n2, n1) interleaving two uniformly shuffled lists gives a uniform permutation). The
+ * word: the labels (0 for the first half, 1 for the second) merged by this merge's own coin loop
+ * and random insertions -- uniform over C(N, n1) by the Merge lemma, drawn from the same
+ * streams as the stable merge, with the same bits. The data is then interleaved stably by the
+ * word: no insertion moves an element. */
+static uint64_t merge_balanced(ms_src *src, const unsigned char *A, uint64_t n1,
+                               const unsigned char *Bh, uint64_t n2, unsigned char *out,
+                               uint32_t w, uint32_t level, uint32_t id, ms_oracle_stats *st) {
+  uint64_t N = n1 + n2;
+  unsigned char *lab = (unsigned char *)calloc(2 * N + 2, 1);
+  if (!lab) { src->failed = 1; return 0; }
+  unsigned char *word = lab + N + 1;
+  for (uint64_t i = 0; i < N; ++i) lab[i] = i < n1 ? 0 : 1;
+  uint64_t T = merge_stable(src, lab, n1, lab + n1, n2, word, 1, level, id, st);
+  uint64_t z = 0, o = 0;
+  for (uint64_t t = 0; t < N; ++t) {
+    if (word[t] == 0) memcpy(out + t * w, A + (z++) * w, w);
+    else memcpy(out + t * w, Bh + (o++) * w, w);
+  }
+  free(lab);
+  return T;
+}
+
 /* ------------------------------------------------------------------ Algorithm 2 --------- */
 /* Split into q = 2^c blocks, Fisher-Yates each block, then merge adjacent blocks level by level:
  * on level l (p = 2^l) merge r joins [b(2pr), b(2pr+p)) and [b(2pr+p), b(2pr+2p)). */
 static int run_mergeshuffle(ms_src *src, unsigned char *data, uint64_t n, uint32_t w, uint32_t B,
-                            int literal, ms_oracle_stats *st) {
+                            int literal, ms_oracle_stats *st, int balanced) {
   if (n <= 1) return 0;
   uint32_t c = ms_oracle_levels(n, B);
   uint64_t q = (uint64_t)1 << c;
@@ -369,8 +393,12 @@ static int run_mergeshuffle(ms_src *src, unsigned char *data, uint64_t n, uint32
       uint64_t s = boundary(n, c, 2 * p * r);
       uint64_t mid = boundary(n, c, 2 * p * r + p);
       uint64_t e = boundary(n, c, 2 * p * r + 2 * p);
-      merge_stable(src, cur + s * w, mid - s, cur + mid * w, e - mid, nxt + s * w, w, level,
-                   (uint32_t)r, st);
+      if (balanced)
+        merge_balanced(src, cur + s * w, mid - s, cur + mid * w, e - mid, nxt + s * w, w, level,
+                       (uint32_t)r, st);
+      else
+        merge_stable(src, cur + s * w, mid - s, cur + mid * w, e - mid, nxt + s * w, w, level,
+                     (uint32_t)r, st);
     }
     unsigned char *t = cur; cur = nxt; nxt = t;
   }
@@ -514,12 +542,14 @@ int ms_oracle_shuffle(void *data, uint64_t n, uint32_t w, uint64_t seed, uint32_
   if (mode & MS_ORACLE_SEQFDR) {
     seq_src q;
     init_seq(&q, seed);
-    return run_mergeshuffle(&q.base, (unsigned char *)data, n, w, B, literal, st);
+    return run_mergeshuffle(&q.base, (unsigned char *)data, n, w, B, literal, st,
+                            (mode & MS_ORACLE_BALANCED) != 0);
   }
   philox_src p;
   init_philox(&p, seed);
   if (mode & MS_ORACLE_FDR) p.base.uniform = philox_fdr_uniform;
-  return run_mergeshuffle(&p.base, (unsigned char *)data, n, w, B, literal, st);
+  return run_mergeshuffle(&p.base, (unsigned char *)data, n, w, B, literal, st,
+                          (mode & MS_ORACLE_BALANCED) != 0);
 }
 
 int ms_oracle_perm(uint32_t *out, uint64_t n, uint64_t seed, uint32_t B, int mode,
@@ -545,6 +575,13 @@ int ms_oracle_merge(uint32_t *a, uint64_t n1, uint64_t n2, uint64_t seed, uint32
   uint64_t T;
   if (mode & MS_ORACLE_LITERAL) {
     T = merge_literal(src, (unsigned char *)a, n1, n2, 4, level, id, st);
+  } else if (mode & MS_ORACLE_BALANCED) {
+    uint32_t *out = (uint32_t *)malloc((n1 + n2 + 1) * sizeof(uint32_t));
+    if (!out) return 2;
+    T = merge_balanced(src, (unsigned char *)a, n1, (unsigned char *)(a + n1), n2,
+                       (unsigned char *)out, 4, level, id, st);
+    memcpy(a, out, (n1 + n2) * sizeof(uint32_t));
+    free(out);
   } else {
     uint32_t *out = (uint32_t *)malloc((n1 + n2 + 1) * sizeof(uint32_t));
     if (!out) return 2;
@@ -684,7 +721,7 @@ int ms_oracle_enumerate(uint32_t n, uint32_t B, int mode, uint64_t *num, uint64_
     e.depth = 0;
     e.prod = 1;
     run_mergeshuffle(&e.base, (unsigned char *)perm, n, 4, B, (mode & MS_ORACLE_LITERAL) != 0,
-                     &st);
+                     &st, (mode & MS_ORACLE_BALANCED) != 0);
     if (e.overflow || D % e.prod != 0) { rc = 4; break; }
     acc[lehmer_rank(perm, n)] += D / e.prod;
     ++leaves;
@@ -728,6 +765,9 @@ int ms_oracle_enumerate_merge(uint32_t a, uint32_t b, int mode, uint64_t *num, u
     if (mode & MS_ORACLE_LITERAL) {
       merge_literal(&e.base, (unsigned char *)in, a, b, 4, 0, 0, &st);
       memcpy(out, in, sizeof in);
+    } else if (mode & MS_ORACLE_BALANCED) {
+      merge_balanced(&e.base, (unsigned char *)in, a, (unsigned char *)(in + a), b,
+                     (unsigned char *)out, 4, 0, 0, &st);
     } else {
       merge_stable(&e.base, (unsigned char *)in, a, (unsigned char *)(in + a), b,
                    (unsigned char *)out, 4, 0, 0, &st);

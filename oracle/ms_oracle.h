@@ -52,6 +52,8 @@ enum {
   MS_ORACLE_SEQFDR = 2,
   MS_ORACLE_FDR = 4, /* Philox streams, uniform draws by the Fast Dice Roller on each draw's
                         own stream (MS-Philox-FDR; coins unchanged) */
+  MS_ORACLE_BALANCED = 8, /* merges driven by a balanced word: the labels merged by the coin
+                             loop and insertions, then a stable interleave of the data */
   /* Planted mistakes, for tests that show the pins catch them (never used otherwise):
    * Sattolo-style off-by-one ranges in Algorithm 1 or in the merge tail, or no tail at all. */
   MS_ORACLE_PLANT_FY_RANGE = 16,
