@@ -521,7 +521,7 @@ def run_ours(args, world, rank, local):
         line["batched_large"] = run_batched(args, large=True, steps=ks, warmup=kw)
         line["serve"] = run_serve(args)
         line["rao_sandelius"] = run_rs(args, t_perm_ms)
-        line["literal_and_fdr"] = run_literal_fdr(args)
+        line["merge_variants"] = run_literal_fdr(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -786,10 +786,11 @@ def run_rs(args, t_ms_mergeshuffle=None, steps: int = 5, warmup: int = 2) -> dic
 
 
 def run_literal_fdr(args, steps: int = 3, warmup: int = 1) -> dict:
-    """Algorithm 3 as printed (MS_FLAG_LITERAL) and Fast Dice Roller draws (MS_FLAG_FDR) on the
-    scale workload's perm (2^30, seed 7, B = 512), timed beside the default plan with the same
-    forced shape (fuse_depth 0, one global pass per level); and Table 1's measure, the random bits
-    consumed, counted on the GPU for n = 10^5 .. 10^8 with rejection draws and with FDR draws."""
+    """Algorithm 3 as printed (MS_FLAG_LITERAL), Fast Dice Roller draws (MS_FLAG_FDR) and merges
+    driven by a balanced word (MS_FLAG_BALANCED) on the scale workload's perm (2^30, seed 7,
+    B = 512), timed beside the default plan with the same forced shape (fuse_depth 0, one global
+    pass per level); and Table 1's measure, the random bits consumed, counted on the GPU for
+    n = 10^5 .. 10^8 with rejection draws and with FDR draws."""
     import torch
 
     import paper_1508_03167_gb300 as ms
@@ -801,7 +802,8 @@ def run_literal_fdr(args, steps: int = 3, warmup: int = 1) -> dict:
     res = {}
     for tag, flags in (("single_levels", ms.MS_FLAG_GLOBAL_LEVELS | ms.MS_FLAG_SINGLE_LEVELS),
                        ("literal", ms.MS_FLAG_LITERAL), ("fdr", ms.MS_FLAG_FDR),
-                       ("literal_fdr", ms.MS_FLAG_LITERAL | ms.MS_FLAG_FDR)):
+                       ("literal_fdr", ms.MS_FLAG_LITERAL | ms.MS_FLAG_FDR),
+                       ("balanced_word", ms.MS_FLAG_BALANCED)):
         p = ms.params(B=B, fuse_depth=0, flags=flags)
         ws = torch.empty(ms.ms_workspace_bytes(n, 4, p), dtype=torch.uint8, device="cuda")
 

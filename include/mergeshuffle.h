@@ -111,6 +111,15 @@ typedef void *ms_stream_t;
                                         Single calls only (the batched form returns
                                         MS_ERR_UNSUPPORTED); runs with fuse_depth 0 and one
                                         global pass per level. */
+#define MS_FLAG_BALANCED 0x1000u     /* every merge driven by a balanced word (the idea of the
+                                        paper's Section 3): the halves' labels merged by the
+                                        merge's own coins and insertions give a uniform word
+                                        with exactly n1 zeros, and the data is interleaved
+                                        stably by it, so no insertion moves an element (a
+                                        different result, same random bits; the oracle's
+                                        BALANCED mode). Not with MS_FLAG_LITERAL
+                                        (MS_ERR_INVALID); single calls only; fuse_depth 0 and
+                                        one global pass per level. */
 #define MS_FLAG_SINGLE_STREAM 0x20u  /* enqueue every kernel on the caller's stream: no plan
                                         stream beside it (the result is identical). By default
                                         the data-independent plan of each global merge level

@@ -14,7 +14,7 @@ import threading
 
 __all__ = [
     "MS_OK", "MS_ERR_INVALID", "MS_ERR_UNSUPPORTED", "MS_ERR_NOMEM", "MS_ERR_CUDA",
-    "MS_ERR_TIMEOUT", "RANDOM_BIT_FIELDS", "ms_random_bits", "ms_random_bits_workspace", "random_bits", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_FLAG_SINGLE_LEVELS", "MS_FLAG_PAIR_LEVELS", "MS_FLAG_CTA_TILES", "MS_FLAG_LITERAL", "MS_FLAG_FDR", "MS_MAX_B", "ms_batch_workspace_bytes",
+    "MS_ERR_TIMEOUT", "RANDOM_BIT_FIELDS", "ms_random_bits", "ms_random_bits_workspace", "random_bits", "MS_FLAG_TAIL_SEQUENTIAL", "MS_FLAG_PROFILE", "MS_FLAG_GLOBAL_LEVELS", "MS_FLAG_CTA_LEVELS", "MS_FLAG_PERM", "MS_FLAG_SINGLE_STREAM", "MS_FLAG_WARP_LEVELS", "MS_FLAG_SINGLE_LEVELS", "MS_FLAG_PAIR_LEVELS", "MS_FLAG_CTA_TILES", "MS_FLAG_LITERAL", "MS_FLAG_FDR", "MS_FLAG_BALANCED", "MS_MAX_B", "ms_batch_workspace_bytes",
     "ms_batch_prepare", "ms_batch_run", "ms_shuffle_batch", "batch_workspace", "shuffle_batch", "MsParams",
     "MsPlan", "MsProfile", "MsError", "ms_profile_read", "profile",
     "lib", "library_path", "ms_default_params", "ms_plan_info", "ms_workspace_bytes",
@@ -38,6 +38,7 @@ MS_FLAG_PAIR_LEVELS = 0x100
 MS_FLAG_CTA_TILES = 0x200
 MS_FLAG_LITERAL = 0x400
 MS_FLAG_FDR = 0x800
+MS_FLAG_BALANCED = 0x1000
 MS_MAX_B = 4096
 MS_STATIC_MAX_N = 1 << 21
 MS_STATIC_SCRATCH_BYTES = 16 << 20

@@ -133,7 +133,8 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   if (B == 0) return 1;
   if (n > 0xFFFFFFFFull) return 1;
   if (B > kMaxB) return 2;
-  if (flags & (MS_FLAG_LITERAL | MS_FLAG_FDR)) {
+  if ((flags & MS_FLAG_LITERAL) && (flags & MS_FLAG_BALANCED)) return 1;
+  if (flags & (MS_FLAG_LITERAL | MS_FLAG_FDR | MS_FLAG_BALANCED)) {
     // the literal merge and the FDR draws run on the global levels only: no fused levels, no
     // fused pairs
     fuse_depth = 0;
@@ -372,6 +373,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   p.hbm_passes = nlocal + units;
   const bool pairs = xhbits_max > 0;
   const bool literal = (flags & MS_FLAG_LITERAL) != 0;
+  const bool balanced = (flags & MS_FLAG_BALANCED) != 0;
   uint32_t lcap_max = 0;
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     uint32_t lg = 0;
@@ -401,7 +403,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     p.plan_sets = units >= 2 ? 4u : 2u;
     off += (p.plan_sets - 1) * p.plan_set_bytes;
     // exception structures of a pair's first level, one copy per live unit (after the sets)
-    if (pairs || literal) {
+    if (pairs || literal || balanced) {
       const size_t ebase = off;
       p.off_zb = off - ebase;     off += round_up(zc_cap * 32ull, 256);
       if (pairs) {
@@ -411,6 +413,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       }
       if (literal) {
         p.off_laps = off - ebase;   off += round_up(static_cast<size_t>(lcap_max) * 8u, 256);
+      }
+      if (balanced) {
+        p.off_labels = off - ebase; off += round_up(n, 256);
+        p.off_zlab = off - ebase;   off += round_up(zc_cap * 4ull, 256);
       }
       p.exc_base = ebase;
       p.exc_bytes = off - ebase;
@@ -530,6 +536,8 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   b.xkeys = reinterpret_cast<uint32_t *>(es + p.off_xkeys);
   b.xvals = reinterpret_cast<uint32_t *>(es + p.off_xvals);
   b.laps = reinterpret_cast<uint2 *>(es + p.off_laps);
+  b.labels = reinterpret_cast<uint8_t *>(es + p.off_labels);
+  b.zlab = reinterpret_cast<uint32_t *>(es + p.off_zlab);
   b.zc = reinterpret_cast<uint32_t *>(ps + p.off_zc);
   b.minfo = reinterpret_cast<uint4 *>(ps + p.off_minfo);
   b.ctrl = reinterpret_cast<uint32_t *>(ps + p.off_ctrl);
@@ -726,7 +734,7 @@ ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_par
   const ms_params r = msk::resolve_batch(k, h_n, w, params);
   if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
   if ((r.flags & MS_FLAG_PERM) && w != 4) return MS_ERR_INVALID;
-  if (r.flags & (MS_FLAG_LITERAL | MS_FLAG_FDR)) return MS_ERR_UNSUPPORTED;
+  if (r.flags & (MS_FLAG_LITERAL | MS_FLAG_FDR | MS_FLAG_BALANCED)) return MS_ERR_UNSUPPORTED;
   if (r.B == 0) return MS_ERR_INVALID;
   if (r.B > MS_MAX_B) return MS_ERR_UNSUPPORTED;
   if (k > 0 && h_n == nullptr) return MS_ERR_INVALID;

@@ -1177,6 +1177,156 @@ __global__ void __launch_bounds__(kThreads) literal_scatter_kernel(LevelArgs a) 
   }
 }
 
+// ---------------------------------------------------------- balanced-word merge (flag) -----
+// Merges driven by a balanced word (MS_FLAG_BALANCED; the idea of the paper's Section 3). The word
+// of merge r is its halves' labels (0 first half, 1 second half) merged by the merge's own coin
+// loop and random insertions: label t is coin t for t < T and the label of the half that did not
+// run out beyond, then the insertions move labels exactly as they would move elements. So the
+// label bytes of a level are written, the usual tail patches (or the sequential fallback) run on
+// them, and the data is interleaved stably by the resulting word -- no element is moved by an
+// insertion. Label bytes sit at the global position of their merge output.
+
+// the level's labels before the insertions: one chunk of 4096 steps of one merge per CTA
+__global__ void __launch_bounds__(kThreads) label_kernel(LevelArgs a, uint8_t *lab) {
+  __shared__ uint32_t cw[kChunk / 32u];
+  const uint32_t tid = threadIdx.x;
+  const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t r = static_cast<uint32_t>(cid / a.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(r) * a.J);
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t t0 = j * kChunk;
+    if (t0 >= N) continue;  // uniform across the CTA
+    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint4 mi = a.minfo[r];
+    const uint32_t T = mi.x;
+    const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+    const uint8_t left = (mi.y == n1) ? 1u : 0u;  // the first half ran out: the rest are its other
+    if (tid < 32u) {
+      const uint4 c = coin_block(a.key, a.level, r, j * (kChunk / 128u) + tid);
+      cw[4u * tid + 0u] = c.x;
+      cw[4u * tid + 1u] = c.y;
+      cw[4u * tid + 2u] = c.z;
+      cw[4u * tid + 3u] = c.w;
+    }
+    __syncthreads();
+    uint8_t *const L = lab + mb.s;
+    for (uint32_t t = t0 + tid; t < t1; t += kThreads) {
+      const uint32_t q = t - t0;
+      L[t] = t < T ? static_cast<uint8_t>((cw[q >> 5] >> (q & 31u)) & 1u) : left;
+    }
+    __syncthreads();
+  }
+}
+
+// zeros among each chunk's final labels (one warp per chunk)
+__global__ void __launch_bounds__(kThreads) label_count_kernel(LevelArgs a, const uint8_t *lab,
+                                                               uint32_t *zl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kThreads / 32);
+  for (uint64_t cid = (static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+       cid < nchunks; cid += warps) {
+    const uint32_t r = static_cast<uint32_t>(cid / a.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(r) * a.J);
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t t0 = j * kChunk;
+    const uint32_t t1 = min(t0 + kChunk, N);
+    uint32_t z = 0;
+    for (uint32_t t = t0 + lane; t < t1; t += 32u) z += lab[mb.s + t] == 0u ? 1u : 0u;
+    z = warp_sum(z);
+    if (lane == 0) zl[cid] = z;
+  }
+}
+
+// exclusive prefix of the chunk zero counts along each merge's row (one warp per merge)
+__global__ void __launch_bounds__(kThreads) label_scan_kernel(LevelArgs a, uint32_t *zl) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (kThreads / 32);
+  for (uint64_t r = (static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5; r < a.M;
+       r += warps) {
+    uint32_t carry = 0;
+    for (uint32_t j0 = 0; j0 < a.J; j0 += 32u) {
+      const uint32_t j = j0 + lane;
+      const uint32_t v = j < a.J ? zl[r * a.J + j] : 0u;
+      const uint32_t incl = warp_inclusive_scan(v);
+      if (j < a.J) zl[r * a.J + j] = carry + incl - v;
+      carry += __shfl_sync(kFullMask, incl, 31);
+    }
+  }
+}
+
+// the data interleaved stably by the final words: a chunk's two source runs (its zeros from the
+// first half, its ones from the second) staged in shared memory, then one output a thread
+template <typename E>
+__global__ void __launch_bounds__(kStageThreads) word_gather_kernel(LevelArgs a, const uint8_t *lab,
+                                                                    const uint32_t *zl) {
+  constexpr uint32_t kV = 16u / sizeof(E) > 0 ? 16u / sizeof(E) : 1u;
+  constexpr uint32_t kBuf = kChunk + 4u * kV + 8u;
+  extern __shared__ __align__(16) unsigned char wg_raw[];
+  E *const sbuf = reinterpret_cast<E *>(wg_raw);
+  __shared__ uint32_t cw[kChunk / 32u];
+  __shared__ uint32_t zw[kChunk / 32u];
+  __shared__ uint32_t scratch[33];
+  const E *__restrict__ in = static_cast<const E *>(a.in);
+  E *__restrict__ out = static_cast<E *>(a.out);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
+  for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
+    const uint32_t r = static_cast<uint32_t>(cid / a.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(r) * a.J);
+    const MergeBounds mb = merge_bounds(a, r);
+    const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
+    const uint32_t t0 = j * kChunk;
+    if (t0 >= N) continue;  // uniform across the CTA
+    const uint32_t len = min(t0 + kChunk, N) - t0;
+    const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
+    const uint32_t n2 = N - n1;
+    // the chunk's words: bit = label (1: second half)
+    for (uint32_t k = warp; k < kChunk / 32u; k += kStageThreads / 32u) {
+      const uint32_t t = 32u * k + lane;
+      const bool one = t < len && lab[mb.s + t0 + t] != 0u;
+      const uint32_t m = __ballot_sync(kFullMask, one);
+      if (lane == 0) cw[k] = m;
+    }
+    __syncthreads();
+    uint32_t zc = 0;
+    {
+      // zeros before each word (one word a thread: kStageThreads = kChunk / 32), and the total
+      static_assert(kStageThreads == kChunk / 32u, "one label word per thread");
+      const uint32_t valid = 32u * tid >= len ? 0u : min(32u, len - 32u * tid);
+      const uint32_t zk = static_cast<uint32_t>(__popc(~cw[tid] & low_mask(valid)));
+      zw[tid] = block_exclusive_scan(zk, scratch, &zc);
+    }
+    const uint32_t Z0 = zl[cid];  // zeros before the chunk
+    // the runs: first half [Z0, Z0 + zc), second half [t0 - Z0, t0 - Z0 + len - zc)
+    const uint32_t za = min(Z0, n1), na = min(zc, n1 - za);
+    const uint32_t ob = min(t0 - Z0, n2), nb = min(len - zc, n2 - ob);
+    const E *const srcA = in + mb.s + za;
+    const E *const srcB = in + mb.mid + ob;
+    const uint32_t offA = static_cast<uint32_t>((reinterpret_cast<uintptr_t>(srcA) & 15u) / sizeof(E));
+    const uint32_t offB = ((offA + na + kV - 1u) / kV) * kV +
+                          static_cast<uint32_t>((reinterpret_cast<uintptr_t>(srcB) & 15u) / sizeof(E));
+    stage_run(sbuf + offA, srcA, min(na, kBuf - offA));
+    stage_run(sbuf + offB, srcB, min(nb, kBuf - min(offB, kBuf)));
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    E *const C = out + mb.s + t0;
+    for (uint32_t t = tid; t < len; t += kStageThreads) {
+      const uint32_t word = cw[t >> 5];
+      const uint32_t Z = zw[t >> 5] + static_cast<uint32_t>(__popc(~word & low_mask(t & 31u)));
+      const uint32_t src = ((word >> (t & 31u)) & 1u) ? offB + (t - Z) : offA + Z;
+      C[t] = sbuf[min(src, kBuf - 1u)];
+    }
+    __syncthreads();  // the buffers are reused by the next chunk
+  }
+}
+
 // ---------------------------------------------------------- staged fused pair (w = 4) ----
 // Two levels l, l+1 in one pass for 4-byte elements. A CTA takes 4096 outputs of level l+1;
 // they read one range of each of its halves (merges 2R and 2R+1 of level l), and each range is
@@ -1567,6 +1717,26 @@ cudaError_t launch_data_t(const Plan &p, const LevelPlan &lv, const void *in, vo
                           const Buffers &b, uint64_t seed, cudaStream_t s) {
   const LevelArgs a = level_args(p, lv, in, out, b, seed);
   const uint64_t nchunks = static_cast<uint64_t>(lv.M) * lv.J;
+  if (p.flags & MS_FLAG_BALANCED) {
+    // the labels, their insertions (on the label bytes), their chunk prefix, then the data
+    LevelArgs la = level_args(p, lv, nullptr, b.labels, b, seed);
+    label_kernel<<<grid_for(nchunks, 1, 1u << 20), kThreads, 0, s>>>(la, b.labels);
+    tail_sequential_kernel<uint8_t><<<grid_for(lv.M, kThreads, 1u << 16), kThreads, 0, s>>>(la);
+    patch_read_kernel<uint8_t><<<kResident, kThreads, 0, s>>>(la);
+    patch_write_kernel<uint8_t><<<kResident, kThreads, 0, s>>>(la);
+    label_count_kernel<<<grid_for(nchunks, kThreads / 32, 1u << 20), kThreads, 0, s>>>(
+        la, b.labels, b.zlab);
+    label_scan_kernel<<<grid_for(lv.M, kThreads / 32, 1u << 16), kThreads, 0, s>>>(la, b.zlab);
+    constexpr uint32_t kV = 16u / sizeof(E);
+    const size_t smem = (kChunk + 4u * kV + 8u) * sizeof(E);
+    auto wk = word_gather_kernel<E>;
+    cudaError_t e = allow_dynamic_smem(wk, smem);
+    if (e != cudaSuccess) return e;
+    timed(p.prof, kKindGather, s, [&] {
+      wk<<<grid_for(nchunks, 1, 1u << 20), kStageThreads, smem, s>>>(a, b.labels, b.zlab);
+    });
+    return cudaGetLastError();
+  }
   timed(p.prof, kKindGather, s, [&] {
     if constexpr (sizeof(E) <= 8)
       gather_staged_kernel<E><<<grid_for(nchunks, 1, 1u << 20), kStageThreads, 0, s>>>(a);

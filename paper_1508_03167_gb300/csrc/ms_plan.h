@@ -121,6 +121,9 @@ struct Plan {
   // literal merge (MS_FLAG_LITERAL): per merge, the first step of each lap of the first half's
   // rotating queue and the zero coins before it (uint2), lcap entries a merge (same copies)
   size_t off_laps = 0;
+  // balanced-word merge (MS_FLAG_BALANCED): one label byte per element and the chunk zero counts
+  // of the labels (same copies)
+  size_t off_labels = 0, off_zlab = 0;
   uint32_t units = 0;         // global-level units: single levels and fused pairs
   uint32_t hbm_passes = 0;    // data passes after the base-block pass
   uint32_t zc_cap = 0, minfo_cap = 0, kcap_max = 0, hbits_max = 0;
@@ -149,6 +152,8 @@ struct Buffers {
   void *ptmp;
   uint32_t *ostart;  // first merge of every 1024 tail steps of a level (kscan), + one sentinel
   uint2 *laps;       // literal merge: lap table (see Plan::off_laps)
+  uint8_t *labels;   // balanced-word merge: label bytes of a level
+  uint32_t *zlab;    // balanced-word merge: zeros before each chunk of labels
 };
 
 // Lets `kern` launch with `smem` bytes of dynamic shared memory. The attribute is process-wide,
