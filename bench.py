@@ -64,8 +64,16 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="scale workload only: skip the batched, batched-large and serving "
                          "sub-objects of the default line")
-    ap.add_argument("--workload", choices=["scale", "batched", "batched-large", "serve"],
-                    default="scale")
+    ap.add_argument("--workload", choices=["scale", "batched", "batched-large", "serve", "rs",
+                                           "variants"],
+                    default="scale",
+                    help="rs: the Rao-Sandelius perm alone; variants: the literal, FDR and "
+                         "balanced-word perms and the Table 1 bit counts alone")
+    ap.add_argument("--flags-perm", type=lambda x: int(x, 0), default=0,
+                    help="MS_FLAG_* bits added to the perm's resolved flags (e.g. 0x100: fused "
+                         "pairs of 4-byte levels)")
+    ap.add_argument("--flags-rec", type=lambda x: int(x, 0), default=0,
+                    help="MS_FLAG_* bits added to the records' resolved flags")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: perm 2^26 + 2^24+17 records (inputs still above L2)")
     return ap.parse_args()
@@ -215,6 +223,8 @@ def run_ours(args, world, rank, local):
     fd_rec = args.fuse_depth if args.fuse_depth_rec is None else args.fuse_depth_rec
     p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=fd_perm, tile_bytes=args.tile_bytes)
     p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=fd_rec, tile_bytes=args.tile_bytes)
+    p_perm.flags |= args.flags_perm
+    p_rec.flags |= args.flags_rec
     prof_perm = ms.params(p_perm.B, p_perm.fuse_depth, p_perm.flags | ms.MS_FLAG_PROFILE,
                           p_perm.tile_bytes)
     prof_rec = ms.params(p_rec.B, p_rec.fuse_depth, p_rec.flags | ms.MS_FLAG_PROFILE,
@@ -908,6 +918,10 @@ def main():
         print(json.dumps(run_batched(args, large=True)), flush=True)
     elif args.workload == "serve":
         print(json.dumps(run_serve(args)), flush=True)
+    elif args.workload == "rs":
+        print(json.dumps(run_rs(args)), flush=True)
+    elif args.workload == "variants":
+        print(json.dumps(run_literal_fdr(args)), flush=True)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -1052,9 +1052,19 @@ __device__ uint32_t zeros_before(const LevelArgs &a, uint32_t r, uint32_t x) {
   const uint64_t cid = static_cast<uint64_t>(r) * a.J + chunk;
   uint32_t Z = a.zc[cid];
   const uint32_t rel = min(x - chunk * kChunk, kChunk);
-  const uint32_t nb = rel >> 7;  // whole 128-step blocks before x
-  const uint8_t *zb = a.zb + cid * 32u;
-  for (uint32_t b = 0; b < nb; ++b) Z += zb[b];
+  const uint32_t nb = rel >> 7;  // whole 128-step blocks before x (their counts: 32 bytes read
+                                 // as two vectors, the first nb bytes summed)
+  {
+    const uint4 *zb4 = reinterpret_cast<const uint4 *>(a.zb + cid * 32u);
+    const uint4 lo = zb4[0], hi = zb4[1];
+    const uint32_t w8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) {
+      const uint32_t keep = nb >= 4u * k + 4u ? 4u : (nb > 4u * k ? nb - 4u * k : 0u);
+      const uint32_t m = keep >= 4u ? 0xFFFFFFFFu : ((1u << (8u * keep)) - 1u);
+      Z += __vsadu4(w8[k] & m, 0u);  // sum of the kept bytes
+    }
+  }
   const uint32_t q = rel & 127u;
   if (q != 0u && nb < 32u) {
     const uint4 c = coin_block(a.key, a.level, r, chunk * 32u + nb);
@@ -1286,12 +1296,28 @@ __global__ void __launch_bounds__(kStageThreads) word_gather_kernel(LevelArgs a,
     const uint32_t len = min(t0 + kChunk, N) - t0;
     const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
     const uint32_t n2 = N - n1;
-    // the chunk's words: bit = label (1: second half)
-    for (uint32_t k = warp; k < kChunk / 32u; k += kStageThreads / 32u) {
-      const uint32_t t = 32u * k + lane;
-      const bool one = t < len && lab[mb.s + t0 + t] != 0u;
-      const uint32_t m = __ballot_sync(kFullMask, one);
-      if (lane == 0) cw[k] = m;
+    // the chunk's words: bit = label (1: second half). Thread k builds word k from its 32 label
+    // bytes (eight 4-byte loads when the row is 4-byte aligned, all issued before use)
+    {
+      const uint8_t *const Lr = lab + mb.s + t0;
+      const uint32_t t = 32u * tid;
+      uint32_t m = 0;
+      if ((reinterpret_cast<uintptr_t>(Lr) & 3u) == 0u && t + 32u <= len) {
+        uint32_t v[8];
+#pragma unroll
+        for (uint32_t u = 0; u < 8u; ++u) v[u] = reinterpret_cast<const uint32_t *>(Lr + t)[u];
+#pragma unroll
+        for (uint32_t u = 0; u < 8u; ++u) {
+          // label bytes are 0 or 1: gather bit 0 of each of the four bytes
+          const uint32_t x = v[u];
+          const uint32_t b4 = (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
+          m |= b4 << (4u * u);
+        }
+      } else {
+        for (uint32_t i = 0; i < 32u; ++i)
+          if (t + i < len && Lr[t + i] != 0u) m |= 1u << i;
+      }
+      cw[tid] = m;
     }
     __syncthreads();
     uint32_t zc = 0;
