@@ -306,10 +306,10 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
 
   // consecutive global levels fuse in pairs (one data pass for two levels)
   uint32_t nlocal = 0, units = 0;
-  uint32_t xhbits_max = 0;
+  uint32_t xcap_max = 0;
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     p.levels[i].pair = 0;
-    p.levels[i].xhbits = 0;
+    p.levels[i].xcap = 0;
   }
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     LevelPlan &lv = p.levels[i];
@@ -326,10 +326,8 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     if (want_pairs && i + 1 < p.nlevels && !p.levels[i + 1].local) {
       lv.pair = 1;
       p.levels[i + 1].pair = 2;
-      uint32_t xb = 10;
-      while ((1ull << xb) < 4ull * lv.kcap) ++xb;
-      lv.xhbits = xb;
-      xhbits_max = std::max(xhbits_max, xb);
+      lv.xcap = 2u * lv.kcap;
+      xcap_max = std::max(xcap_max, lv.xcap);
     }
   }
   // The tile kernel of a shuffle reads its input rows after computing their order, so its
@@ -351,19 +349,17 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
     }
     if (last >= 0) {
       p.levels[last].pair = 0;
-      p.levels[last].xhbits = 0;
+      p.levels[last].xcap = 0;
       p.levels[last + 1].pair = 0;
       ++units;
-      xhbits_max = 0;
-      for (uint32_t i = 0; i < p.nlevels; ++i) xhbits_max = std::max(xhbits_max, p.levels[i].xhbits);
+      xcap_max = 0;
+      for (uint32_t i = 0; i < p.nlevels; ++i) xcap_max = std::max(xcap_max, p.levels[i].xcap);
     } else if (top >= 0) {
       LevelPlan &lv = p.levels[top];
       lv.pair = 1;
       p.levels[top + 1].pair = 2;
-      uint32_t xb = 10;
-      while ((1ull << xb) < 4ull * lv.kcap) ++xb;
-      lv.xhbits = xb;
-      xhbits_max = std::max(xhbits_max, xb);
+      lv.xcap = 2u * lv.kcap;
+      xcap_max = std::max(xcap_max, lv.xcap);
       --units;
     } else if (d > 0) {
       return make_plan(n, w, B, static_cast<int32_t>(d - 1), tile_bytes, flags, out);
@@ -371,7 +367,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
   }
   p.units = units;
   p.hbm_passes = nlocal + units;
-  const bool pairs = xhbits_max > 0;
+  const bool pairs = xcap_max > 0;
   const bool literal = (flags & MS_FLAG_LITERAL) != 0;
   const bool balanced = (flags & MS_FLAG_BALANCED) != 0;
   uint32_t lcap_max = 0;
@@ -407,9 +403,14 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       const size_t ebase = off;
       p.off_zb = off - ebase;     off += round_up(zc_cap * 32ull, 256);
       if (pairs) {
+        const uint64_t xblocks = (n + kXBlock - 1) / kXBlock;
         p.off_xbits = off - ebase;  off += round_up((n + 31) / 32 * 4, 256);
-        p.off_xkeys = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
-        p.off_xvals = off - ebase;  off += round_up((1ull << xhbits_max) * 4, 256);
+        p.off_xsrc = off - ebase;   off += round_up(static_cast<size_t>(xcap_max) * 4, 256);
+        p.off_xval = off - ebase;   off += round_up(static_cast<size_t>(xcap_max) * 4, 256);
+        p.off_xbpre = off - ebase;  off += round_up(xblocks * 4, 256);
+        p.off_xtpre = off - ebase;
+        off += round_up((xblocks + kXTileBlocks - 1) / kXTileBlocks * 4, 256);
+        p.off_xrange = off - ebase; off += round_up(zc_cap * 128ull, 256);  // 2 x 16 words a chunk
       }
       if (literal) {
         p.off_laps = off - ebase;   off += round_up(static_cast<size_t>(lcap_max) * 8u, 256);
@@ -533,8 +534,11 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   char *es = base + p.exc_base + static_cast<size_t>(set / 2) * p.exc_bytes;  // unit's copy
   b.zb = reinterpret_cast<uint8_t *>(es + p.off_zb);
   b.xbits = reinterpret_cast<uint32_t *>(es + p.off_xbits);
-  b.xkeys = reinterpret_cast<uint32_t *>(es + p.off_xkeys);
-  b.xvals = reinterpret_cast<uint32_t *>(es + p.off_xvals);
+  b.xsrc = reinterpret_cast<uint32_t *>(es + p.off_xsrc);
+  b.xval = reinterpret_cast<uint32_t *>(es + p.off_xval);
+  b.xbpre = reinterpret_cast<uint32_t *>(es + p.off_xbpre);
+  b.xtpre = reinterpret_cast<uint32_t *>(es + p.off_xtpre);
+  b.xrange = reinterpret_cast<uint4 *>(es + p.off_xrange);
   b.laps = reinterpret_cast<uint2 *>(es + p.off_laps);
   b.labels = reinterpret_cast<uint8_t *>(es + p.off_labels);
   b.zlab = reinterpret_cast<uint32_t *>(es + p.off_zlab);

@@ -692,23 +692,82 @@ __global__ void __launch_bounds__(kStageThreads) gather_staged_kernel(LevelArgs 
   }
 }
 
+// zeros among the coins of steps [0, x) of merge r, x <= N (zb and the scanned zc)
+__device__ uint32_t zeros_before(const LevelArgs &a, uint32_t r, uint32_t x) {
+  uint32_t chunk = x / kChunk;
+  if (chunk >= a.J) chunk = a.J - 1u;  // x = N on a chunk boundary: the whole last chunk
+  const uint64_t cid = static_cast<uint64_t>(r) * a.J + chunk;
+  uint32_t Z = a.zc[cid];
+  const uint32_t rel = min(x - chunk * kChunk, kChunk);
+  const uint32_t nb = rel >> 7;  // whole 128-step blocks before x (their counts: 32 bytes read
+                                 // as two vectors, the first nb bytes summed)
+  {
+    const uint4 *zb4 = reinterpret_cast<const uint4 *>(a.zb + cid * 32u);
+    const uint4 lo = zb4[0], hi = zb4[1];
+    const uint32_t w8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 8u; ++k) {
+      const uint32_t keep = nb >= 4u * k + 4u ? 4u : (nb > 4u * k ? nb - 4u * k : 0u);
+      const uint32_t m = keep >= 4u ? 0xFFFFFFFFu : ((1u << (8u * keep)) - 1u);
+      Z += __vsadu4(w8[k] & m, 0u);  // sum of the kept bytes
+    }
+  }
+  const uint32_t q = rel & 127u;
+  if (q != 0u && nb < 32u) {
+    const uint4 c = coin_block(a.key, a.level, r, chunk * 32u + nb);
+    const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (uint32_t k = 0; k < 4u; ++k) {
+      const uint32_t lo = 32u * k;
+      if (q > lo) Z += __popc(~w4[k] & low_mask(min(q - lo, 32u)));
+    }
+  }
+  return Z;
+}
+
 // ---------------------------------------------------------------------------- fused pairs --
 // Two consecutive levels l, l+1 in one data pass. Level l's output (never written) is the
 // stable interleave of its halves with the tail moves applied; a tail move is an exception:
-// output position q holds the interleave element of merge position F(q) != q. The plan stores,
-// for every exception, the input index that element comes from (a bitmap marks the exception
-// positions, an open-addressing hash maps position -> input index). The data pass then gathers
-// level l+1's interleave straight from level l's input.
+// output position q holds the interleave element of merge position F(q) != q. The plan lists,
+// for every exception in position order, the input index that element comes from: a bitmap
+// marks the exception positions, and the rank of an exception (exceptions at lower positions)
+// is its index in the list. Ranks come from a two-level prefix of the bitmap's bit counts
+// (per 1024 positions within their tile of 2^20 positions, and per tile), so a data chunk finds
+// its range's exceptions as one contiguous slice of the list. The data pass then gathers level
+// l+1's interleave straight from level l's input.
 
 struct ExcArgs {
-  uint32_t *bits;   // one bit per element of level l's output
-  uint32_t *keys;   // hash keys (output position), ~0 = empty
-  uint32_t *vals;   // input index of the element at that position
-  uint32_t hbits;
+  uint32_t *bits;  // one bit per element of level l's output
+  uint32_t *src;   // input index of each tail patch's element (by patch)
+  uint32_t *val;   // input index of each exception's element (by rank)
+  uint32_t *bpre;  // exceptions before each block of kXBlock positions, within its tile
+  uint32_t *tpre;  // exceptions before each tile of kXTileBlocks blocks
+  uint64_t n;
 };
 
-__device__ __forceinline__ uint32_t xhash_slot(uint32_t key, uint32_t hbits) {
-  return (key * 0x9E3779B1u) >> (32u - hbits);
+// Exceptions at positions below q (q < n): the block and tile prefixes plus the bits of q's
+// block before it. The block's 32 bitmap words arrive as eight 16-byte loads.
+__device__ __forceinline__ uint32_t exception_rank(const ExcArgs &x, uint32_t q) {
+  const uint32_t b = q / kXBlock;
+  uint32_t rank = x.tpre[b / kXTileBlocks] + x.bpre[b];
+  const uint4 *const w4 = reinterpret_cast<const uint4 *>(x.bits + static_cast<uint64_t>(b) * 32u);
+  const uint64_t nwords = (x.n + 31u) >> 5;
+  const uint32_t wq = (q >> 5) & 31u;  // q's word within the block
+  uint4 v[8];
+#pragma unroll
+  for (uint32_t k = 0; k < 8u; ++k)
+    v[k] = (static_cast<uint64_t>(b) * 32u + 4u * k < nwords) ? w4[k] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (uint32_t k = 0; k < 8u; ++k) {
+    const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+    for (uint32_t e = 0; e < 4u; ++e) {
+      const uint32_t wi = 4u * k + e;
+      const uint32_t m = wi < wq ? 0xFFFFFFFFu : (wi == wq ? low_mask(q & 31u) : 0u);
+      rank += static_cast<uint32_t>(__popc(w[e] & m));
+    }
+  }
+  return rank;
 }
 
 // Input index (into level l's input) of the interleave element at merge position p of merge r.
@@ -748,24 +807,83 @@ __device__ uint32_t interleave_source(const LevelArgs &a, uint32_t r, uint32_t p
 __global__ void __launch_bounds__(kThreads) exceptions_kernel(LevelArgs a, ExcArgs x) {
   if (a.ctrl[1]) return;  // the unfused fallback runs instead
   const uint32_t K = a.ctrl[0];
-  const uint32_t hmask = (1u << x.hbits) - 1u;
   for (uint32_t g = blockIdx.x * kThreads + threadIdx.x; g < 2u * K; g += gridDim.x * kThreads) {
     const uint32_t pi = g < K ? g : a.kcap + (g - K);
     const uint32_t dst = a.pdst[pi];
     if (dst == kNone || dst >= a.n) continue;
     const uint32_t r = owner_merge(a, g < K ? g : g - K);
     const uint32_t s = static_cast<uint32_t>(merge_bounds(a, r).s);
-    const uint32_t xs = interleave_source(a, r, a.psrc[pi] - s);
+    x.src[g] = interleave_source(a, r, a.psrc[pi] - s);
     atomicOr(&x.bits[dst >> 5], 1u << (dst & 31u));
-    uint32_t h = xhash_slot(dst, x.hbits);
-    for (uint32_t probe = 0; probe <= hmask; ++probe) {
-      const uint32_t old = atomicCAS(&x.keys[h], 0xFFFFFFFFu, dst);
-      if (old == 0xFFFFFFFFu) {
-        x.vals[h] = xs;
-        break;
-      }
-      h = (h + 1u) & hmask;
-    }
+  }
+}
+
+// Rank index, first level: CTA t counts the exceptions of the kXTileBlocks blocks of tile t
+// (a warp a block: one bitmap word a lane), then writes each block's prefix within the tile
+// and the tile's total.
+__global__ void __launch_bounds__(kThreads) xcount_kernel(LevelArgs a, ExcArgs x) {
+  __shared__ uint32_t cnt[kXTileBlocks];
+  __shared__ uint32_t scratch[33];
+  if (a.ctrl[1]) return;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint64_t nwords = (x.n + 31u) >> 5;
+  const uint64_t nblocks = (x.n + kXBlock - 1u) / kXBlock;
+  const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * kXTileBlocks;
+  for (uint32_t k = warp; k < kXTileBlocks; k += kThreads / 32u) {
+    const uint64_t wi = (b0 + k) * 32u + lane;
+    const uint32_t c = warp_sum(wi < nwords ? static_cast<uint32_t>(__popc(x.bits[wi])) : 0u);
+    if (lane == 0) cnt[k] = c;
+  }
+  __syncthreads();
+  constexpr uint32_t kPer = kXTileBlocks / kThreads;
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < kPer; ++i) {
+    v[i] = cnt[kPer * tid + i];
+    sum += v[i];
+  }
+  uint32_t total;
+  uint32_t ex = block_exclusive_scan(sum, scratch, &total);
+#pragma unroll
+  for (uint32_t i = 0; i < kPer; ++i) {
+    const uint64_t b = b0 + kPer * tid + i;
+    if (b < nblocks) x.bpre[b] = ex;
+    ex += v[i];
+  }
+  if (tid == 0) x.tpre[blockIdx.x] = total;
+}
+
+// Rank index, second level: exclusive prefix of the tile totals, in place (one CTA of 1024
+// threads, four tiles a thread: up to 2^32 positions).
+__global__ void __launch_bounds__(1024) xtiles_kernel(LevelArgs a, ExcArgs x) {
+  __shared__ uint32_t scratch[33];
+  if (a.ctrl[1]) return;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t ntiles = ((x.n + kXBlock - 1u) / kXBlock + kXTileBlocks - 1u) / kXTileBlocks;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < 4u; ++i) {
+    v[i] = (4u * tid + i < ntiles) ? x.tpre[4u * tid + i] : 0u;
+    sum += v[i];
+  }
+  uint32_t total;
+  uint32_t ex = block_exclusive_scan(sum, scratch, &total);
+#pragma unroll
+  for (uint32_t i = 0; i < 4u; ++i) {
+    if (4u * tid + i < ntiles) x.tpre[4u * tid + i] = ex;
+    ex += v[i];
+  }
+}
+
+// Every exception's input index into the list at its rank.
+__global__ void __launch_bounds__(kThreads) xscatter_kernel(LevelArgs a, ExcArgs x) {
+  if (a.ctrl[1]) return;
+  const uint32_t K = a.ctrl[0];
+  for (uint32_t g = blockIdx.x * kThreads + threadIdx.x; g < 2u * K; g += gridDim.x * kThreads) {
+    const uint32_t pi = g < K ? g : a.kcap + (g - K);
+    const uint32_t dst = a.pdst[pi];
+    if (dst == kNone || dst >= a.n) continue;
+    x.val[exception_rank(x, dst)] = x.src[g];
   }
 }
 
@@ -774,22 +892,203 @@ struct PairArgs {
   void *out;
   LevelArgs l1, l2;  // the two levels' plans (l1.J, zc, zb, minfo; l2.M, J, zc, minfo)
   ExcArgs x;
+  uint4 *xr;  // per chunk of level l+1: the ranges its halves read (pair_ranges_kernel)
 };
+
+// Exceptions at positions below q, q <= n.
+__device__ __forceinline__ uint32_t exception_rank_end(const ExcArgs &x, uint64_t q) {
+  if (q < x.n) return exception_rank(x, static_cast<uint32_t>(q));
+  const uint32_t last = static_cast<uint32_t>(x.n - 1u);
+  return exception_rank(x, last) + ((x.bits[last >> 5] >> (last & 31u)) & 1u);
+}
+
+// What one half h of a level-(l+1) chunk reads of merge 2R+h of level l, in 16 words (four
+// uint4 of the chunk's record, half 0 first):
+constexpr uint32_t kRgLo = 0;     // range start (merge position) and
+constexpr uint32_t kRgCnt = 1;    //   length
+constexpr uint32_t kRgTc = 2;     // range-relative break step of level l (0 past it)
+constexpr uint32_t kRgZT = 3;     // zeros of level l's coins in [lo, lo + Tc)
+constexpr uint32_t kRgAbit = 4;   // 1: level l's first half ran out at its break step
+constexpr uint32_t kRgBlo = 5;    // first 128-step block of level l's coins the range uses
+constexpr uint32_t kRgRunA = 6;   // input index and length of the first half's run,
+constexpr uint32_t kRgNa = 7;
+constexpr uint32_t kRgRunB = 8;   //   and of the second half's run
+constexpr uint32_t kRgNb = 9;
+constexpr uint32_t kRgGlo = 10;   // global position of the range start
+constexpr uint32_t kRgZlo = 11;   // zeros before lo
+constexpr uint32_t kRgXbase = 12; // rank of the range's first exception and
+constexpr uint32_t kRgXcnt = 13;  //   the range's exception count
+constexpr uint32_t kRgZblk = 14;  // zeros before block blo
+constexpr uint32_t kRgMerge = 15; // 2R + h
+constexpr uint32_t kRgWords = 16;
+
+// The ranges of every chunk of level l+1, on the plan stream once both levels are planned: a
+// thread per chunk and half. Level l+1's chunk [t0, t1) takes positions [lo0, lo0 + cnt0) of
+// merge 2R and [lo1, lo1 + cnt1) of merge 2R+1 (its zero coins before t0 and in the chunk); each
+// range is the interleave of one run of each half of its merge (up to level l's break step),
+// then that merge's leftover.
+__global__ void __launch_bounds__(kThreads) pair_ranges_kernel(PairArgs pa) {
+  const LevelArgs &a1 = pa.l1;
+  const LevelArgs &a2 = pa.l2;
+  if (a1.ctrl[1]) return;  // level l's tails overflowed: the unfused fallback runs instead
+  const uint64_t nchunks = static_cast<uint64_t>(a2.M) * a2.J;
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * kThreads + threadIdx.x; g < 2u * nchunks;
+       g += static_cast<uint64_t>(gridDim.x) * kThreads) {
+    const uint64_t cid = g >> 1;
+    const uint32_t h = static_cast<uint32_t>(g & 1u);
+    const uint32_t R = static_cast<uint32_t>(cid / a2.J);
+    const uint32_t j = static_cast<uint32_t>(cid - static_cast<uint64_t>(R) * a2.J);
+    uint32_t rg[kRgWords] = {};
+    const MergeBounds mb2 = merge_bounds(a2, R);
+    const uint32_t N2 = static_cast<uint32_t>(mb2.e - mb2.s);
+    const uint32_t t0 = j * kChunk;
+    rg[kRgMerge] = 2u * R + h;
+    if (t0 < N2) {
+      const uint32_t t1 = min(t0 + kChunk, N2);
+      const uint32_t len = t1 - t0;
+      const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);
+      const uint32_t h2 = N2 - h1;
+      const uint4 mi2 = a2.minfo[R];
+      const uint32_t T2 = mi2.x;
+      const uint32_t abit2 = (mi2.y == h1) ? 1u : 0u;
+      uint32_t Tc2, zT2, lo;
+      if (t0 >= T2) {
+        Tc2 = 0;
+        zT2 = 0;
+        lo = h ? (abit2 ? t0 - h1 : 0u) : (abit2 ? 0u : t0 - h2);
+      } else {
+        const uint32_t Z0 = a2.zc[cid];
+        Tc2 = min(t1, T2) - t0;
+        const uint32_t Jr = (N2 + kChunk - 1u) / kChunk;
+        zT2 = (t1 <= T2) ? ((j + 1u < Jr) ? a2.zc[cid + 1] - Z0 : h1 - Z0) : mi2.y - Z0;
+        lo = h ? t0 - Z0 : Z0;
+      }
+      const uint32_t cnt =
+          h ? min((Tc2 - zT2) + (abit2 ? len - Tc2 : 0u), h2 - min(lo, h2))
+            : min(zT2 + (abit2 ? 0u : len - Tc2), h1 - min(lo, h1));
+      const uint32_t r1 = 2u * R + h;
+      const MergeBounds mb1 = merge_bounds(a1, r1);
+      const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
+      const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
+      const uint32_t n12 = N1 - n11;
+      const uint4 mi1 = a1.minfo[r1];
+      const uint32_t T1 = mi1.x;
+      const uint32_t abit1 = (mi1.y == n11) ? 1u : 0u;
+      const uint32_t qe = min(lo + cnt, T1);  // [lo, qe): interleave positions
+      uint32_t Tc1 = 0, zT1 = 0, Zlo = 0, za, na, ob, nb;
+      if (lo >= T1) {
+        za = abit1 ? 0u : lo - n12;
+        ob = abit1 ? lo - n11 : 0u;
+        na = abit1 ? 0u : cnt;
+        nb = abit1 ? cnt : 0u;
+      } else {
+        Zlo = zeros_before(a1, r1, lo);
+        const uint32_t Zqe = (qe == T1) ? mi1.y : zeros_before(a1, r1, qe);
+        Tc1 = qe - lo;
+        zT1 = Zqe - Zlo;
+        const uint32_t rest = lo + cnt - qe;
+        za = Zlo;
+        ob = lo - Zlo;
+        na = zT1 + (abit1 ? 0u : rest);
+        nb = (Tc1 - zT1) + (abit1 ? rest : 0u);
+      }
+      // (the runs stay inside their halves even for an inconsistent plan)
+      za = min(za, n11);
+      na = min(na, n11 - za);
+      ob = min(ob, n12);
+      nb = min(nb, n12 - ob);
+      const uint32_t blo = lo >> 7;
+      const uint32_t g_lo = static_cast<uint32_t>(mb1.s) + lo;
+      rg[kRgLo] = lo;
+      rg[kRgCnt] = cnt;
+      rg[kRgTc] = Tc1;
+      rg[kRgZT] = zT1;
+      rg[kRgAbit] = abit1;
+      rg[kRgBlo] = blo;
+      rg[kRgRunA] = static_cast<uint32_t>(mb1.s) + za;
+      rg[kRgNa] = na;
+      rg[kRgRunB] = static_cast<uint32_t>(mb1.mid) + ob;
+      rg[kRgNb] = nb;
+      rg[kRgGlo] = g_lo;
+      rg[kRgZlo] = Zlo;
+      rg[kRgZblk] = Tc1 ? zeros_before(a1, r1, 128u * blo) : 0u;
+      if (cnt) {
+        rg[kRgXbase] = exception_rank(pa.x, g_lo);
+        rg[kRgXcnt] = exception_rank_end(pa.x, static_cast<uint64_t>(g_lo) + cnt) - rg[kRgXbase];
+      }
+    }
+    uint4 *const o = pa.xr + g * 4u;
+#pragma unroll
+    for (uint32_t k = 0; k < 4u; ++k)
+      o[k] = make_uint4(rg[4u * k], rg[4u * k + 1u], rg[4u * k + 2u], rg[4u * k + 3u]);
+  }
+}
 
 // half h of level l+1's merge R is merge 2R+h of level l; its used position range in the chunk
 // is [lo, lo+cnt); the coin words of level l covering it start at block blo.
 constexpr uint32_t kPairW = 136;  // words per half: <= 4096 positions + block alignment
 
+// The bitmap words of global positions [g_lo, g_lo + cnt) into xb (word 0: word g_lo / 32),
+// bits outside the range cleared; thread t of nt loads words t, t + nt, ...
+__device__ __forceinline__ void load_range_bits(const ExcArgs &x, uint32_t g_lo, uint32_t cnt,
+                                                uint32_t *xb, uint32_t t, uint32_t nt) {
+  const uint64_t nwords = (x.n + 31u) >> 5;
+  const uint32_t w0 = g_lo >> 5;
+  const uint32_t nw = cnt ? ((g_lo + cnt + 31u) >> 5) - w0 : 0u;
+  for (uint32_t wi = t; wi < nw && wi < kPairW; wi += nt) {
+    const uint64_t bw = static_cast<uint64_t>(w0) + wi;
+    uint32_t v = bw < nwords ? x.bits[bw] : 0u;
+    const uint32_t ws = (w0 + wi) << 5;  // first position of the word
+    const uint32_t lo_b = g_lo > ws ? g_lo - ws : 0u;
+    const uint32_t hi_b = min(g_lo + cnt - ws, 32u);
+    xb[wi] = v & low_mask(hi_b) & ~low_mask(lo_b);
+  }
+}
+
+// Exclusive prefix of the bit counts of the nw range words xb into xwp, by one full warp (five
+// words a lane); the exception of rank k in the range then sits in the last word whose prefix is
+// at most k.
+__device__ __forceinline__ void range_word_prefix(const uint32_t *xb, uint32_t nw, uint32_t *xwp) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t c5[5], cs = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 5u; ++k) {
+    const uint32_t wi = 5u * lane + k;
+    c5[k] = wi < nw && wi < kPairW ? static_cast<uint32_t>(__popc(xb[wi])) : 0u;
+    cs += c5[k];
+  }
+  uint32_t ex = warp_inclusive_scan(cs) - cs;
+#pragma unroll
+  for (uint32_t k = 0; k < 5u; ++k) {
+    const uint32_t wi = 5u * lane + k;
+    if (wi < kPairW) xwp[wi] = ex;
+    ex += c5[k];
+  }
+}
+
+__device__ __forceinline__ uint32_t range_words(uint32_t g_lo, uint32_t cnt) {
+  return cnt ? min(((g_lo + cnt + 31u) >> 5) - (g_lo >> 5), kPairW) : 0u;
+}
+
+// The data pass of a fused pair for 8- and 16-byte elements: a CTA takes 4096 outputs of level
+// l+1 and reads every element straight from level l's input (coalesced within each of the four
+// runs). Per chunk: level l+1's coins and zero prefix; the record of the two level-l ranges
+// (pair_ranges_kernel); level l's coins over each range, the range's exception bits and its
+// slice of the exception list; then each output's source through both levels.
 template <typename E>
-__global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
+__global__ void __launch_bounds__(kThreads, 5) pair_gather_kernel(PairArgs pa) {
   __shared__ uint32_t cw2[kChunk / 32u];
   __shared__ uint32_t zw2[kChunk / 32u];
   __shared__ uint32_t cw1[2][kPairW];
   __shared__ uint32_t zw1[2][kPairW];
   __shared__ uint32_t xb1[2][kPairW];  // exception bits of each half's range (word-aligned)
-  __shared__ uint32_t xval[2][kChunk];  // input index of each exception, by position in range
+  __shared__ uint32_t xwp[2][kPairW];  // exceptions of the range before each word
+  __shared__ uint32_t xval[2][kChunk];   // input index of each exception, by position in range
   __shared__ uint32_t scratch[33];
-  __shared__ uint32_t hs[2][12];
+  // per half: the chunk's record (kRgWords), then s1, n11, T1, the leftover shift, N1, nblk
+  constexpr uint32_t kS1 = kRgWords, kN11 = kRgWords + 1u, kT1 = kRgWords + 2u,
+                     kShift = kRgWords + 3u, kN1 = kRgWords + 4u, kNblk = kRgWords + 5u;
+  __shared__ uint32_t hs[2][kRgWords + 6u];
   const LevelArgs &a1 = pa.l1;
   const LevelArgs &a2 = pa.l2;
   if (a1.ctrl[1]) return;  // level l's tails overflowed: the unfused fallback runs instead
@@ -814,105 +1113,82 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
     const bool first_exh2 = (mi2.y == h1);
     const uint32_t Z0 = a2.zc[cid];
     const uint32_t tA = min(t1, T2);  // [t0, tA): interleave part of the chunk
-    if (tid < kChunk / 128u) {
-      const uint4 c = coin_block(a2.key, a2.level, R, j * (kChunk / 128u) + tid);
-      cw2[4u * tid + 0u] = c.x;
-      cw2[4u * tid + 1u] = c.y;
-      cw2[4u * tid + 2u] = c.z;
-      cw2[4u * tid + 3u] = c.w;
-    }
-    __syncthreads();
-    uint32_t zA;  // zeros in [t0, tA)
-    {
-      uint32_t z = 0;
-      if (tid < kChunk / 32u) {
-        const uint32_t tw = t0 + 32u * tid;
+    if (warp == 0u) {
+      // level l+1's coins of the chunk and the zeros before each word (interleave part)
+      const uint4 c = coin_block(a2.key, a2.level, R, j * (kChunk / 128u) + lane);
+      const uint32_t c4[4] = {c.x, c.y, c.z, c.w};
+      uint32_t z4[4], zs = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        cw2[4u * lane + k] = c4[k];
+        const uint32_t tw = t0 + 32u * (4u * lane + k);
         const uint32_t valid = tw >= tA ? 0u : min(32u, tA - tw);
-        z = __popc(~cw2[tid] & low_mask(valid));
+        z4[k] = static_cast<uint32_t>(__popc(~c4[k] & low_mask(valid)));
+        zs += z4[k];
       }
-      const uint32_t excl = block_exclusive_scan(z, scratch, &zA);
-      if (tid < kChunk / 32u) zw2[tid] = excl;
-    }
-    // ranges of the two halves (merges 2R and 2R+1 of level l) this chunk reads
-    if (tid < 2u) {
-      const uint32_t h = tid;
-      const uint32_t ni = tA > t0 ? tA - t0 : 0u;  // interleave outputs
-      const uint32_t nl = t1 > max(t0, T2) ? t1 - max(t0, T2) : 0u;  // leftover outputs
-      uint32_t lo, cnt;
-      if (h == 0) {
-        lo = t0 < T2 ? Z0 : t0 - h2;
-        cnt = zA + (first_exh2 ? 0u : nl);
-      } else {
-        lo = t0 < T2 ? t0 - Z0 : t0 - h1;
-        cnt = (ni - zA) + (first_exh2 ? nl : 0u);
+      uint32_t ex = warp_inclusive_scan(zs) - zs;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        zw2[4u * lane + k] = ex;
+        ex += z4[k];
       }
-      const uint32_t r1 = 2u * R + h;
-      const MergeBounds mb1 = merge_bounds(a1, r1);
-      const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
-      const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
-      const uint4 mi1 = a1.minfo[r1];
-      const uint32_t T1 = mi1.x;
-      const uint32_t hi = min(lo + cnt, T1);  // positions needing coins: [lo, hi)
-      const uint32_t blo = lo >> 7;
-      const uint32_t nblk = hi > lo ? ((hi + 127u) >> 7) - blo : 0u;
-      hs[h][0] = r1;
-      hs[h][1] = static_cast<uint32_t>(mb1.s);
-      hs[h][2] = n11;
-      hs[h][3] = T1;
-      hs[h][4] = (mi1.y == n11) ? 0u : N1 - n11;  // leftover shift: first half exhausted -> 0
-      hs[h][5] = blo;
-      hs[h][6] = nblk;
-      hs[h][8] = N1;
-      hs[h][9] = lo;
-      hs[h][10] = cnt;
+    } else if (warp == 1u) {
+      // the two ranges' records (lane: half lane / 16, word lane % 16) and their merges' shape
+      const uint32_t h = lane >> 4, w = lane & 15u;
+      hs[h][w] = reinterpret_cast<const uint32_t *>(pa.xr + (2u * cid + h) * 4u)[w];
+      if (w == 0u) {
+        const uint32_t r1 = 2u * R + h;
+        const MergeBounds mb1 = merge_bounds(a1, r1);
+        const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
+        const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
+        const uint4 mi1 = a1.minfo[r1];
+        hs[h][kS1] = static_cast<uint32_t>(mb1.s);
+        hs[h][kN11] = n11;
+        hs[h][kT1] = mi1.x;
+        hs[h][kShift] = (mi1.y == n11) ? 0u : N1 - n11;  // leftover shift: first half exhausted -> 0
+        hs[h][kN1] = N1;
+      }
     }
     __syncthreads();
-    // coin words of level l for both ranges (threads 0..127: half 0, 128..255: half 1), their
-    // zero counts, and the exception bits of the ranges
+    // level l's coin words over both ranges (threads 0..127: half 0, 128..255: half 1), the
+    // ranges' exception bits and their slices of the exception list
+    uint32_t xv0, xv1;
     {
       const uint32_t h = tid >> 7;
       const uint32_t k = tid & 127u;
-      const uint32_t nblk = hs[h][6];
-      const uint32_t blo = hs[h][5];
-      const uint32_t N1 = hs[h][8];
-      if (k < 32u) {
-        // zeros before block blo: the chunk prefix plus the blocks of the chunk before it
-        const uint32_t chunk = blo >> 5;
-        const uint32_t b = chunk * 32u + k;
-        const uint64_t row = static_cast<uint64_t>(hs[h][0]) * a1.J;
-        uint32_t zb = (nblk && b < blo) ? a1.zb[row * 32u + b] : 0u;
-        zb = warp_sum(zb);
-        if (k == 0) hs[h][7] = nblk ? a1.zc[row + chunk] + zb : 0u;
-      }
+      const uint32_t lo = hs[h][kRgLo], Tc = hs[h][kRgTc], blo = hs[h][kRgBlo];
+      const uint32_t nblk = Tc ? min(((lo + Tc + 127u) >> 7) - blo, kPairW / 4u) : 0u;
+      if (k == 0u) hs[h][kNblk] = nblk;
       if (k < nblk) {
-        const uint32_t blk = blo + k;
-        const uint4 c = coin_block(a1.key, a1.level, hs[h][0], blk);
+        const uint4 c = coin_block(a1.key, a1.level, hs[h][kRgMerge], blo + k);
         cw1[h][4u * k + 0u] = c.x;
         cw1[h][4u * k + 1u] = c.y;
         cw1[h][4u * k + 2u] = c.z;
         cw1[h][4u * k + 3u] = c.w;
       }
-      // exception bit words for global positions [s1 + lo, s1 + lo + cnt)
-      const uint32_t g_lo = hs[h][1] + hs[h][9];
-      const uint32_t nw = hs[h][10] ? ((g_lo + hs[h][10] + 31u) >> 5) - (g_lo >> 5) : 0u;
-      const uint64_t nbw = (a1.n + 31u) >> 5;  // words of the bitmap
-      for (uint32_t wi = k; wi < nw && wi < kPairW; wi += 128u) {
-        const uint64_t bw = (g_lo >> 5) + wi;
-        xb1[h][wi] = bw < nbw ? pa.x.bits[bw] : 0u;
-      }
-      (void)N1;
+      load_range_bits(pa.x, hs[h][kRgGlo], hs[h][kRgCnt], xb1[h], k, 128u);
+      // the range's first exceptions from the list (ranks k and k + 128), placed once their
+      // positions are known
+      const uint32_t xc = hs[h][kRgXcnt], xb = hs[h][kRgXbase];
+      xv0 = k < xc ? pa.x.val[xb + k] : 0u;
+      xv1 = k + 128u < xc ? pa.x.val[xb + k + 128u] : 0u;
     }
     __syncthreads();
+    // the exception prefix of each range's words (the second warp of each half), then the zero
+    // counts of level l's words and their prefix per half
+    if (((tid & 127u) >> 5) == 1u) {
+      const uint32_t h = tid >> 7;
+      range_word_prefix(xb1[h], range_words(hs[h][kRgGlo], hs[h][kRgCnt]), xwp[h]);
+    }
     {
-      // zero counts per word (valid positions of the merge), exclusive prefix per half
       uint32_t z0 = 0, z1 = 0;  // thread k handles words 2k, 2k+1 of the combined array
       const uint32_t wA = 2u * tid, wB = 2u * tid + 1u;
       auto wz = [&](uint32_t wc) -> uint32_t {
         const uint32_t h = wc >= kPairW ? 1u : 0u;
         const uint32_t wi = wc - h * kPairW;
-        if (wi >= 4u * hs[h][6]) return 0u;
-        const uint32_t pos = 32u * (4u * hs[h][5] + wi);  // merge position of the word
-        const uint32_t N1 = hs[h][8];
+        if (wi >= 4u * hs[h][kNblk]) return 0u;
+        const uint32_t pos = 32u * (4u * hs[h][kRgBlo] + wi);  // merge position of the word
+        const uint32_t N1 = hs[h][kN1];
         const uint32_t valid = pos >= N1 ? 0u : min(32u, N1 - pos);
         return __popc(~cw1[h][wi] & low_mask(valid));
       };
@@ -926,44 +1202,31 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
       const uint32_t base1 = scratch[32];
       if (wA < 2u * kPairW) {
         const uint32_t h = wA >= kPairW ? 1u : 0u;
-        zw1[h][wA - h * kPairW] = hs[h][7] + excl - (h ? base1 : 0u);
+        zw1[h][wA - h * kPairW] = hs[h][kRgZblk] + excl - (h ? base1 : 0u);
       }
       if (wB < 2u * kPairW) {
         const uint32_t h = wB >= kPairW ? 1u : 0u;
-        zw1[h][wB - h * kPairW] = hs[h][7] + excl + z0 - (h ? base1 : 0u);
+        zw1[h][wB - h * kPairW] = hs[h][kRgZblk] + excl + z0 - (h ? base1 : 0u);
       }
     }
-    // exceptions of both ranges, looked up once per chunk: every set bit of the range's bitmap
-    // words is a position whose element the tail moved
+    // every exception of the ranges at its position: rank e sits at the e-th set bit of the
+    // range's words (the last word whose prefix is at most e)
     {
-      const uint32_t hmask = (1u << pa.x.hbits) - 1u;
-      for (uint32_t wc = tid; wc < 2u * kPairW; wc += kThreads) {
-        const uint32_t h = wc >= kPairW ? 1u : 0u;
-        const uint32_t wi = wc - h * kPairW;
-        const uint32_t cnt = hs[h][10];
-        if (cnt == 0) continue;
-        const uint32_t g_lo = hs[h][1] + hs[h][9];
-        const uint32_t nw = ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5);
-        if (wi >= nw) continue;
-        uint32_t bits = xb1[h][wi];
-        while (bits) {
-          const uint32_t b = __ffs(static_cast<int>(bits)) - 1u;
-          bits &= bits - 1u;
-          const uint32_t gq = (((g_lo >> 5) + wi) << 5) + b;
-          if (gq < g_lo || gq >= g_lo + cnt) continue;
-          uint32_t slot = xhash_slot(gq, pa.x.hbits);
-          uint32_t xs = 0u;
-          for (uint32_t probe = 0; probe <= hmask; ++probe) {
-            const uint32_t key = pa.x.keys[slot];
-            if (key == gq) {
-              xs = pa.x.vals[slot];
-              break;
-            }
-            if (key == 0xFFFFFFFFu) break;
-            slot = (slot + 1u) & hmask;
-          }
-          xval[h][gq - g_lo] = xs;
+      const uint32_t h = tid >> 7;
+      const uint32_t k = tid & 127u;
+      const uint32_t xc = hs[h][kRgXcnt], xb = hs[h][kRgXbase];
+      const uint32_t g_lo = hs[h][kRgGlo];
+      const uint32_t nxw = range_words(g_lo, hs[h][kRgCnt]);
+      for (uint32_t e = k; e < xc; e += 128u) {
+        uint32_t lo = 0, hi = nxw;
+        while (hi - lo > 1u) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (xwp[h][mid] <= e) lo = mid;
+          else hi = mid;
         }
+        const uint32_t bit = select_set_bit(xb1[h][lo], e - xwp[h][lo]);
+        const uint32_t pos = min(32u * lo + bit - (g_lo & 31u), kChunk - 1u);
+        xval[h][pos] = e == k ? xv0 : (e == k + 128u ? xv1 : pa.x.val[xb + e]);
       }
     }
     __syncthreads();
@@ -971,12 +1234,12 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
     uint32_t hs1[2], hn11[2], hT1[2], hshift[2], hw0[2], hglo[2];
 #pragma unroll
     for (uint32_t h = 0; h < 2u; ++h) {
-      hs1[h] = hs[h][1];
-      hn11[h] = hs[h][2];
-      hT1[h] = hs[h][3];
-      hshift[h] = hs[h][4];
-      hw0[h] = 4u * hs[h][5];
-      hglo[h] = hs[h][1] + hs[h][9];
+      hs1[h] = hs[h][kS1];
+      hn11[h] = hs[h][kN11];
+      hT1[h] = hs[h][kT1];
+      hshift[h] = hs[h][kShift];
+      hw0[h] = 4u * hs[h][kRgBlo];
+      hglo[h] = hs[h][kRgGlo];
     }
     // outputs: lane = position in a word of level l+1; warp w owns words w, w+8, ...
     E *C = out + mb2.s;
@@ -1045,38 +1308,6 @@ __global__ void __launch_bounds__(kThreads) pair_gather_kernel(PairArgs pa) {
 // of the stable interleave writes every position first; this pass then overwrites the
 // first-half positions with their literal elements. The tails follow unchanged.
 
-// zeros among the coins of steps [0, x) of merge r, x <= N (zb and the scanned zc)
-__device__ uint32_t zeros_before(const LevelArgs &a, uint32_t r, uint32_t x) {
-  uint32_t chunk = x / kChunk;
-  if (chunk >= a.J) chunk = a.J - 1u;  // x = N on a chunk boundary: the whole last chunk
-  const uint64_t cid = static_cast<uint64_t>(r) * a.J + chunk;
-  uint32_t Z = a.zc[cid];
-  const uint32_t rel = min(x - chunk * kChunk, kChunk);
-  const uint32_t nb = rel >> 7;  // whole 128-step blocks before x (their counts: 32 bytes read
-                                 // as two vectors, the first nb bytes summed)
-  {
-    const uint4 *zb4 = reinterpret_cast<const uint4 *>(a.zb + cid * 32u);
-    const uint4 lo = zb4[0], hi = zb4[1];
-    const uint32_t w8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-    for (uint32_t k = 0; k < 8u; ++k) {
-      const uint32_t keep = nb >= 4u * k + 4u ? 4u : (nb > 4u * k ? nb - 4u * k : 0u);
-      const uint32_t m = keep >= 4u ? 0xFFFFFFFFu : ((1u << (8u * keep)) - 1u);
-      Z += __vsadu4(w8[k] & m, 0u);  // sum of the kept bytes
-    }
-  }
-  const uint32_t q = rel & 127u;
-  if (q != 0u && nb < 32u) {
-    const uint4 c = coin_block(a.key, a.level, r, chunk * 32u + nb);
-    const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-    for (uint32_t k = 0; k < 4u; ++k) {
-      const uint32_t lo = 32u * k;
-      if (q > lo) Z += __popc(~w4[k] & low_mask(min(q - lo, 32u)));
-    }
-  }
-  return Z;
-}
 
 // the lap starts S_j and Z(S_j) of every merge, while S_j < T (one thread per merge)
 __global__ void __launch_bounds__(kThreads) lap_kernel(LevelArgs a) {
@@ -1283,8 +1514,6 @@ __global__ void __launch_bounds__(kStageThreads) word_gather_kernel(LevelArgs a,
   const E *__restrict__ in = static_cast<const E *>(a.in);
   E *__restrict__ out = static_cast<E *>(a.out);
   const uint32_t tid = threadIdx.x;
-  const uint32_t lane = tid & 31u;
-  const uint32_t warp = tid >> 5;
   const uint64_t nchunks = static_cast<uint64_t>(a.M) * a.J;
   for (uint64_t cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
     const uint32_t r = static_cast<uint32_t>(cid / a.J);
@@ -1357,11 +1586,12 @@ __global__ void __launch_bounds__(kStageThreads) word_gather_kernel(LevelArgs a,
 // Two levels l, l+1 in one pass for 4-byte elements. A CTA takes 4096 outputs of level l+1;
 // they read one range of each of its halves (merges 2R and 2R+1 of level l), and each range is
 // the interleave of one run of each half of its level-l merge (then that merge's leftover),
-// with level l's tail moves as exceptions. The four input runs are copied to shared memory
-// with 16-byte asynchronous copies; the two level-l ranges are built there (walking the runs
-// with level l's coins, then overwriting the exception positions from the exception hash); the
-// level l+1 outputs are placed from them as in the staged single gather.
-__global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa) {
+// with level l's tail moves as exceptions. The chunk's record (pair_ranges_kernel) names the
+// four input runs, which are copied to shared memory with 16-byte asynchronous copies while
+// the coins are generated; the two level-l ranges are built there (walking the runs with level
+// l's coins, then overwriting the exception positions from the exception list); the level l+1
+// outputs are placed from them as in the staged single gather.
+__global__ void __launch_bounds__(kStageThreads, 6) pair_staged_kernel(PairArgs pa) {
   using E = uint32_t;
   constexpr uint32_t kV = 4;
   constexpr uint32_t kRunBuf = kChunk + 8u * kV + kStageGroup;  // four runs with their phases
@@ -1373,7 +1603,8 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
   __shared__ uint32_t cw1[2][kPairW + 1u];
   __shared__ uint32_t zw1[2][kPairW];
   __shared__ uint32_t xb1[2][kPairW];
-  __shared__ uint32_t hs[2][12];
+  __shared__ uint32_t xwp[2][kPairW];
+  __shared__ uint32_t hs[2][kRgWords];  // the chunk's record: its two level-l ranges
   const LevelArgs &a1 = pa.l1;
   const LevelArgs &a2 = pa.l2;
   if (a1.ctrl[1]) return;  // level l's tails overflowed: the unfused fallback runs instead
@@ -1397,23 +1628,38 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
     const uint4 mi2 = a2.minfo[R];
     const uint32_t T2 = mi2.x;
     const uint32_t abit2 = (mi2.y == h1) ? 1u : 0u;  // 1: level l+1's first half ran out
-    // level l+1: chunk-relative break step Tc2, zeros before it zT2; the two level-l ranges
-    uint32_t Tc2, zT2, lo0, lo1;
-    if (t0 >= T2) {
-      Tc2 = 0;
-      zT2 = 0;
-      lo0 = abit2 ? 0u : t0 - h2;
-      lo1 = abit2 ? t0 - h1 : 0u;
-    } else {
+    // level l+1: chunk-relative break step Tc2 and the zeros before it zT2
+    uint32_t Tc2 = 0, zT2 = 0;
+    if (t0 < T2) {
       const uint32_t Z0 = a2.zc[cid];
       Tc2 = min(t1, T2) - t0;
       const uint32_t Jr = (N2 + kChunk - 1u) / kChunk;
       zT2 = (t1 <= T2) ? ((j + 1u < Jr) ? a2.zc[cid + 1] - Z0 : h1 - Z0) : mi2.y - Z0;
-      lo0 = Z0;
-      lo1 = t0 - Z0;
     }
-    const uint32_t cnt0 = min(zT2 + (abit2 ? 0u : len - Tc2), h1 - min(lo0, h1));
-    const uint32_t cnt1 = min((Tc2 - zT2) + (abit2 ? len - Tc2 : 0u), h2 - min(lo1, h2));
+    (void)h2;
+    // the record of the two level-l ranges (pair_ranges_kernel), then their four input runs
+    // staged at once, each at its own 16-byte phase; the coins follow while the copies run
+    if (warp == 1u) hs[lane >> 4][lane & 15u] =
+        reinterpret_cast<const uint32_t *>(pa.xr + (2u * cid + (lane >> 4)) * 4u)[lane & 15u];
+    __syncthreads();
+    const uint32_t cnt0 = hs[0][kRgCnt], cnt1 = hs[1][kRgCnt];
+    auto phase_of = [](const E *p) {
+      return static_cast<uint32_t>((reinterpret_cast<uintptr_t>(p) & 15u) / sizeof(E));
+    };
+    auto up = [](uint32_t x) { return ((x + kV - 1u) / kV) * kV; };
+    const E *const sa0 = in + hs[0][kRgRunA];
+    const E *const sb0 = in + hs[0][kRgRunB];
+    const E *const sa1 = in + hs[1][kRgRunA];
+    const E *const sb1 = in + hs[1][kRgRunB];
+    const uint32_t offA0 = phase_of(sa0);
+    const uint32_t offB0 = up(offA0 + hs[0][kRgNa]) + phase_of(sb0);
+    const uint32_t offA1 = up(offB0 + hs[0][kRgNb]) + phase_of(sa1);
+    const uint32_t offB1 = up(offA1 + hs[1][kRgNa]) + phase_of(sb1);
+    stage_run(sruns + offA0, sa0, min(hs[0][kRgNa], kRunBuf - min(offA0, kRunBuf)));
+    stage_run(sruns + offB0, sb0, min(hs[0][kRgNb], kRunBuf - min(offB0, kRunBuf)));
+    stage_run(sruns + offA1, sa1, min(hs[1][kRgNa], kRunBuf - min(offA1, kRunBuf)));
+    stage_run(sruns + offB1, sb1, min(hs[1][kRgNb], kRunBuf - min(offB1, kRunBuf)));
+    cp_async_commit();
     if (warp == 2u) {
       // coins of level l+1 for steps [t0, t0 + Tc2) and the zeros before each word
       const uint32_t nwords = (Tc2 + 31u) >> 5;
@@ -1438,37 +1684,19 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
         ex += z4[k];
       }
     } else if (warp < 2u) {
-      // level l, half h = warp: merge r1 = 2R + h, positions [lo, lo + cnt)
+      // level l, half h = warp: the coin words over its range, the zeros before each word, the
+      // range's exception bits and their prefix
       const uint32_t h = warp;
-      const uint32_t lo = h ? lo1 : lo0;
-      const uint32_t cnt = h ? cnt1 : cnt0;
-      const uint32_t r1 = 2u * R + h;
-      const MergeBounds mb1 = merge_bounds(a1, r1);
-      const uint32_t N1 = static_cast<uint32_t>(mb1.e - mb1.s);
-      const uint32_t n11 = static_cast<uint32_t>(mb1.mid - mb1.s);
-      const uint32_t n12 = N1 - n11;
-      const uint4 mi1 = a1.minfo[r1];
-      const uint32_t T1 = mi1.x;
-      const uint32_t abit1 = (mi1.y == n11) ? 1u : 0u;
-      const uint32_t qe = min(lo + cnt, T1);  // [lo, qe): interleave positions
-      const uint32_t blo = lo >> 7;
-      const uint32_t nblk = qe > lo ? min(((qe + 127u) >> 7) - blo, kPairW / 4u) : 0u;
-      const uint64_t row = static_cast<uint64_t>(r1) * a1.J;
-      // zeros before block blo: the chunk prefix plus the chunk's earlier blocks
-      uint32_t zb = 0;
-      if (nblk) {
-        const uint32_t b = (blo & ~31u) + lane;
-        if (b < blo) zb = a1.zb[row * 32u + b];
-      }
-      zb = warp_sum(zb);
-      const uint32_t zbase = nblk ? a1.zc[row + (blo >> 5)] + zb : 0u;
+      const uint32_t lo = hs[h][kRgLo], Tc1 = hs[h][kRgTc], blo = hs[h][kRgBlo];
+      const uint32_t nblk = Tc1 ? min(((lo + Tc1 + 127u) >> 7) - blo, kPairW / 4u) : 0u;
       for (uint32_t k = lane; k < nblk; k += 32u) {
-        const uint4 c = coin_block(a1.key, a1.level, r1, blo + k);
+        const uint4 c = coin_block(a1.key, a1.level, hs[h][kRgMerge], blo + k);
         cw1[h][4u * k + 0u] = c.x;
         cw1[h][4u * k + 1u] = c.y;
         cw1[h][4u * k + 2u] = c.z;
         cw1[h][4u * k + 3u] = c.w;
       }
+      load_range_bits(pa.x, hs[h][kRgGlo], hs[h][kRgCnt], xb1[h], lane, 32u);
       __syncwarp();
       // zeros before each word (merge-relative): lane takes words 5*lane .. 5*lane+4
       {
@@ -1480,7 +1708,7 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
           z5[k] = wi < nw ? static_cast<uint32_t>(__popc(~cw1[h][wi])) : 0u;
           zs += z5[k];
         }
-        uint32_t ex = zbase + warp_inclusive_scan(zs) - zs;
+        uint32_t ex = hs[h][kRgZblk] + warp_inclusive_scan(zs) - zs;
 #pragma unroll
         for (uint32_t k = 0; k < 5u; ++k) {
           const uint32_t wi = 5u * lane + k;
@@ -1488,75 +1716,8 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
           ex += z5[k];
         }
       }
-      // exception bit words for global positions [s1 + lo, s1 + lo + cnt)
-      const uint32_t g_lo = static_cast<uint32_t>(mb1.s) + lo;
-      const uint32_t nxw = cnt ? ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5) : 0u;
-      const uint64_t nbw = (a1.n + 31u) >> 5;
-      for (uint32_t wi = lane; wi < nxw && wi < kPairW; wi += 32u) {
-        const uint64_t bw = (g_lo >> 5) + wi;
-        xb1[h][wi] = bw < nbw ? pa.x.bits[bw] : 0u;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        uint32_t Tc1 = 0, zT1 = 0, Zlo = 0, za, na, ob, nb;
-        if (lo >= T1) {
-          za = abit1 ? 0u : lo - n12;
-          ob = abit1 ? lo - n11 : 0u;
-          na = abit1 ? 0u : cnt;
-          nb = abit1 ? cnt : 0u;
-        } else {
-          auto zpref = [&](uint32_t q) {
-            const uint32_t wi = min((q >> 5) - 4u * blo, kPairW - 1u);
-            return zw1[h][wi] + static_cast<uint32_t>(__popc(~cw1[h][wi] & low_mask(q & 31u)));
-          };
-          Zlo = zpref(lo);
-          const uint32_t Zqe = (qe == T1) ? mi1.y : zpref(qe);
-          Tc1 = qe - lo;
-          zT1 = Zqe - Zlo;
-          const uint32_t rest = lo + cnt - qe;
-          za = Zlo;
-          ob = lo - Zlo;
-          na = zT1 + (abit1 ? 0u : rest);
-          nb = (Tc1 - zT1) + (abit1 ? rest : 0u);
-        }
-        // (the runs stay inside their halves even for an inconsistent plan)
-        za = min(za, n11);
-        na = min(na, n11 - za);
-        ob = min(ob, n12);
-        nb = min(nb, n12 - ob);
-        hs[h][0] = lo;
-        hs[h][1] = cnt;
-        hs[h][2] = Tc1;
-        hs[h][3] = zT1;
-        hs[h][4] = abit1;
-        hs[h][5] = blo;
-        hs[h][6] = static_cast<uint32_t>(mb1.s) + za;    // first half's run (input index)
-        hs[h][7] = na;
-        hs[h][8] = static_cast<uint32_t>(mb1.mid) + ob;  // second half's run (input index)
-        hs[h][9] = nb;
-        hs[h][10] = g_lo;
-        hs[h][11] = Zlo;
-      }
+      range_word_prefix(xb1[h], range_words(hs[h][kRgGlo], hs[h][kRgCnt]), xwp[h]);
     }
-    __syncthreads();
-    // stage the four input runs, each at its own 16-byte phase
-    auto phase_of = [](const E *p) {
-      return static_cast<uint32_t>((reinterpret_cast<uintptr_t>(p) & 15u) / sizeof(E));
-    };
-    auto up = [](uint32_t x) { return ((x + kV - 1u) / kV) * kV; };
-    const E *const sa0 = in + hs[0][6];
-    const E *const sb0 = in + hs[0][8];
-    const E *const sa1 = in + hs[1][6];
-    const E *const sb1 = in + hs[1][8];
-    const uint32_t offA0 = phase_of(sa0);
-    const uint32_t offB0 = up(offA0 + hs[0][7]) + phase_of(sb0);
-    const uint32_t offA1 = up(offB0 + hs[0][9]) + phase_of(sa1);
-    const uint32_t offB1 = up(offA1 + hs[1][7]) + phase_of(sb1);
-    stage_run(sruns + offA0, sa0, min(hs[0][7], kRunBuf - min(offA0, kRunBuf)));
-    stage_run(sruns + offB0, sb0, min(hs[0][9], kRunBuf - min(offB0, kRunBuf)));
-    stage_run(sruns + offA1, sa1, min(hs[1][7], kRunBuf - min(offA1, kRunBuf)));
-    stage_run(sruns + offB1, sb1, min(hs[1][9], kRunBuf - min(offB1, kRunBuf)));
-    cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
     // level l: the two ranges into svals (half 0 at 0, half 1 at voff1), eight positions a thread
@@ -1598,36 +1759,39 @@ __global__ void __launch_bounds__(kStageThreads) pair_staged_kernel(PairArgs pa)
       }
     }
     __syncthreads();
-    // level l's tail moves: the element at an exception position comes from the exception hash
+    // level l's tail moves: exception e of a range (its rank in the range) sits at the e-th set
+    // bit of the range's words; its element comes from the list. Four exceptions a thread at a
+    // time, their loads in flight together.
     {
-      const uint32_t hmask = (1u << pa.x.hbits) - 1u;
-      for (uint32_t wc = tid; wc < 2u * kPairW; wc += kStageThreads) {
-        const uint32_t h = wc >= kPairW ? 1u : 0u;
-        const uint32_t wi = wc - h * kPairW;
-        const uint32_t cnt = hs[h][1];
-        if (cnt == 0u) continue;
-        const uint32_t g_lo = hs[h][10];
-        const uint32_t nxw = ((g_lo + cnt + 31u) >> 5) - (g_lo >> 5);
-        if (wi >= nxw) continue;
-        uint32_t xbits = xb1[h][wi];
-        while (xbits) {
-          const uint32_t b = __ffs(static_cast<int>(xbits)) - 1u;
-          xbits &= xbits - 1u;
-          const uint32_t gq = (((g_lo >> 5) + wi) << 5) + b;
-          if (gq < g_lo || gq >= g_lo + cnt) continue;
-          uint32_t slot = xhash_slot(gq, pa.x.hbits);
-          uint32_t xs = 0u;
-          for (uint32_t probe = 0; probe <= hmask; ++probe) {
-            const uint32_t key = pa.x.keys[slot];
-            if (key == gq) {
-              xs = pa.x.vals[slot];
-              break;
+      const uint32_t c0 = hs[0][13], ctot = c0 + hs[1][13];
+      for (uint32_t e0 = 4u * tid; e0 < ctot; e0 += 4u * kStageThreads) {
+        uint32_t xs[4], dst[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u) {
+          const uint32_t e = e0 + u;
+          dst[u] = kNone;
+          if (e < ctot) {
+            const uint32_t h = e < c0 ? 0u : 1u;
+            const uint32_t k = h ? e - c0 : e;
+            // the word holding it: the last word whose prefix is <= k
+            const uint32_t nxw = min(((hs[h][10] + hs[h][1] + 31u) >> 5) - (hs[h][10] >> 5), kPairW);
+            uint32_t lo = 0, hi = nxw;
+            while (hi - lo > 1u) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (xwp[h][mid] <= k) lo = mid;
+              else hi = mid;
             }
-            if (key == 0xFFFFFFFFu) break;
-            slot = (slot + 1u) & hmask;
+            const uint32_t b = select_set_bit(xb1[h][lo], k - xwp[h][lo]);
+            dst[u] = (h ? voff1 : 0u) + min(32u * lo + b - (hs[h][10] & 31u), kChunk - 1u);
+            xs[u] = pa.x.val[hs[h][12] + k];
           }
-          svals[(h ? voff1 : 0u) + (gq - g_lo)] = in[xs < a1.n ? xs : 0u];
         }
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u)
+          if (dst[u] != kNone) xs[u] = in[xs[u] < a1.n ? xs[u] : 0u];
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u)
+          if (dst[u] != kNone) svals[min(dst[u], kValBuf - 1u)] = xs[u];
       }
     }
     __syncthreads();
@@ -1731,6 +1895,17 @@ LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *o
 
 constexpr unsigned kResident = 152u * 8u;
 
+ExcArgs exc_args(const Plan &p, const Buffers &b) {
+  ExcArgs x;
+  x.bits = b.xbits;
+  x.src = b.xsrc;
+  x.val = b.xval;
+  x.bpre = b.xbpre;
+  x.tpre = b.xtpre;
+  x.n = p.n;
+  return x;
+}
+
 template <typename F>
 void timed(Prof *pf, int kind, cudaStream_t s, F &&launch) {
   if (pf) pf->begin(kind, s);
@@ -1821,10 +1996,8 @@ cudaError_t pair_data_t(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv
   pa.l1 = level_args(p, lv1, in, out, b1, seed);
   pa.l1.zb = b1.zb;
   pa.l2 = level_args(p, lv2, out, out, b2, seed);
-  pa.x.bits = b1.xbits;
-  pa.x.keys = b1.xkeys;
-  pa.x.vals = b1.xvals;
-  pa.x.hbits = lv1.xhbits;
+  pa.x = exc_args(p, b1);
+  pa.xr = b1.xrange;
   const uint64_t nchunks2 = static_cast<uint64_t>(lv2.M) * lv2.J;
   timed(p.prof, kKindPairGather, s, [&] {
     if constexpr (sizeof(E) == 4)
@@ -1875,21 +2048,35 @@ cudaError_t launch_pair_plan(const Plan &p, const LevelPlan &lv1, const LevelPla
   a1.zb = b1.zb;
   cudaError_t err = plan_kernels(p, a1, lv1, b1, s);
   if (err != cudaSuccess) return err;
-  // the first level's tail moves as exceptions of the pair's data pass
+  // the first level's tail moves as exceptions of the pair's data pass: their bitmap and
+  // sources, the rank index, then the list in position order
   err = cudaMemsetAsync(b1.xbits, 0, (p.n + 31) / 32 * 4, s);
   if (err != cudaSuccess) return err;
-  err = cudaMemsetAsync(b1.xkeys, 0xFF, sizeof(uint32_t) << lv1.xhbits, s);
-  if (err != cudaSuccess) return err;
-  ExcArgs x;
-  x.bits = b1.xbits;
-  x.keys = b1.xkeys;
-  x.vals = b1.xvals;
-  x.hbits = lv1.xhbits;
-  timed(p.prof, kKindExceptions, s,
-        [&] { exceptions_kernel<<<kResident, kThreads, 0, s>>>(a1, x); });
+  const ExcArgs x = exc_args(p, b1);
+  const uint64_t xtiles = ((p.n + kXBlock - 1) / kXBlock + kXTileBlocks - 1) / kXTileBlocks;
+  timed(p.prof, kKindExceptions, s, [&] {
+    exceptions_kernel<<<kResident, kThreads, 0, s>>>(a1, x);
+    xcount_kernel<<<static_cast<unsigned>(xtiles), kThreads, 0, s>>>(a1, x);
+    xtiles_kernel<<<1, 1024, 0, s>>>(a1, x);
+    xscatter_kernel<<<kResident, kThreads, 0, s>>>(a1, x);
+  });
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return plan_kernels(p, level_args(p, lv2, nullptr, nullptr, b2, seed), lv2, b2, s);
+  err = plan_kernels(p, level_args(p, lv2, nullptr, nullptr, b2, seed), lv2, b2, s);
+  if (err != cudaSuccess) return err;
+  // what every chunk of the data pass reads: the records of its two level-l ranges
+  PairArgs pa;
+  pa.in = nullptr;
+  pa.out = nullptr;
+  pa.l1 = a1;
+  pa.l2 = level_args(p, lv2, nullptr, nullptr, b2, seed);
+  pa.x = x;
+  pa.xr = b1.xrange;
+  const uint64_t nchunks2 = static_cast<uint64_t>(lv2.M) * lv2.J;
+  timed(p.prof, kKindExceptions, s, [&] {
+    pair_ranges_kernel<<<grid_for(2 * nchunks2, kThreads, kResident), kThreads, 0, s>>>(pa);
+  });
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pair_data(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv2,

@@ -25,6 +25,8 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kTileMaxDepth = 6u;        // tile kernel: at most 2^6 base blocks a tile
 constexpr uint64_t kPairParityBytes = 1ull << 28;  // arrays from which a shuffle fixes its pass
                                                    // parity with a fused pair of levels
+constexpr uint32_t kXBlock = 1024u;       // positions per block of a pair's exception rank index
+constexpr uint32_t kXTileBlocks = 1024u;  // blocks per tile of that index (one CTA counts one)
 
 // Kernel classes timed by the optional profiler (MS_FLAG_PROFILE).
 enum KernelKind : int {
@@ -75,7 +77,7 @@ struct LevelPlan {
   // global levels fused in pairs: 1 = first level of a pair (its tail moves become exceptions
   // of the pair's single data pass), 2 = second level of a pair, 0 = unpaired
   uint32_t pair;
-  uint32_t xhbits;  // exception hash of a pair's first level: 2^xhbits slots
+  uint32_t xcap;    // a pair's first level: entries of its exception lists (2 kcap), else 0
   uint32_t lcap;    // literal merge (MS_FLAG_LITERAL): laps cached per merge
 };
 
@@ -116,8 +118,13 @@ struct Plan {
   uint32_t plan_sets = 0;
   // exception structures of a pair's first level (offsets within one copy; one copy per two
   // plan sets): per-block zero counts (one byte per 128 coins), the exception bitmap (one bit
-  // per element) and the exception hash (keys, values)
-  size_t off_zb = 0, off_xbits = 0, off_xkeys = 0, off_xvals = 0, exc_base = 0, exc_bytes = 0;
+  // per element), the input index of each tail patch's element (by patch), the same indices in
+  // position order (by rank), the rank index (exceptions before every 1024 positions within
+  // their tile of 2^20 positions, and before every tile), and, for every chunk of the pair's
+  // second level, the record of the two ranges it reads (2 x 16 words)
+  size_t off_zb = 0, off_xbits = 0, off_xsrc = 0, off_xval = 0, off_xbpre = 0, off_xtpre = 0;
+  size_t off_xrange = 0;
+  size_t exc_base = 0, exc_bytes = 0;
   // literal merge (MS_FLAG_LITERAL): per merge, the first step of each lap of the first half's
   // rotating queue and the zero coins before it (uint2), lcap entries a merge (same copies)
   size_t off_laps = 0;
@@ -139,8 +146,11 @@ struct Buffers {
   void *other;      // ping-pong partner
   uint8_t *zb;
   uint32_t *xbits;
-  uint32_t *xkeys;
-  uint32_t *xvals;
+  uint32_t *xsrc;
+  uint32_t *xval;
+  uint32_t *xbpre;
+  uint32_t *xtpre;
+  uint4 *xrange;
   uint32_t *zc;
   uint4 *minfo;
   uint32_t *ctrl;

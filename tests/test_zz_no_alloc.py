@@ -75,15 +75,15 @@ def test_static_entry_point_at_its_size_limit():
     assert np.array_equal(got, want)
 
 
-def test_static_entry_point_drops_fused_pairs_that_do_not_fit():
-    """Fused pairs of levels need more plan scratch than the fixed array holds at
-    n = MS_STATIC_MAX_N; the entry point then runs one data pass per level instead, which gives
-    the same permutation as ms_perm with the pairs."""
+def test_static_entry_point_runs_fused_pairs_from_its_scratch():
+    """At n = MS_STATIC_MAX_N the plan with fused pairs of levels (their exception bitmap, the
+    exception lists in patch and in position order, and the rank index) fits the fixed array, so
+    the pairs run from it and give the same permutation as ms_perm with its own workspace."""
     import torch
 
     n = ms.MS_STATIC_MAX_N
     p = ms.params(B=1024, flags=ms.MS_FLAG_PAIR_LEVELS)
-    assert ms.ms_workspace_bytes(n, 4, p) > ms.MS_STATIC_SCRATCH_BYTES
+    assert ms.ms_workspace_bytes(n, 4, p) <= ms.MS_STATIC_SCRATCH_BYTES
     assert ms.plan(n, 4, B=1024, flags=ms.MS_FLAG_PAIR_LEVELS)["fused_pairs"] > 0
     want = _perm_with_workspace(torch, n, 11, p)
     got = _perm_static(torch, n, 11, p)
