@@ -350,138 +350,189 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 }
 
 // Algorithm 1 on every final segment (at most B elements each; a segment starts at every set
-// bit of the boundary bitmap and ends at the next one, or at n). One warp per CTA walks windows
-// of kRsFyWinWords bitmap words, collecting the starts in order into a shared list; each batch
-// of `lanes` starts goes to the lanes, one segment a lane: the lane shuffles the local indices
-// 0..L-1 of its segment in shared memory (stride P = 2 mod 64: the lanes' entries at one index
-// sit in distinct banks) with the draws of stream (5, 0, s, i), then the warp writes each
-// segment of the batch through its indices: out[s + i] = in[s + idx[i]].
+// bit of the boundary bitmap and ends at the next one, or at n). CTAs of eight warps walk
+// windows of kRsFyWinWords bitmap words; warp 0 collects a window's segment starts, in order,
+// into a shared list. Each batch of `lanes` segments (segment k of the batch on lane k) then
+// runs in three phases on 16-bit local indices in shared memory (stride P = 2 mod 64: the lanes'
+// entries at one index sit in distinct banks):
+//   draws   all eight warps (warp w: quads w, w + 8, ... of every segment) write the identity
+//           and the draw of every position i >= 1 of stream (5, 0, s, i); a draw whose first
+//           Philox word rejects every slice is queued by its thread and finished after the loop;
+//   swaps   warp 0 runs each segment's chain i = L-1 .. 1 (one lane a segment, the draws read
+//           four steps ahead);
+//   write   a warp per segment: out[s + i] = in[s + idx[i]], eight loads a lane in flight.
 constexpr uint32_t kRsFyWinWords = 1024u;
+constexpr uint32_t kRsFyWarps = 8u;
+constexpr uint32_t kRsFyThreads = 32u * kRsFyWarps;
+constexpr uint32_t kRsFyFail = 8u;  // queued second-word draws a thread
 
+__device__ __forceinline__ void rs_swap16(uint16_t *A, uint32_t i, uint32_t j) {
+  const uint16_t t = A[i];
+  A[i] = A[j];
+  A[j] = t;
+}
+
+// One batch: the first kb starts of the list (cnt starts are waiting; the segment of start k
+// ends at start k + 1, else at the next set bit of the bitmap).
 template <typename E>
 __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const uint32_t *bnd,
-                            uint32_t P, const uint32_t *list, uint32_t k, uint16_t *idx,
-                            uint32_t *pre) {
-  const uint32_t lane = threadIdx.x;
-  const uint64_t nwords = (n + 31u) >> 5;
-  uint32_t s_pos = 0u, L = 0u;
-  if (lane < k) {
-    s_pos = list[lane];
+                            uint32_t P, const uint32_t *list, uint32_t kb, uint32_t cnt,
+                            uint16_t *Abuf, uint16_t *Dbuf, uint16_t *F, uint32_t *sS,
+                            uint32_t *sL) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  if (warp == 0u && lane < kb) {
+    const uint32_t s_pos = list[lane];
     uint64_t e = n;
-    if (lane + 1u < k) {
+    if (lane + 1u < cnt) {
       e = list[lane + 1u];
     } else {
       // the next start after s_pos in the bitmap (a later bit of its word, else a later word)
+      const uint64_t nwords = (n + 31u) >> 5;
       const uint64_t w = static_cast<uint64_t>(s_pos) >> 5;
       uint32_t bw = bnd[w] & ~low_mask((s_pos & 31u) + 1u);
       uint64_t q = w;
       while (bw == 0u && ++q < nwords) bw = bnd[q];
       if (bw) e = (q << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(bw)) - 1);
     }
-    L = static_cast<uint32_t>(min(e, n) - s_pos);
-    L = min(L, P - 2u);  // (a final segment never exceeds B <= P - 2)
-    uint16_t *const A = idx + lane * P;
-    for (uint32_t i = 0; i < L; ++i) A[i] = static_cast<uint16_t>(i);
-    // i = L-1 .. 1 by quads of positions (one Philox block draws four of them); the next quad's
-    // block is computed while the current one's swaps run
-    if (L >= 2u) {
-      uint32_t quad = (L - 1u) >> 2;
-      uint4 cur = philox10(make_uint4(quad, s_pos, kTagRsLeaf << 16, 0u), key);
-      for (;;) {
-        const uint4 nxt =
-            quad > 0 ? philox10(make_uint4(quad - 1u, s_pos, kTagRsLeaf << 16, 0u), key) : cur;
-        const uint32_t lo = quad << 2;
+    sS[lane] = s_pos;
+    // (a final segment never exceeds B <= P - 2)
+    const uint64_t len = min(e, n) - s_pos;
+    sL[lane] = len < P - 2u ? static_cast<uint32_t>(len) : P - 2u;
+  }
+  __syncthreads();
+  // draws
+  if (lane < kb) {
+    const uint32_t L = sL[lane], id = sS[lane];
+    uint16_t *const A = Abuf + lane * P;
+    uint16_t *const D = Dbuf + lane * P;
+    uint16_t *const Fq = F + tid * kRsFyFail;
+    const uint32_t nq = L ? ((L - 1u) >> 2) + 1u : 0u;
+    uint32_t nf = 0;
+#pragma unroll 2
+    for (uint32_t qd = warp; qd < nq; qd += kRsFyWarps) {
+      const uint4 blk = philox10(make_uint4(qd, id, kTagRsLeaf << 16, 0u), key);
+      // slice width of the quad's ranges (positions 1..3 of quad 0 take the general draw)
+      const uint32_t qb = 32u - __clz(4u * qd + 1u);
+      const uint32_t qmask = 0xFFFFFFFFu >> (32u - qb);
 #pragma unroll
-        for (uint32_t v = 4; v-- > 0;) {
-          const uint32_t pos = lo + v;
-          if (pos < L && pos >= 1u) {
-            const uint32_t j = min(draw_with_word0_flat(key, kTagRsLeaf, 0u, s_pos, pos, pos + 1u,
-                                                        pick_word(cur, v)),
-                                   pos);
-            const uint16_t t = A[pos];
-            A[pos] = A[j];
-            A[j] = t;
+      for (uint32_t v = 0; v < 4u; ++v) {
+        const uint32_t pos = 4u * qd + v;
+        if (pos < L) {
+          A[pos] = static_cast<uint16_t>(pos);
+          if (pos >= 1u) {
+            uint32_t x;
+            const uint32_t word = pick_word(blk, v);
+            const bool ok = qd ? draw_first_word_b(word, pos + 1u, qb, qmask, 2u * qb, 3u * qb, x)
+                               : draw_first_word(word, pos + 1u, x);
+            if (ok) {
+              D[pos] = static_cast<uint16_t>(x);
+            } else if (nf < kRsFyFail) {
+              Fq[nf++] = static_cast<uint16_t>(pos);
+            } else {
+              D[pos] = static_cast<uint16_t>(draw_continue(key, kTagRsLeaf, 0u, id, pos, pos + 1u));
+            }
           }
         }
-        if (quad == 0) break;
-        --quad;
-        cur = nxt;
+      }
+    }
+    // draws whose first word rejected every slice: words 1, 2, ... of their streams
+    for (uint32_t e = 0; e < nf; ++e) {
+      const uint32_t pos = Fq[e];
+      D[pos] = static_cast<uint16_t>(draw_continue(key, kTagRsLeaf, 0u, id, pos, pos + 1u));
+    }
+  }
+  __syncthreads();
+  // swaps, i = L-1 .. 1 (the draws are read four ahead of the chain and clamped to the segment)
+  if (warp == 0u && lane < kb) {
+    const uint32_t L = sL[lane];
+    uint16_t *const A = Abuf + lane * P;
+    const uint16_t *const D = Dbuf + lane * P;
+    uint32_t i = L;
+    while (i >= 5u) {
+      const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
+      const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
+      const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
+      const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
+      rs_swap16(A, i - 1u, j0);
+      rs_swap16(A, i - 2u, j1);
+      rs_swap16(A, i - 3u, j2);
+      rs_swap16(A, i - 4u, j3);
+      i -= 4u;
+    }
+    for (; i >= 2u; --i) rs_swap16(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+  }
+  __syncthreads();
+  // the batch's rows through the indices, a warp per segment
+  constexpr uint32_t kRows = sizeof(E) >= 16u ? 4u : 8u;
+  for (uint32_t k = warp; k < kb; k += kRsFyWarps) {
+    const uint32_t s_pos = sS[k], L = sL[k];
+    const uint16_t *const A = Abuf + k * P;
+    for (uint32_t i0 = 0; i0 < L; i0 += 32u * kRows) {
+      E v[kRows];
+#pragma unroll
+      for (uint32_t u = 0; u < kRows; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        if (i < L) v[u] = in[static_cast<uint64_t>(s_pos) + min(static_cast<uint32_t>(A[i]), L - 1u)];
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < kRows; ++u) {
+        const uint32_t i = i0 + 32u * u + lane;
+        if (i < L) out[static_cast<uint64_t>(s_pos) + i] = v[u];
       }
     }
   }
-  // the batch's rows through the indices, flattened over its segments (pre: exclusive prefix of
-  // the lengths): sixteen independent row loads a lane in flight before their stores
-  const uint32_t incl = warp_inclusive_scan(L);
-  pre[lane] = incl - L;
-  const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-  __syncwarp();
-  constexpr uint32_t kRows = sizeof(E) >= 16u ? 8u : 16u;
-  for (uint32_t e0 = 0; e0 < total; e0 += 32u * kRows) {
-    E v[kRows];
-    uint32_t dst[kRows];
-#pragma unroll
-    for (uint32_t t = 0; t < kRows; ++t) {
-      const uint32_t e = e0 + 32u * t + lane;
-      dst[t] = 0xFFFFFFFFu;
-      if (e < total) {
-        // the segment of flat index e: the last r < k with pre[r] <= e
-        uint32_t lo = 0, hi = k;
-        while (hi - lo > 1u) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (pre[mid] <= e) lo = mid;
-          else hi = mid;
-        }
-        const uint32_t i = e - pre[lo];
-        const uint32_t base = list[lo];
-        const uint16_t *const Ar = idx + lo * P;
-        const uint32_t Lr = (lo + 1u < k ? pre[lo + 1u] : total) - pre[lo];
-        v[t] = in[static_cast<uint64_t>(base) + min(static_cast<uint32_t>(Ar[i]), Lr - 1u)];
-        dst[t] = base + i;
-      }
-    }
-#pragma unroll
-    for (uint32_t t = 0; t < kRows; ++t)
-      if (dst[t] != 0xFFFFFFFFu) out[dst[t]] = v[t];
-  }
-  __syncwarp();
+  __syncthreads();
 }
 
 template <typename E>
-__global__ void __launch_bounds__(32) rs_fy_kernel(const E *in, E *out, uint64_t n, uint2 key,
-                                                  const uint32_t *bnd, uint32_t P,
-                                                  uint32_t lanes) {
-  extern __shared__ __align__(16) uint16_t idx[];
-  __shared__ uint32_t pre[32];
-  uint32_t *const list = reinterpret_cast<uint32_t *>(idx + ((lanes * P + 1u) & ~1u));
-  const uint32_t lane = threadIdx.x;
+__global__ void __launch_bounds__(kRsFyThreads) rs_fy_kernel(const E *in, E *out, uint64_t n,
+                                                            uint2 key, const uint32_t *bnd,
+                                                            uint32_t P, uint32_t lanes) {
+  extern __shared__ __align__(16) uint16_t fy_smem[];
+  __shared__ uint32_t sS[32], sL[32], s_cnt;
+  uint16_t *const Abuf = fy_smem;
+  uint16_t *const Dbuf = fy_smem + lanes * P;
+  uint32_t *const list = reinterpret_cast<uint32_t *>(fy_smem + ((2u * lanes * P + 1u) & ~1u));
+  uint16_t *const F = reinterpret_cast<uint16_t *>(list + lanes + 32u * 32u + 32u);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
   const uint64_t nwords = (n + 31u) >> 5;
   for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * kRsFyWinWords; w0 < nwords;
        w0 += static_cast<uint64_t>(gridDim.x) * kRsFyWinWords) {
-    uint32_t cnt = 0;  // starts waiting in the list (uniform across the warp)
+    uint32_t cnt = 0;  // starts waiting in the list (the same in every thread)
     for (uint32_t cw = 0; cw < kRsFyWinWords && w0 + cw < nwords; cw += 32u) {
-      const uint64_t wi = w0 + cw + lane;
-      uint32_t word = wi < nwords ? bnd[wi] : 0u;
-      const uint32_t c = static_cast<uint32_t>(__popc(word));
-      const uint32_t incl = warp_inclusive_scan(c);
-      uint32_t pos = cnt + incl - c;
-      while (word) {
-        list[pos++] = static_cast<uint32_t>(wi << 5) + static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
-        word &= word - 1u;
-      }
-      cnt += __shfl_sync(kFullMask, incl, 31);
-      __syncwarp();
-      while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
-        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, idx, pre);
-        for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
-          const uint32_t v = list[i + lanes];
-          __syncwarp(__activemask());
-          list[i] = v;
+      if (warp == 0u) {
+        const uint64_t wi = w0 + cw + lane;
+        uint32_t word = wi < nwords ? bnd[wi] : 0u;
+        const uint32_t c = static_cast<uint32_t>(__popc(word));
+        const uint32_t incl = warp_inclusive_scan(c);
+        uint32_t pos = cnt + incl - c;
+        while (word) {
+          list[pos++] = static_cast<uint32_t>(wi << 5) +
+                        static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
+          word &= word - 1u;
         }
-        __syncwarp();
+        if (lane == 31u) s_cnt = cnt + incl;
+      }
+      __syncthreads();
+      cnt = s_cnt;
+      while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
+        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
+        if (warp == 0u) {
+          for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
+            const uint32_t v = list[i + lanes];
+            __syncwarp(__activemask());
+            list[i] = v;
+          }
+        }
+        __syncthreads();
         cnt -= lanes;
       }
     }
-    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, idx, pre);
+    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, cnt, Abuf, Dbuf, F, sS, sL);
   }
 }
 
@@ -612,22 +663,24 @@ cudaError_t rs_launch_fy(const void *in, void *out, uint64_t n, uint2 key, const
                          uint32_t B, int sms, cudaStream_t s) {
   uint32_t P = B + 2u;
   while (P % 64u != 2u) ++P;
-  constexpr uint32_t kBudget = 96u * 1024u;  // (index regions; the start list adds ~4.3 KB)
-  const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (2u * P)));
-  // the lanes' index regions, then the window's list of segment starts
-  const size_t smem = ((static_cast<size_t>(lanes) * P + 1u) & ~static_cast<size_t>(1u)) * 2u +
-                      (lanes + 32u * 32u + 32u) * 4u;  // (lanes waiting + one read of 32 words)
+  // the lanes' index and draw regions (two of P 16-bit entries a lane) within kBudget
+  constexpr uint32_t kBudget = 132u * 1024u;
+  const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (4u * P)));
+  // the regions, the window's list of segment starts (the starts waiting plus one read of 32
+  // bitmap words) and the threads' queues of second-word draws
+  const size_t smem = ((2u * static_cast<size_t>(lanes) * P + 1u) & ~static_cast<size_t>(1u)) * 2u +
+                      (lanes + 32u * 32u + 32u) * 4u + kRsFyThreads * kRsFyFail * 2u;
   auto kern = rs_fy_kernel<E>;
   cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRsFyThreads, smem);
   if (e != cudaSuccess) return e;
   const uint64_t windows = ((n + 31u) / 32u + kRsFyWinWords - 1u) / kRsFyWinWords;
   const uint64_t resident = static_cast<uint64_t>(std::max(per_sm, 1)) * sms;
   const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1u, std::min(windows, resident)));
-  kern<<<grid, 32, smem, s>>>(static_cast<const E *>(in), static_cast<E *>(out), n, key, bnd, P,
-                              lanes);
+  kern<<<grid, kRsFyThreads, smem, s>>>(static_cast<const E *>(in), static_cast<E *>(out), n, key,
+                                        bnd, P, lanes);
   return cudaGetLastError();
 }
 
