@@ -414,6 +414,7 @@ int make_plan(uint64_t n, uint32_t w, uint32_t B, int32_t fuse_depth, uint32_t t
       }
       if (literal) {
         p.off_laps = off - ebase;   off += round_up(static_cast<size_t>(lcap_max) * 8u, 256);
+        p.off_ctab = off - ebase;   off += round_up(zc_cap * 128ull * 8u, 256);
       }
       if (balanced) {
         p.off_labels = off - ebase; off += round_up(n, 256);
@@ -540,6 +541,7 @@ msk::Buffers buffers_for(const Plan &p, void *data, void *ws, uint32_t set) {
   b.xtpre = reinterpret_cast<uint32_t *>(es + p.off_xtpre);
   b.xrange = reinterpret_cast<uint4 *>(es + p.off_xrange);
   b.laps = reinterpret_cast<uint2 *>(es + p.off_laps);
+  b.ctab = reinterpret_cast<uint2 *>(es + p.off_ctab);
   b.labels = reinterpret_cast<uint8_t *>(es + p.off_labels);
   b.zlab = reinterpret_cast<uint32_t *>(es + p.off_zlab);
   b.zc = reinterpret_cast<uint32_t *>(ps + p.off_zc);

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(32) fy_perm16_kernel(LeafArgs a, uint32_t per_
 // Algorithm 1 on every base block with uniform draws by the Fast Dice Roller (MS_FLAG_FDR): one
 // thread per block copies it to the output (a perm writes its positions) and swaps there, in
 // order, i = L-1 .. 1 with j from stream (LEAF, 0, block, i). The output is out of place or the
-// input itself; a thread touches only its own block.
+// input itself; a thread touches only its own block. (Used for an in-place shuffle.)
 template <typename E, bool kPerm>
 __global__ void __launch_bounds__(128) fy_fdr_kernel(const E *in, E *out, uint64_t n, uint32_t c,
                                                     uint2 key) {
@@ -307,16 +307,181 @@ __global__ void __launch_bounds__(128) fy_fdr_kernel(const E *in, E *out, uint64
   }
 }
 
+// The same pass out of place on eight-warp CTAs, 16-bit local indices in shared memory (stride
+// P = 2 mod 64 a block), a batch of `lanes` consecutive base blocks at a time (block k of the
+// batch on lane k): all eight warps make the draws (warp w: quads w, w + 8, ... of every block;
+// one Philox block serves a quad's four first words, and a draw that needs more than its first
+// word is queued by its thread and redone from word 0 after the loop), warp 0 runs the swap
+// chains, and a warp per block writes it through the indices.
+constexpr uint32_t kFdrWarps = 8u;
+constexpr uint32_t kFdrThreads = 32u * kFdrWarps;
+constexpr uint32_t kFdrFail = 8u;  // queued draws a thread
+
+// The Fast Dice Roller of draw_fdr on word 0 of its stream alone: true with the value if the
+// word's bits decide it (the loop then stops exactly where draw_fdr's does).
+__device__ __forceinline__ bool fdr_first_word(uint32_t word, uint32_t R, uint32_t &x) {
+  uint32_t v = 1u, c = 0u;  // (v < 2R and c < v throughout)
+  for (uint32_t u = 0; u < 32u; ++u) {
+    v <<= 1;
+    c = (c << 1) | ((word >> u) & 1u);
+    if (v >= R) {
+      if (c < R) {
+        x = c;
+        return true;
+      }
+      v -= R;
+      c -= R;
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void swap16(uint16_t *A, uint32_t i, uint32_t j) {
+  const uint16_t t = A[i];
+  A[i] = A[j];
+  A[j] = t;
+}
+
+template <typename E, bool kPerm>
+__global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *out, uint64_t n,
+                                                             uint32_t c, uint2 key, uint32_t P,
+                                                             uint32_t lanes) {
+  extern __shared__ __align__(16) uint16_t fdr_smem[];
+  uint16_t *const Abuf = fdr_smem;
+  uint16_t *const Dbuf = fdr_smem + lanes * P;
+  uint16_t *const F = Dbuf + lanes * P;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const uint32_t warp = tid >> 5;
+  const uint64_t q = 1ull << c;
+  for (uint64_t k0 = static_cast<uint64_t>(blockIdx.x) * lanes; k0 < q;
+       k0 += static_cast<uint64_t>(gridDim.x) * lanes) {
+    const uint32_t kb = (q - k0 < lanes) ? static_cast<uint32_t>(q - k0) : lanes;
+    // draws
+    if (lane < kb) {
+      const uint64_t k = k0 + lane;
+      const uint32_t id = static_cast<uint32_t>(k);
+      const uint32_t L = min(static_cast<uint32_t>(boundary(n, c, k + 1) - boundary(n, c, k)),
+                             P - 2u);
+      uint16_t *const A = Abuf + lane * P;
+      uint16_t *const D = Dbuf + lane * P;
+      uint16_t *const Fq = F + tid * kFdrFail;
+      const uint32_t nq = L ? ((L - 1u) >> 2) + 1u : 0u;
+      uint32_t nf = 0;
+#pragma unroll 2
+      for (uint32_t qd = warp; qd < nq; qd += kFdrWarps) {
+        const uint4 blk = philox10(make_uint4(qd, id, kTagLeaf << 16, 0u), key);
+#pragma unroll
+        for (uint32_t v = 0; v < 4u; ++v) {
+          const uint32_t pos = 4u * qd + v;
+          if (pos < L) {
+            A[pos] = static_cast<uint16_t>(pos);
+            if (pos >= 1u) {
+              uint32_t x;
+              if (fdr_first_word(pick_word(blk, v), pos + 1u, x)) {
+                D[pos] = static_cast<uint16_t>(x);
+              } else if (nf < kFdrFail) {
+                Fq[nf++] = static_cast<uint16_t>(pos);
+              } else {
+                uint32_t nb;
+                D[pos] = static_cast<uint16_t>(draw_fdr(key, kTagLeaf, 0u, id, pos, pos + 1u, &nb));
+              }
+            }
+          }
+        }
+      }
+      for (uint32_t e = 0; e < nf; ++e) {
+        const uint32_t pos = Fq[e];
+        uint32_t nb;
+        D[pos] = static_cast<uint16_t>(draw_fdr(key, kTagLeaf, 0u, id, pos, pos + 1u, &nb));
+      }
+    }
+    __syncthreads();
+    // swaps, i = L-1 .. 1 (the draws are read four ahead of the chain and clamped to the block)
+    if (warp == 0u && lane < kb) {
+      const uint64_t k = k0 + lane;
+      const uint32_t L = min(static_cast<uint32_t>(boundary(n, c, k + 1) - boundary(n, c, k)),
+                             P - 2u);
+      uint16_t *const A = Abuf + lane * P;
+      const uint16_t *const D = Dbuf + lane * P;
+      uint32_t i = L;
+      while (i >= 5u) {
+        const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
+        const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
+        const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
+        const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
+        swap16(A, i - 1u, j0);
+        swap16(A, i - 2u, j1);
+        swap16(A, i - 3u, j2);
+        swap16(A, i - 4u, j3);
+        i -= 4u;
+      }
+      for (; i >= 2u; --i) swap16(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+    }
+    __syncthreads();
+    // the blocks through their indices, a warp per block
+    constexpr uint32_t kRows = sizeof(E) >= 16u ? 4u : 8u;
+    for (uint32_t kk = warp; kk < kb; kk += kFdrWarps) {
+      const uint64_t k = k0 + kk;
+      const uint64_t s0 = boundary(n, c, k);
+      const uint32_t L = min(static_cast<uint32_t>(boundary(n, c, k + 1) - s0), P - 2u);
+      const uint16_t *const A = Abuf + kk * P;
+      for (uint32_t i0 = 0; i0 < L; i0 += 32u * kRows) {
+        E v[kRows];
+#pragma unroll
+        for (uint32_t u = 0; u < kRows; ++u) {
+          const uint32_t i = i0 + 32u * u + lane;
+          if (i < L) {
+            const uint32_t src = min(static_cast<uint32_t>(A[i]), L - 1u);
+            if constexpr (kPerm) v[u] = static_cast<E>(s0 + src);
+            else v[u] = in[s0 + src];
+          }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < kRows; ++u) {
+          const uint32_t i = i0 + 32u * u + lane;
+          if (i < L) out[s0 + i] = v[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename E, bool kPerm>
 cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t seed,
                           cudaStream_t s) {
   if (p.flags & MS_FLAG_FDR) {
-    // Algorithm 1 with the Fast Dice Roller draws: one thread per base block
-    const uint64_t grid = std::min<uint64_t>((p.q + 127u) / 128u, 1048576ull);
+    // Algorithm 1 with the Fast Dice Roller draws
+    const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    uint32_t P = p.leaf_max + 2u;  // (a base block has at most leaf_max elements)
+    while (P % 64u != 2u) ++P;
+    constexpr uint32_t kBudget = 132u * 1024u;  // index and draw regions (two of P entries a lane)
+    const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (4u * P)));
+    if (!kPerm && in == out) {
+      // in place: one thread per base block copies nothing and swaps in the array
+      const uint64_t grid = std::min<uint64_t>((p.q + 127u) / 128u, 1048576ull);
+      if (p.prof) p.prof->begin(kKindLeaf, s);
+      fy_fdr_kernel<E, kPerm><<<static_cast<unsigned>(grid), 128, 0, s>>>(
+          static_cast<const E *>(in), static_cast<E *>(out), p.n, p.c, key);
+      if (p.prof) p.prof->end(s);
+      return cudaGetLastError();
+    }
+    const size_t smem = (2u * static_cast<size_t>(lanes) * P + kFdrThreads * kFdrFail) * 2u;
+    auto fk = fy_fdr8_kernel<E, kPerm>;
+    cudaError_t e = allow_dynamic_smem(fk, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk, kFdrThreads, smem) !=
+            cudaSuccess)
+      return cudaErrorUnknown;
+    const uint64_t batches = (p.q + lanes - 1u) / lanes;
+    const uint64_t grid = std::min<uint64_t>(batches, static_cast<uint64_t>(std::max(per_sm, 1)) * sms);
     if (p.prof) p.prof->begin(kKindLeaf, s);
-    fy_fdr_kernel<E, kPerm><<<static_cast<unsigned>(grid), 128, 0, s>>>(
-        static_cast<const E *>(in), static_cast<E *>(out), p.n, p.c,
-        make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+    fk<<<static_cast<unsigned>(grid), kFdrThreads, smem, s>>>(
+        static_cast<const E *>(in), static_cast<E *>(out), p.n, p.c, key, P, lanes);
     if (p.prof) p.prof->end(s);
     return cudaGetLastError();
   }

@@ -59,6 +59,8 @@ struct LevelArgs {
   const uint32_t *alt_sel;
   uint2 *laps;             // literal merge: per merge, lcap entries (lap start, zeros before it)
   uint32_t lcap;
+  uint2 *ctab;             // literal merge: per coin word (128 a chunk), the word and the zeros
+                           // of the chunk's earlier words (count_kernel)
 };
 
 __device__ __forceinline__ bool gated_off(const LevelArgs &a) {
@@ -108,8 +110,30 @@ __global__ void __launch_bounds__(kThreads) count_kernel(LevelArgs a) {
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t blk = j * (kChunk / 128u) + lane;
     uint32_t z = 0;
-    if (128ull * blk < N) z = block_zero_count(coin_block(a.key, a.level, r, blk), blk, N);
+    uint4 c = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    if (128ull * blk < N) {
+      c = coin_block(a.key, a.level, r, blk);
+      z = block_zero_count(c, blk, N);
+    }
     if (a.zb) a.zb[cid * 32u + lane] = static_cast<uint8_t>(z);  // z <= 128
+    if (a.ctab) {
+      // the block's words with the zeros of the chunk's earlier words (whole words: a query at
+      // step x < N counts only words below x)
+      const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
+      uint32_t zw4[4], zs = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        zw4[k] = static_cast<uint32_t>(__popc(~w4[k]));
+        zs += zw4[k];
+      }
+      uint32_t ex = warp_inclusive_scan(zs) - zs;
+      uint2 *const t = a.ctab + cid * 128u + 4u * lane;
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        t[k] = make_uint2(w4[k], ex);
+        ex += zw4[k];
+      }
+    }
     z = warp_sum(z);
     if (lane == 0) a.zc[cid] = z;
   }
@@ -1403,13 +1427,14 @@ __global__ void __launch_bounds__(kThreads) literal_scatter_kernel(LevelArgs a) 
             P = x;
             break;
           }
-          const uint4 c = coin_block(a.key, a.level, r, x >> 7);
-          const uint32_t wx = pick_word(c, (x >> 5) & 3u);
-          if (((wx >> (x & 31u)) & 1u) == 0u) {
+          // the coin word at x and the zeros before x, from the level's word table
+          const uint64_t cx = static_cast<uint64_t>(r) * a.J + (x >> 12);
+          const uint2 tw = a.ctab[cx * 128u + ((x >> 5) & 127u)];
+          if (((tw.x >> (x & 31u)) & 1u) == 0u) {
             P = x;
             break;
           }
-          Zx = zeros_before(a, r, x);
+          Zx = a.zc[cx] + tw.y + static_cast<uint32_t>(__popc(~tw.x & low_mask(x & 31u)));
         }
       }
       out[mb.s + min(P, N - 1u)] = in[mb.s + k];
@@ -1889,7 +1914,11 @@ LevelArgs level_args(const Plan &p, const LevelPlan &lv, const void *in, void *o
   a.alt_sel = nullptr;
   a.laps = b.laps;
   a.lcap = lv.lcap;
-  if (p.flags & MS_FLAG_LITERAL) a.zb = b.zb;  // the literal merge's rank queries read it
+  a.ctab = nullptr;
+  if (p.flags & MS_FLAG_LITERAL) {  // the literal merge's rank queries read them
+    a.zb = b.zb;
+    a.ctab = b.ctab;
+  }
   return a;
 }
 

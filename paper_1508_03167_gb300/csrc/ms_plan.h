@@ -126,8 +126,9 @@ struct Plan {
   size_t off_xrange = 0;
   size_t exc_base = 0, exc_bytes = 0;
   // literal merge (MS_FLAG_LITERAL): per merge, the first step of each lap of the first half's
-  // rotating queue and the zero coins before it (uint2), lcap entries a merge (same copies)
-  size_t off_laps = 0;
+  // rotating queue and the zero coins before it (uint2), lcap entries a merge; and per coin word
+  // of a level, the word and the zeros of its chunk's earlier words (uint2) (same copies)
+  size_t off_laps = 0, off_ctab = 0;
   // balanced-word merge (MS_FLAG_BALANCED): one label byte per element and the chunk zero counts
   // of the labels (same copies)
   size_t off_labels = 0, off_zlab = 0;
@@ -162,6 +163,7 @@ struct Buffers {
   void *ptmp;
   uint32_t *ostart;  // first merge of every 1024 tail steps of a level (kscan), + one sentinel
   uint2 *laps;       // literal merge: lap table (see Plan::off_laps)
+  uint2 *ctab;       // literal merge: coin word table of a level (see Plan::off_ctab)
   uint8_t *labels;   // balanced-word merge: label bytes of a level
   uint32_t *zlab;    // balanced-word merge: zeros before each chunk of labels
 };
