@@ -756,7 +756,7 @@ __device__ uint32_t zeros_before(const LevelArgs &a, uint32_t r, uint32_t x) {
 // for every exception in position order, the input index that element comes from: a bitmap
 // marks the exception positions, and the rank of an exception (exceptions at lower positions)
 // is its index in the list. Ranks come from a two-level prefix of the bitmap's bit counts
-// (per 1024 positions within their tile of 2^20 positions, and per tile), so a data chunk finds
+// (per 1024 positions within their tile of 2^17 positions, and per tile), so a data chunk finds
 // its range's exceptions as one contiguous slice of the list. The data pass then gathers level
 // l+1's interleave straight from level l's input.
 
@@ -846,6 +846,7 @@ __global__ void __launch_bounds__(kThreads) exceptions_kernel(LevelArgs a, ExcAr
 // (a warp a block: one bitmap word a lane), then writes each block's prefix within the tile
 // and the tile's total.
 __global__ void __launch_bounds__(kThreads) xcount_kernel(LevelArgs a, ExcArgs x) {
+  static_assert(kXTileBlocks <= kThreads, "one block count a thread");
   __shared__ uint32_t cnt[kXTileBlocks];
   __shared__ uint32_t scratch[33];
   if (a.ctrl[1]) return;
@@ -853,49 +854,40 @@ __global__ void __launch_bounds__(kThreads) xcount_kernel(LevelArgs a, ExcArgs x
   const uint64_t nwords = (x.n + 31u) >> 5;
   const uint64_t nblocks = (x.n + kXBlock - 1u) / kXBlock;
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * kXTileBlocks;
+#pragma unroll 4
   for (uint32_t k = warp; k < kXTileBlocks; k += kThreads / 32u) {
     const uint64_t wi = (b0 + k) * 32u + lane;
     const uint32_t c = warp_sum(wi < nwords ? static_cast<uint32_t>(__popc(x.bits[wi])) : 0u);
     if (lane == 0) cnt[k] = c;
   }
   __syncthreads();
-  constexpr uint32_t kPer = kXTileBlocks / kThreads;
-  uint32_t v[kPer], sum = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < kPer; ++i) {
-    v[i] = cnt[kPer * tid + i];
-    sum += v[i];
-  }
+  const uint32_t v = tid < kXTileBlocks ? cnt[tid] : 0u;
   uint32_t total;
-  uint32_t ex = block_exclusive_scan(sum, scratch, &total);
-#pragma unroll
-  for (uint32_t i = 0; i < kPer; ++i) {
-    const uint64_t b = b0 + kPer * tid + i;
-    if (b < nblocks) x.bpre[b] = ex;
-    ex += v[i];
-  }
+  const uint32_t ex = block_exclusive_scan(v, scratch, &total);
+  if (tid < kXTileBlocks && b0 + tid < nblocks) x.bpre[b0 + tid] = ex;
   if (tid == 0) x.tpre[blockIdx.x] = total;
 }
 
 // Rank index, second level: exclusive prefix of the tile totals, in place (one CTA of 1024
-// threads, four tiles a thread: up to 2^32 positions).
+// threads, each a run of consecutive tiles: up to 2^32 positions).
 __global__ void __launch_bounds__(1024) xtiles_kernel(LevelArgs a, ExcArgs x) {
   __shared__ uint32_t scratch[33];
   if (a.ctrl[1]) return;
   const uint32_t tid = threadIdx.x;
   const uint64_t ntiles = ((x.n + kXBlock - 1u) / kXBlock + kXTileBlocks - 1u) / kXTileBlocks;
-  uint32_t v[4], sum = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < 4u; ++i) {
-    v[i] = (4u * tid + i < ntiles) ? x.tpre[4u * tid + i] : 0u;
-    sum += v[i];
-  }
+  const uint32_t per = static_cast<uint32_t>((ntiles + 1023u) / 1024u);
+  const uint64_t t0 = static_cast<uint64_t>(tid) * per;
+  uint32_t sum = 0;
+  for (uint32_t i = 0; i < per; ++i)
+    if (t0 + i < ntiles) sum += x.tpre[t0 + i];
   uint32_t total;
   uint32_t ex = block_exclusive_scan(sum, scratch, &total);
-#pragma unroll
-  for (uint32_t i = 0; i < 4u; ++i) {
-    if (4u * tid + i < ntiles) x.tpre[4u * tid + i] = ex;
-    ex += v[i];
+  for (uint32_t i = 0; i < per; ++i) {
+    if (t0 + i < ntiles) {
+      const uint32_t v = x.tpre[t0 + i];
+      x.tpre[t0 + i] = ex;
+      ex += v;
+    }
   }
 }
 

@@ -26,7 +26,7 @@ constexpr uint32_t kTileMaxDepth = 6u;        // tile kernel: at most 2^6 base b
 constexpr uint64_t kPairParityBytes = 1ull << 28;  // arrays from which a shuffle fixes its pass
                                                    // parity with a fused pair of levels
 constexpr uint32_t kXBlock = 1024u;       // positions per block of a pair's exception rank index
-constexpr uint32_t kXTileBlocks = 1024u;  // blocks per tile of that index (one CTA counts one)
+constexpr uint32_t kXTileBlocks = 128u;   // blocks per tile of that index (one CTA counts one)
 
 // Kernel classes timed by the optional profiler (MS_FLAG_PROFILE).
 enum KernelKind : int {
@@ -120,7 +120,7 @@ struct Plan {
   // plan sets): per-block zero counts (one byte per 128 coins), the exception bitmap (one bit
   // per element), the input index of each tail patch's element (by patch), the same indices in
   // position order (by rank), the rank index (exceptions before every 1024 positions within
-  // their tile of 2^20 positions, and before every tile), and, for every chunk of the pair's
+  // their tile of 2^17 positions, and before every tile), and, for every chunk of the pair's
   // second level, the record of the two ranges it reads (2 x 16 words)
   size_t off_zb = 0, off_xbits = 0, off_xsrc = 0, off_xval = 0, off_xbpre = 0, off_xtpre = 0;
   size_t off_xrange = 0;
