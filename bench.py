@@ -74,6 +74,9 @@ def parse():
                          "pairs of 4-byte levels)")
     ap.add_argument("--flags-rec", type=lambda x: int(x, 0), default=0,
                     help="MS_FLAG_* bits added to the records' resolved flags")
+    ap.add_argument("--unflags-perm", type=lambda x: int(x, 0), default=0,
+                    help="MS_FLAG_* bits removed from the perm's resolved flags (e.g. 0x80, "
+                         "the table's one-pass-a-level choice at 2^30)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: perm 2^26 + 2^24+17 records (inputs still above L2)")
     return ap.parse_args()
@@ -223,7 +226,7 @@ def run_ours(args, world, rank, local):
     fd_rec = args.fuse_depth if args.fuse_depth_rec is None else args.fuse_depth_rec
     p_perm = ms.resolve(n_perm, 4, B=args.B_perm, fuse_depth=fd_perm, tile_bytes=args.tile_bytes)
     p_rec = ms.resolve(n_rec, 16, B=args.B_rec, fuse_depth=fd_rec, tile_bytes=args.tile_bytes)
-    p_perm.flags |= args.flags_perm
+    p_perm.flags = (p_perm.flags | args.flags_perm) & ~args.unflags_perm
     p_rec.flags |= args.flags_rec
     prof_perm = ms.params(p_perm.B, p_perm.fuse_depth, p_perm.flags | ms.MS_FLAG_PROFILE,
                           p_perm.tile_bytes)

@@ -2031,13 +2031,15 @@ cudaError_t pair_data_t(const Plan &p, const LevelPlan &lv1, const LevelPlan &lv
   LevelArgs f1 = level_args(p, lv1, in, out, b1, seed);
   f1.gate = ovf;
   f1.gate_on = 1;
+  // (the fallback's gathers loop over their chunks on a resident grid: when gated off, as almost
+  // always, each costs one launch of a resident grid rather than one CTA a chunk)
   const uint64_t nchunks1 = static_cast<uint64_t>(lv1.M) * lv1.J;
-  gather_kernel<E><<<grid_for(nchunks1, 1, 1u << 20), kThreads, 0, s>>>(f1);
+  gather_kernel<E><<<grid_for(nchunks1, 1, kResident), kThreads, 0, s>>>(f1);
   tail_sequential_kernel<E><<<grid_for(lv1.M, kThreads, 1u << 16), kThreads, 0, s>>>(f1);
   LevelArgs f2 = level_args(p, lv2, out, X, b2, seed);
   f2.gate = ovf;
   f2.gate_on = 1;
-  gather_kernel<E><<<grid_for(nchunks2, 1, 1u << 20), kThreads, 0, s>>>(f2);
+  gather_kernel<E><<<grid_for(nchunks2, 1, kResident), kThreads, 0, s>>>(f2);
   // level l+1's tail, on out (fused) or on X (fallback)
   LevelArgs t2 = level_args(p, lv2, nullptr, out, b2, seed);
   t2.out_alt = X;
