@@ -44,7 +44,10 @@ extern "C" ms_status ms_perm_static(uint32_t *d_out, uint64_t n, uint64_t seed,
   size_t need = ms_workspace_bytes(n, 4, &q);
   if (need == 0) return MS_ERR_INVALID;
   if (need > kStaticBytes) {
-    // one data pass per level needs less plan scratch (the result is the same)
+    // one data pass per level needs less plan scratch (the result is the same). At this
+    // version's sizes fused pairs fit (16.0 MB at 2^21 with MS_FLAG_PAIR_LEVELS), so only a
+    // plan that grows reaches this; the literal, FDR and balanced-word plans do not fit either
+    // way at large n and return MS_ERR_UNSUPPORTED below.
     q.flags |= MS_FLAG_SINGLE_LEVELS;
     need = ms_workspace_bytes(n, 4, &q);
   }
