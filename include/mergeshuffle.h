@@ -30,8 +30,8 @@
  * (256-byte aligned); it holds the second ping-pong buffer of n*w bytes plus the plan scratch
  * of the merge levels (coin prefixes per 4096 steps, tail tables sized to the expected tails,
  * double-buffered so the next level is planned while one streams; fused level pairs add a
- * bitmap of n/8 bytes and an exception hash). Total device footprint: 2*n*w bytes + scratch
- * (the scratch is about 0.4*n*w for 4-byte elements at n = 2^30).
+ * bitmap of n/8 bytes, exception lists and per-chunk range records). Total device footprint:
+ * 2*n*w bytes + scratch (the scratch is about 0.4*n*w for 4-byte elements at n = 2^30).
  *
  * Streams. Each call enqueues on the caller's stream; the data-independent plan of the global
  * merge levels runs on a second stream at the caller's priority, paired with it (created on
