@@ -337,6 +337,16 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
 
     // ---- merge levels 0 .. d-1 of the tile (Algorithm 2)
     for (uint32_t lv = 0; lv < a.d; ++lv) {
+      if constexpr (!kPerm) {
+        if (lv + 1u == a.d) {
+          // the tile's input rows into L2 while the last level runs: its gather then reads them
+          // in a random order from L2 rather than from DRAM
+          const char *const rb = static_cast<const char *>(a.in) + g0 * sizeof(E);
+          const uint32_t nbytes = boff[nb] * static_cast<uint32_t>(sizeof(E));
+          for (uint32_t off = tid * 128u; off < nbytes; off += kTileThreads * 128u)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(rb + off));
+        }
+      }
       const uint16_t *const X = (lv & 1u) ? bufB : bufA;
       uint16_t *const Y = (lv & 1u) ? bufA : bufB;
       const uint32_t Sout = s_S[lv];
