@@ -220,8 +220,11 @@ size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *p);
 
 /*
  * Permute d_data[0..n) in place, uniformly at random (Algorithm 2 of the paper), stream-ordered.
- *   d_data  device pointer to n elements of w bytes (w in {4, 8, 16}); w-byte aligned
- *           (16-byte aligned for w = 16). Elements are moved as opaque w-byte records.
+ *   d_data  device pointer to n elements of w bytes (w in {1, 2, 4, 8, 16}); w-byte aligned
+ *           (16-byte aligned for w = 16). Elements are moved as opaque w-byte records. For
+ *           w = 1 and 2 the call builds ms_perm's permutation for the same (n, seed, B) in the
+ *           workspace (B = 0 resolves as for 4-byte elements), gathers the elements through it
+ *           and copies them back: the same result, a 4-byte perm's time plus two passes.
  *   n       0 <= n <= 2^32 - 1 (the paper's 32-bit n); n <= 1 returns MS_OK and launches
  *           nothing.
  *   seed    64-bit key of every Philox stream.

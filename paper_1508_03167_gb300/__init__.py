@@ -404,7 +404,7 @@ def workspace(n: int, w: int = 4, device=None, host: bool = False, **kw):
 
 def shuffle_(x, seed: int, B: int = 1024, fuse_depth: int = -1, flags: int = 0,
              tile_bytes: int = 0, ws=None, stream=None):
-    """Permute the rows of a contiguous CUDA tensor in place (rows of 4, 8 or 16 bytes)."""
+    """Permute the rows of a contiguous CUDA tensor in place (rows of 1, 2, 4, 8 or 16 bytes)."""
     n, w = _width(x)
     p = params(B, fuse_depth, flags, tile_bytes)
     if n == 0:

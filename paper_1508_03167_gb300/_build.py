@@ -21,7 +21,7 @@ LIB_NAME = "libmergeshuffle.so"
 LIB_PATH = os.path.join(BUILD_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ms_api.cu", "ms_leaf.cu", "ms_level.cu", "ms_static.cu", "ms_batch.cu", "ms_wlevel.cu",
-           "ms_tune.cu", "ms_span.cu", "ms_tile.cu", "ms_bits.cu", "ms_rs.cu"]
+           "ms_tune.cu", "ms_span.cu", "ms_tile.cu", "ms_bits.cu", "ms_rs.cu", "ms_narrow.cu"]
 
 _lock = threading.Lock()
 

@@ -610,7 +610,46 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
 }
 
 ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
+              size_t ws_bytes, const ms_params *params, cudaStream_t s);
+
+// 1- and 2-byte elements: the permutation ms_perm gives for (n, seed, B) into the front of the
+// workspace, the elements gathered through it into the 4-byte path's ping-pong buffer, then
+// copied back (a shuffle is its input gathered through that permutation, whatever the width).
+ms_status run_narrow(void *data, uint64_t n, uint32_t w, uint64_t seed, void *ws,
+                     size_t ws_bytes, const ms_params *params, cudaStream_t s) {
+  ms_params pp;
+  ms_default_params(&pp);
+  if (params) pp = *params;
+  pp = msk::resolve_single(n, w, &pp);  // (narrow widths resolve as 4-byte elements)
+  Plan p4;
+  ms_params pp4 = pp;
+  pp4.flags |= MS_FLAG_PERM;
+  const ms_status ps = plan_for(n, 4, &pp4, &p4);
+  if (ps != MS_OK) return ps;
+  if (n <= 1) return MS_OK;
+  const size_t need = ms_workspace_bytes(n, w, &pp);
+  if (need == 0) return MS_ERR_INVALID;
+  if (data == nullptr || reinterpret_cast<uintptr_t>(data) % w != 0) return MS_ERR_INVALID;
+  if (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+    return MS_ERR_INVALID;
+  const size_t front = msk::round_up(n * 4u, 256);
+  uint32_t *const idx = static_cast<uint32_t *>(ws);
+  char *const inner = static_cast<char *>(ws) + front;
+  const ms_status st = run(idx, true, n, 4, seed, inner, ws_bytes - front, &pp, s);
+  if (st != MS_OK) return st;
+  void *const tmp = inner + p4.off_buf;  // n * 4 bytes, free once the permutation is written
+  int dev = 0, sms = 0;
+  if (failed(cudaGetDevice(&dev)) ||
+      failed(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+    return MS_ERR_CUDA;
+  if (failed(msk::launch_narrow_gather(data, idx, tmp, n, w, sms, s))) return MS_ERR_CUDA;
+  if (failed(cudaMemcpyAsync(data, tmp, n * w, cudaMemcpyDeviceToDevice, s))) return MS_ERR_CUDA;
+  return MS_OK;
+}
+
+ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
               size_t ws_bytes, const ms_params *params, cudaStream_t s) {
+  if (!perm && (w == 1 || w == 2)) return run_narrow(data, n, w, seed, ws, ws_bytes, params, s);
   Plan p;
   ms_params pp;
   ms_default_params(&pp);
@@ -738,6 +777,7 @@ constexpr uint32_t kBatchSideStreams = 4;
 ms_status batch_layout(uint32_t k, const uint64_t *h_n, uint32_t w, const ms_params *params,
                        BatchLayout *L) {
   const ms_params r = msk::resolve_batch(k, h_n, w, params);
+  if (w == 1 || w == 2) return MS_ERR_UNSUPPORTED;  // (the single call takes them)
   if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
   if ((r.flags & MS_FLAG_PERM) && w != 4) return MS_ERR_INVALID;
   if (r.flags & (MS_FLAG_LITERAL | MS_FLAG_FDR | MS_FLAG_BALANCED)) return MS_ERR_UNSUPPORTED;
@@ -1015,6 +1055,12 @@ ms_status ms_profile_read(ms_profile *out, int reset) {
 }
 
 size_t ms_workspace_bytes(uint64_t n, uint32_t w, const ms_params *params) {
+  // 1- and 2-byte elements: the permutation's indices, then the 4-byte path's workspace (whose
+  // ping-pong buffer later holds the gathered elements)
+  if (w == 1 || w == 2) {
+    const size_t inner = ms_workspace_bytes(n, 4, params);
+    return inner ? msk::round_up(n * 4u, 256) + inner : 0;
+  }
   // enough for ms_shuffle and (w = 4) ms_perm, whose plans may differ in how the levels after
   // the base-block pass are grouped
   ms_params pp;

@@ -168,6 +168,10 @@ struct Buffers {
   uint32_t *zlab;    // balanced-word merge: zeros before each chunk of labels
 };
 
+// 1- and 2-byte elements (w): tmp[i] = data[idx[i]] for i < n (ms_narrow.cu).
+cudaError_t launch_narrow_gather(const void *data, const uint32_t *idx, void *tmp, uint64_t n,
+                                 uint32_t w, int sms, cudaStream_t s);
+
 // Lets `kern` launch with `smem` bytes of dynamic shared memory. The attribute is process-wide,
 // so every caller sets the same value (the device's opt-in maximum less the kernel's static
 // shared memory): threads launching the same kernel with different sizes never lower it under

@@ -95,7 +95,7 @@ ms_params resolve_single(uint64_t n, uint32_t w, const ms_params *p) {
   ms_default_params(&r);
   if (p) r = *p;
   if (r.B == 0) {
-    apply(lookup(n, w, 0), &r);
+    apply(lookup(n, w < 4u ? 4u : w, 0), &r);  // (1- and 2-byte elements run a 4-byte perm)
     r.B = block_for(n, r.B);
   }
   return r;
@@ -126,7 +126,7 @@ extern "C" {
 
 ms_status ms_resolve_params(uint64_t n, uint32_t w, ms_params *inout) {
   if (!inout) return MS_ERR_INVALID;
-  if (w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
+  if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16) return MS_ERR_INVALID;
   *inout = msk::resolve_single(n, w, inout);
   return MS_OK;
 }

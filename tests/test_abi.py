@@ -131,6 +131,23 @@ def test_invalid_arguments_are_rejected_synchronously(n, w, B, status):
     assert ms.ms_shuffle(0x1000, n, w, 1, 0, 0, ms.params(B=B), 0) == status
 
 
+@pytest.mark.parametrize("w", [1, 2])
+def test_narrow_widths_size_and_validate_as_a_4_byte_perm(w):
+    """1- and 2-byte elements run the 4-byte perm of the same (n, seed, B), then gather through
+    it: their workspace is the indices plus the 4-byte workspace, B = 0 resolves as for 4 bytes,
+    and bad arguments get the 4-byte path's status."""
+    n = 1000003
+    p = ms.params(B=64)
+    assert ms.ms_workspace_bytes(n, w, p) == ((4 * n + 255) // 256) * 256 + \
+        ms.ms_workspace_bytes(n, 4, p)
+    assert ms.resolve(n, w, B=0).B == ms.resolve(n, 4, B=0).B
+    assert ms.ms_shuffle(0x1000, n, w, 1, 0, 0, ms.params(B=5000), 0) == ms.MS_ERR_UNSUPPORTED
+    assert ms.ms_shuffle(0x1000, 2**32, w, 1, 0, 0, ms.params(B=16), 0) == ms.MS_ERR_INVALID
+    need = ms.ms_workspace_bytes(n, w, p)
+    assert ms.ms_shuffle(0x1000, n, w, 1, 0x10000, need - 1, p, 0) == ms.MS_ERR_INVALID
+    assert ms.ms_shuffle(0, 1, w, 1, 0, 0, None, 0) == ms.MS_OK
+
+
 def test_small_workspace_is_rejected():
     need = ms.ms_workspace_bytes(10**6, 4, ms.params(B=64))
     assert ms.ms_shuffle(0x1000, 10**6, 4, 1, 0x10000, need - 1, ms.params(B=64), 0) == \

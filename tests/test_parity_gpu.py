@@ -185,6 +185,10 @@ def test_fused_level_pairs_wide_elements(w):
     assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=pl), want)
     assert np.array_equal(gpu_shuffle(arr, 9, B, fuse_depth=0, flags=ms.MS_FLAG_SINGLE_LEVELS),
                           want)
+    # the device-side unfused fallback of every pair (forced by the sequential-tail flag)
+    assert np.array_equal(
+        gpu_shuffle(arr, 9, B, fuse_depth=0,
+                    flags=pl | ms.MS_FLAG_GLOBAL_LEVELS | ms.MS_FLAG_TAIL_SEQUENTIAL), want)
 
 
 def test_concurrent_calls_on_two_streams_from_two_threads():
