@@ -307,12 +307,13 @@ __global__ void __launch_bounds__(128) fy_fdr_kernel(const E *in, E *out, uint64
   }
 }
 
-// The same pass out of place on eight-warp CTAs, 16-bit local indices in shared memory (stride
-// P = 2 mod 64 a block), a batch of `lanes` consecutive base blocks at a time (block k of the
-// batch on lane k): all eight warps make the draws (warp w: quads w, w + 8, ... of every block;
-// one Philox block serves a quad's four first words, and a draw that needs more than its first
-// word is queued by its thread and redone from word 0 after the loop), warp 0 runs the swap
-// chains, and a warp per block writes it through the indices.
+// Algorithm 1 on every base block out of place, on eight-warp CTAs with 16-bit local indices in
+// shared memory (stride P = 2 mod 64 a block), a batch of `lanes` consecutive base blocks at a
+// time (block k of the batch on lane k): all eight warps make the draws (warp w: quads w, w + 8,
+// ... of every block; one Philox block serves a quad's four first words, and a draw that needs
+// more than its first word is queued by its thread and finished after the loop), warp 0 runs
+// the swap chains, and a warp per block writes it through the indices. kFdr selects the Fast
+// Dice Roller draws (MS_FLAG_FDR), else the rejection draws of the other kernels.
 constexpr uint32_t kFdrWarps = 8u;
 constexpr uint32_t kFdrThreads = 32u * kFdrWarps;
 constexpr uint32_t kFdrFail = 8u;  // queued draws a thread
@@ -336,16 +337,27 @@ __device__ __forceinline__ bool fdr_first_word(uint32_t word, uint32_t R, uint32
   return false;
 }
 
+// The whole draw of position pos of block id (from word 0 of its stream on).
+template <bool kFdr>
+__device__ __forceinline__ uint32_t fy8_draw(uint2 key, uint32_t id, uint32_t pos) {
+  if constexpr (kFdr) {
+    uint32_t nb;
+    return draw_fdr(key, kTagLeaf, 0u, id, pos, pos + 1u, &nb);
+  } else {
+    return draw_continue(key, kTagLeaf, 0u, id, pos, pos + 1u);
+  }
+}
+
 __device__ __forceinline__ void swap16(uint16_t *A, uint32_t i, uint32_t j) {
   const uint16_t t = A[i];
   A[i] = A[j];
   A[j] = t;
 }
 
-template <typename E, bool kPerm>
-__global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *out, uint64_t n,
-                                                             uint32_t c, uint2 key, uint32_t P,
-                                                             uint32_t lanes) {
+template <typename E, bool kPerm, bool kFdr>
+__global__ void __launch_bounds__(kFdrThreads) fy8_kernel(const E *in, E *out, uint64_t n,
+                                                         uint32_t c, uint2 key, uint32_t P,
+                                                         uint32_t lanes) {
   extern __shared__ __align__(16) uint16_t fdr_smem[];
   uint16_t *const Abuf = fdr_smem;
   uint16_t *const Dbuf = fdr_smem + lanes * P;
@@ -371,6 +383,10 @@ __global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *ou
 #pragma unroll 2
       for (uint32_t qd = warp; qd < nq; qd += kFdrWarps) {
         const uint4 blk = philox10(make_uint4(qd, id, kTagLeaf << 16, 0u), key);
+        // (rejection draws: the slice width of the quad's ranges; positions 1..3 of quad 0 take
+        // the general draw)
+        const uint32_t qb = 32u - __clz(4u * qd + 1u);
+        const uint32_t qmask = 0xFFFFFFFFu >> (32u - qb);
 #pragma unroll
         for (uint32_t v = 0; v < 4u; ++v) {
           const uint32_t pos = 4u * qd + v;
@@ -378,13 +394,20 @@ __global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *ou
             A[pos] = static_cast<uint16_t>(pos);
             if (pos >= 1u) {
               uint32_t x;
-              if (fdr_first_word(pick_word(blk, v), pos + 1u, x)) {
+              const uint32_t word = pick_word(blk, v);
+              bool ok;
+              if constexpr (kFdr) {
+                ok = fdr_first_word(word, pos + 1u, x);
+              } else {
+                ok = qd ? draw_first_word_b(word, pos + 1u, qb, qmask, 2u * qb, 3u * qb, x)
+                        : draw_first_word(word, pos + 1u, x);
+              }
+              if (ok) {
                 D[pos] = static_cast<uint16_t>(x);
               } else if (nf < kFdrFail) {
                 Fq[nf++] = static_cast<uint16_t>(pos);
               } else {
-                uint32_t nb;
-                D[pos] = static_cast<uint16_t>(draw_fdr(key, kTagLeaf, 0u, id, pos, pos + 1u, &nb));
+                D[pos] = static_cast<uint16_t>(fy8_draw<kFdr>(key, id, pos));
               }
             }
           }
@@ -392,8 +415,7 @@ __global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *ou
       }
       for (uint32_t e = 0; e < nf; ++e) {
         const uint32_t pos = Fq[e];
-        uint32_t nb;
-        D[pos] = static_cast<uint16_t>(draw_fdr(key, kTagLeaf, 0u, id, pos, pos + 1u, &nb));
+        D[pos] = static_cast<uint16_t>(fy8_draw<kFdr>(key, id, pos));
       }
     }
     __syncthreads();
@@ -451,15 +473,17 @@ __global__ void __launch_bounds__(kFdrThreads) fy_fdr8_kernel(const E *in, E *ou
 template <typename E, bool kPerm>
 cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t seed,
                           cudaStream_t s) {
-  if (p.flags & MS_FLAG_FDR) {
-    // Algorithm 1 with the Fast Dice Roller draws
+  const bool fdr = (p.flags & MS_FLAG_FDR) != 0;
+  // Algorithm 1 alone (no fused levels), out of place, or with the Fast Dice Roller draws: the
+  // eight-warp kernel
+  if (fdr || (p.d == 0 && p.fy_per_cta > 0 && (kPerm || in != out))) {
     const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
     uint32_t P = p.leaf_max + 2u;  // (a base block has at most leaf_max elements)
     while (P % 64u != 2u) ++P;
     constexpr uint32_t kBudget = 132u * 1024u;  // index and draw regions (two of P entries a lane)
     const uint32_t lanes = std::max<uint32_t>(1u, std::min<uint32_t>(32u, kBudget / (4u * P)));
     if (!kPerm && in == out) {
-      // in place: one thread per base block copies nothing and swaps in the array
+      // (FDR draws) in place: one thread per base block copies nothing and swaps in the array
       const uint64_t grid = std::min<uint64_t>((p.q + 127u) / 128u, 1048576ull);
       if (p.prof) p.prof->begin(kKindLeaf, s);
       fy_fdr_kernel<E, kPerm><<<static_cast<unsigned>(grid), 128, 0, s>>>(
@@ -468,7 +492,7 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
       return cudaGetLastError();
     }
     const size_t smem = (2u * static_cast<size_t>(lanes) * P + kFdrThreads * kFdrFail) * 2u;
-    auto fk = fy_fdr8_kernel<E, kPerm>;
+    auto fk = fdr ? fy8_kernel<E, kPerm, true> : fy8_kernel<E, kPerm, false>;
     cudaError_t e = allow_dynamic_smem(fk, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
