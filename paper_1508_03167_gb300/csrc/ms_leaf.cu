@@ -248,38 +248,6 @@ __global__ void __launch_bounds__(32) fy_index_kernel(LeafArgs a, uint32_t per_c
   }
 }
 
-// Fisher-Yates only for perm (d = 0): the identity of a base block is its start b plus a local
-// index, so the lane of each block shuffles 16-bit local indices (half the shared memory of
-// 32-bit values, twice the warps per SM) and the warp writes b + idx[i].
-__global__ void __launch_bounds__(32) fy_perm16_kernel(LeafArgs a, uint32_t per_cta) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint16_t *const idx = reinterpret_cast<uint16_t *>(smem_raw);
-  uint32_t *out = static_cast<uint32_t *>(a.out);
-  const uint32_t lane = threadIdx.x;
-  const uint32_t P = a.stride;
-  const uint64_t groups = (a.q + per_cta - 1) / per_cta;
-  for (uint64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
-    const uint64_t lb = gidx * per_cta;
-    const uint32_t cnt = static_cast<uint32_t>(a.q - lb < per_cta ? a.q - lb : per_cta);
-    if (lane < cnt) {
-      const uint64_t leaf = lb + lane;
-      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, leaf + 1) -
-                                               boundary(a.n, a.c, leaf));
-      uint16_t *blk = idx + lane * P;
-      for (uint32_t i = 0; i < L; ++i) blk[i] = static_cast<uint16_t>(i);
-      fisher_yates_block(blk, L, static_cast<uint32_t>(leaf), a.key);
-    }
-    __syncwarp();
-    for (uint32_t k = 0; k < cnt; ++k) {
-      const uint64_t bs = boundary(a.n, a.c, lb + k);
-      const uint32_t L = static_cast<uint32_t>(boundary(a.n, a.c, lb + k + 1) - bs);
-      const uint16_t *blk = idx + k * P;
-      for (uint32_t i = lane; i < L; i += 32u) out[bs + i] = static_cast<uint32_t>(bs) + blk[i];
-    }
-    __syncwarp();
-  }
-}
-
 // Algorithm 1 on every base block with uniform draws by the Fast Dice Roller (MS_FLAG_FDR): one
 // thread per block copies it to the output (a perm writes its positions) and swaps there, in
 // order, i = L-1 .. 1 with j from stream (LEAF, 0, block, i). The output is out of place or the
@@ -530,21 +498,6 @@ cudaError_t launch_leaf_t(const Plan &p, const void *in, void *out, uint64_t see
     auto fk = fy_index_kernel<E>;
     const uint32_t per = 32;
     const size_t smem = static_cast<size_t>(per) * p.leaf_stride * sizeof(uint32_t);
-    cudaError_t e2 = allow_dynamic_smem(fk, smem);
-    if (e2 != cudaSuccess) return e2;
-    const uint64_t groups = (p.q + per - 1) / per;
-    const uint64_t grid = groups < 1048576ull ? groups : 1048576ull;
-    if (p.prof) p.prof->begin(kKindLeaf, s);
-    fk<<<static_cast<unsigned>(grid), 32, smem, s>>>(a, per);
-    if (p.prof) p.prof->end(s);
-    return cudaGetLastError();
-  }
-  if (p.d == 0 && p.fy_per_cta > 0 && kPerm && p.leaf_max < 65536u) {
-    auto fk = fy_perm16_kernel;
-    // up to 32 blocks (one per lane) within 96 KiB of shared memory
-    const uint64_t fit = (96ull * 1024) / (static_cast<uint64_t>(p.leaf_stride) * 2u);
-    const uint32_t per = static_cast<uint32_t>(fit < 1 ? 1 : (fit > 32 ? 32 : fit));
-    const size_t smem = (static_cast<size_t>(per) * p.leaf_stride * sizeof(uint16_t) + 15) & ~15ull;
     cudaError_t e2 = allow_dynamic_smem(fk, smem);
     if (e2 != cudaSuccess) return e2;
     const uint64_t groups = (p.q + per - 1) / per;
