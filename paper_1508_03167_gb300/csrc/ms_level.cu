@@ -97,6 +97,11 @@ __device__ __forceinline__ uint32_t block_zero_count(const uint4 &c, uint32_t bl
   return z;
 }
 
+// chunks of kChunk steps in N steps (N may be close to 2^32: no rounding sum)
+__device__ __forceinline__ uint32_t chunks_of(uint32_t N) {
+  return N / kChunk + ((N % kChunk) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------- count ---------
 __global__ void __launch_bounds__(kThreads) count_kernel(LevelArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(LevelArgs a) {
     const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t n2 = N - n1;
-    const uint32_t J = (N + kChunk - 1u) / kChunk;  // chunks of this merge (<= a.J)
+    const uint32_t J = chunks_of(N);  // chunks of this merge (<= a.J)
     uint32_t *zc = a.zc + static_cast<uint64_t>(r) * a.J;
     if (threadIdx.x == 0) {
       s_zchunk = kNone;
@@ -466,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(LevelArgs a) {
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N) continue;  // uniform across the CTA
-    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint32_t t1 = t0 + min(kChunk, N - t0);  // (t0 < N; no 32-bit overflow)
     const uint4 mi = a.minfo[r];
     const uint32_t T = mi.x;
     const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(kStageThreads) gather_staged_kernel(LevelArgs 
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N) continue;  // uniform across the CTA
-    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint32_t t1 = t0 + min(kChunk, N - t0);  // (t0 < N; no 32-bit overflow)
     const uint32_t len = t1 - t0;
     const uint4 mi = a.minfo[r];
     const uint32_t T = mi.x;
@@ -604,7 +609,7 @@ __global__ void __launch_bounds__(kStageThreads) gather_staged_kernel(LevelArgs 
     } else {
       const uint32_t Z0 = a.zc[cid];
       Tc = min(t1, T) - t0;
-      const uint32_t Jr = (N + kChunk - 1u) / kChunk;
+      const uint32_t Jr = chunks_of(N);
       zT = (t1 <= T) ? ((j + 1u < Jr) ? a.zc[cid + 1] - Z0 : n1 - Z0) : mi.y - Z0;
       za = Z0;
       ob = t0 - Z0;
@@ -960,7 +965,7 @@ __global__ void __launch_bounds__(kThreads) pair_ranges_kernel(PairArgs pa) {
     const uint32_t t0 = j * kChunk;
     rg[kRgMerge] = 2u * R + h;
     if (t0 < N2) {
-      const uint32_t t1 = min(t0 + kChunk, N2);
+      const uint32_t t1 = t0 + min(kChunk, N2 - t0);  // (t0 < N2; no 32-bit overflow)
       const uint32_t len = t1 - t0;
       const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);
       const uint32_t h2 = N2 - h1;
@@ -975,7 +980,7 @@ __global__ void __launch_bounds__(kThreads) pair_ranges_kernel(PairArgs pa) {
       } else {
         const uint32_t Z0 = a2.zc[cid];
         Tc2 = min(t1, T2) - t0;
-        const uint32_t Jr = (N2 + kChunk - 1u) / kChunk;
+        const uint32_t Jr = chunks_of(N2);
         zT2 = (t1 <= T2) ? ((j + 1u < Jr) ? a2.zc[cid + 1] - Z0 : h1 - Z0) : mi2.y - Z0;
         lo = h ? t0 - Z0 : Z0;
       }
@@ -1050,13 +1055,15 @@ __device__ __forceinline__ void load_range_bits(const ExcArgs &x, uint32_t g_lo,
                                                 uint32_t *xb, uint32_t t, uint32_t nt) {
   const uint64_t nwords = (x.n + 31u) >> 5;
   const uint32_t w0 = g_lo >> 5;
-  const uint32_t nw = cnt ? ((g_lo + cnt + 31u) >> 5) - w0 : 0u;
+  const uint32_t nw =
+      cnt ? static_cast<uint32_t>((static_cast<uint64_t>(g_lo) + cnt + 31u) >> 5) - w0 : 0u;
   for (uint32_t wi = t; wi < nw && wi < kPairW; wi += nt) {
     const uint64_t bw = static_cast<uint64_t>(w0) + wi;
     uint32_t v = bw < nwords ? x.bits[bw] : 0u;
     const uint32_t ws = (w0 + wi) << 5;  // first position of the word
     const uint32_t lo_b = g_lo > ws ? g_lo - ws : 0u;
-    const uint32_t hi_b = min(g_lo + cnt - ws, 32u);
+    const uint32_t hi_b = static_cast<uint32_t>(
+        min(static_cast<uint64_t>(g_lo) + cnt - ws, static_cast<uint64_t>(32u)));
     xb[wi] = v & low_mask(hi_b) & ~low_mask(lo_b);
   }
 }
@@ -1083,7 +1090,10 @@ __device__ __forceinline__ void range_word_prefix(const uint32_t *xb, uint32_t n
 }
 
 __device__ __forceinline__ uint32_t range_words(uint32_t g_lo, uint32_t cnt) {
-  return cnt ? min(((g_lo + cnt + 31u) >> 5) - (g_lo >> 5), kPairW) : 0u;
+  return cnt ? min(static_cast<uint32_t>((static_cast<uint64_t>(g_lo) + cnt + 31u) >> 5) -
+                       (g_lo >> 5),
+                   kPairW)
+             : 0u;
 }
 
 // The data pass of a fused pair for 8- and 16-byte elements: a CTA takes 4096 outputs of level
@@ -1121,7 +1131,7 @@ __global__ void __launch_bounds__(kThreads, 5) pair_gather_kernel(PairArgs pa) {
     const uint32_t N2 = static_cast<uint32_t>(mb2.e - mb2.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N2) continue;  // uniform across the CTA
-    const uint32_t t1 = min(t0 + kChunk, N2);
+    const uint32_t t1 = t0 + min(kChunk, N2 - t0);  // (t0 < N2; no 32-bit overflow)
     const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);  // level l+1's first half
     const uint32_t h2 = N2 - h1;
     const uint4 mi2 = a2.minfo[R];
@@ -1456,7 +1466,7 @@ __global__ void __launch_bounds__(kThreads) label_kernel(LevelArgs a, uint8_t *l
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N) continue;  // uniform across the CTA
-    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint32_t t1 = t0 + min(kChunk, N - t0);  // (t0 < N; no 32-bit overflow)
     const uint4 mi = a.minfo[r];
     const uint32_t T = mi.x;
     const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
@@ -1491,9 +1501,9 @@ __global__ void __launch_bounds__(kThreads) label_count_kernel(LevelArgs a, cons
     const MergeBounds mb = merge_bounds(a, r);
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t t0 = j * kChunk;
-    const uint32_t t1 = min(t0 + kChunk, N);
+    const uint32_t len = t0 < N ? min(kChunk, N - t0) : 0u;
     uint32_t z = 0;
-    for (uint32_t t = t0 + lane; t < t1; t += 32u) z += lab[mb.s + t] == 0u ? 1u : 0u;
+    for (uint32_t k = lane; k < len; k += 32u) z += lab[mb.s + t0 + k] == 0u ? 1u : 0u;
     z = warp_sum(z);
     if (lane == 0) zl[cid] = z;
   }
@@ -1539,7 +1549,7 @@ __global__ void __launch_bounds__(kStageThreads) word_gather_kernel(LevelArgs a,
     const uint32_t N = static_cast<uint32_t>(mb.e - mb.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N) continue;  // uniform across the CTA
-    const uint32_t len = min(t0 + kChunk, N) - t0;
+    const uint32_t len = min(kChunk, N - t0);
     const uint32_t n1 = static_cast<uint32_t>(mb.mid - mb.s);
     const uint32_t n2 = N - n1;
     // the chunk's words: bit = label (1: second half). Thread k builds word k from its 32 label
@@ -1638,7 +1648,7 @@ __global__ void __launch_bounds__(kStageThreads, 6) pair_staged_kernel(PairArgs 
     const uint32_t N2 = static_cast<uint32_t>(mb2.e - mb2.s);
     const uint32_t t0 = j * kChunk;
     if (t0 >= N2) continue;  // uniform across the CTA
-    const uint32_t t1 = min(t0 + kChunk, N2);
+    const uint32_t t1 = t0 + min(kChunk, N2 - t0);  // (t0 < N2; no 32-bit overflow)
     const uint32_t len = t1 - t0;
     const uint32_t h1 = static_cast<uint32_t>(mb2.mid - mb2.s);  // level l+1's first half
     const uint32_t h2 = N2 - h1;
@@ -1650,7 +1660,7 @@ __global__ void __launch_bounds__(kStageThreads, 6) pair_staged_kernel(PairArgs 
     if (t0 < T2) {
       const uint32_t Z0 = a2.zc[cid];
       Tc2 = min(t1, T2) - t0;
-      const uint32_t Jr = (N2 + kChunk - 1u) / kChunk;
+      const uint32_t Jr = chunks_of(N2);
       zT2 = (t1 <= T2) ? ((j + 1u < Jr) ? a2.zc[cid + 1] - Z0 : h1 - Z0) : mi2.y - Z0;
     }
     (void)h2;
@@ -1791,7 +1801,7 @@ __global__ void __launch_bounds__(kStageThreads, 6) pair_staged_kernel(PairArgs 
             const uint32_t h = e < c0 ? 0u : 1u;
             const uint32_t k = h ? e - c0 : e;
             // the word holding it: the last word whose prefix is <= k
-            const uint32_t nxw = min(((hs[h][10] + hs[h][1] + 31u) >> 5) - (hs[h][10] >> 5), kPairW);
+            const uint32_t nxw = range_words(hs[h][10], hs[h][1]);
             uint32_t lo = 0, hi = nxw;
             while (hi - lo > 1u) {
               const uint32_t mid = (lo + hi) >> 1;

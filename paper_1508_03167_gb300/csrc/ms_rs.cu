@@ -312,12 +312,15 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
       const uint32_t nlast = static_cast<uint32_t>(a.n - 1u);
       uint32_t j = 0;
       uint4 g = m ? sg[0] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
-      for (uint32_t p0 = lo32 + tid; p0 < hi32; p0 += kU * kRsThreads) {
+      // (offsets from lo32 within the span stay below 4096: no 32-bit overflow near n = 2^32)
+      const uint32_t span = hi32 - lo32;
+      for (uint32_t o0 = tid; o0 < span; o0 += kU * kRsThreads) {
+        const uint32_t p0 = lo32 + o0;
         E v[kU];
 #pragma unroll
         for (uint32_t u = 0; u < kU; ++u) {
           const uint32_t p = p0 + u * kRsThreads;
-          if (p < hi32) {
+          if (o0 + u * kRsThreads < span) {
             if constexpr (kPerm) v[u] = static_cast<E>(p);
             else v[u] = in[p];
           }
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 #pragma unroll
         for (uint32_t u = 0; u < kU; ++u) {
           const uint32_t p = p0 + u * kRsThreads;
-          if (p >= hi32) break;
+          if (o0 + u * kRsThreads >= span) break;
           while (g.y <= p && j < m) {
             ++j;
             g = j < m ? sg[j] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);

@@ -19,9 +19,11 @@ table still resolves them so, so the digests stay tied to what the benchmark run
                  in [10^6, 10^8]), seed 1 + i, B = 256: the largest instance and a small one
   rs_perm        the splitting process (Rao-Sandelius, Fisher-Yates cutoff B) on 2^30 positions,
                  seed 7, B = 512: the comparison workload's perm
+  max_perm       perm(2^32 - 1), seed 3, B = 511: the largest n the boundary takes (positions
+                 near 2^32 exercise every 32-bit index of the GPU path)
 
-Run:  python tests/golden/make_fullsize_digests.py [name ...]   (all rows: about 16 minutes on
-one core, ~20 GB RAM; with names, only those rows are recomputed and the others kept)
+Run:  python tests/golden/make_fullsize_digests.py [name ...]   (all rows: about 30 minutes on
+one core, ~34 GB RAM; with names, only those rows are recomputed and the others kept)
 """
 from __future__ import annotations
 
@@ -57,6 +59,7 @@ C2B = dict(name="c2b_records", n=300_000_017, w=16, seed=7, B=572)
 C3_B = 256
 C4_B = 256
 RS = dict(name="rs_perm", n=1 << 30, w=4, seed=7, B=512)
+MAX = dict(name="max_perm", n=(1 << 32) - 1, w=4, seed=3, B=511)
 
 
 def sha(a: np.ndarray) -> str:
@@ -78,7 +81,7 @@ def main(only: set[str]) -> None:
         rows[name] = f"{name} {n} {w} {seed} {B} {digest}"
         print(f"{name}: n={n} w={w} seed={seed} B={B} {digest} ({dt:.1f} s)", flush=True)
 
-    for cfg in (C1, C2A):
+    for cfg in (C1, C2A, MAX):
         if not want(cfg["name"]):
             continue
         t = time.time()

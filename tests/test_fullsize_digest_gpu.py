@@ -163,3 +163,22 @@ def test_rao_sandelius_perm_2p30_digest():
     assert _sha_device(out) == g["digest"]
     del out
     torch.cuda.empty_cache()
+
+
+def test_max_size_perm_digest():
+    """n = 2^32 - 1, the largest n the boundary takes, at its tuned plan (the tile kernel, then
+    18 global levels): every 32-bit position and index of the path near its limit. The result
+    is hashed from the device in 1 GiB slices."""
+    import torch
+
+    g = _digests()["max_perm"]
+    p = ms.resolve(g["n"], 4, B=0)
+    assert p.B == g["B"], "the tuning table no longer resolves perm(2^32 - 1) to the pinned B"
+    out = _perm(torch, g["n"], g["seed"], p)
+    h = hashlib.sha256()
+    step = 1 << 28
+    for i in range(0, g["n"], step):
+        h.update(out[i:i + step].cpu().numpy())
+    assert h.hexdigest() == g["digest"]
+    del out
+    torch.cuda.empty_cache()
