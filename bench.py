@@ -440,7 +440,7 @@ def run_ours(args, world, rank, local):
             fb.result()
 
         e2e_step()
-        k2 = max(2, min(args.steps, 5))
+        k2 = max(2, min(args.steps, 10))
         barrier(world)
         t0 = time.perf_counter()
         each = []
