@@ -20,9 +20,9 @@
 //           bit is 0, else to s + z + (p - s) - (Z_p - Z_s); every other position is copied.
 // After the planned levels (an odd number, so that the last one writes the workspace buffer)
 // the host reads whether a segment above B is left and runs further pairs of levels if so.
-// The Fisher-Yates pass takes the final segments from the boundary bitmap: one lane per
-// segment shuffles its 16-bit local indices in shared memory, then the warp writes the segment
-// to the caller's buffer through them.
+// The Fisher-Yates pass takes the final segments from the boundary bitmap in batches of 32 on
+// eight-warp CTAs: all warps make the draws, one lane per segment runs its swap chain on 16-bit
+// local indices in shared memory, and a warp per segment writes it through them.
 #include <algorithm>
 
 #include "mergeshuffle.h"
