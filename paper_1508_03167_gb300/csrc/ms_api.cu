@@ -3,9 +3,12 @@
 // of how many low merge levels run inside shared memory, and the workspace layout.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "mergeshuffle.h"
 #include "ms_plan.h"
@@ -612,6 +615,15 @@ ms_status plan_stream(cudaStream_t caller, PlanStream **out) {
 ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void *ws,
               size_t ws_bytes, const ms_params *params, cudaStream_t s);
 
+// An NVTX range over the enqueue of one call or one of its passes (a no-op unless a profiler
+// such as Nsight Systems is attached), so a timeline shows which pass launched which kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // 1- and 2-byte elements: the permutation ms_perm gives for (n, seed, B) into the front of the
 // workspace, the elements gathered through it into the 4-byte path's ping-pong buffer, then
 // copied back (a shuffle is its input gathered through that permutation, whatever the width).
@@ -720,14 +732,22 @@ ms_status run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, void
     for (uint32_t u = 0; u < nu && u < slots; ++u)
       if (!plan_on_side(u)) return MS_ERR_CUDA;
   }
+  NvtxRange call_range(perm ? "ms_perm" : "ms_shuffle");
   void *cur = (p.hbm_passes % 2 == 0) ? data : b0.other;
-  if (failed(msk::launch_leaf(p, data, cur, perm, seed, s))) return MS_ERR_CUDA;
+  {
+    NvtxRange r(p.d > 0 ? "base blocks and fused levels" : "base blocks");
+    if (failed(msk::launch_leaf(p, data, cur, perm, seed, s))) return MS_ERR_CUDA;
+  }
   uint32_t u = 0;  // next global unit
   for (uint32_t i = 0; i < p.nlevels; ++i) {
     const msk::LevelPlan &lv = p.levels[i];
     if (lv.pair == 2) continue;  // done with the pair's first level
     void *dst = (cur == data) ? b0.other : data;
     cudaError_t e = cudaSuccess;
+    char label[48];
+    std::snprintf(label, sizeof label, lv.pair == 1 ? "levels %u-%u" : "level %u", lv.level,
+                  lv.level + 1u);
+    NvtxRange level_range(label);
     if (lv.span) {
       e = msk::launch_span_level(p, lv, cur, dst, seed, s);
     } else if (lv.warp_local) {
