@@ -18,6 +18,9 @@
 //           single-CTA scan, write), and a split point s + z is marked in the boundary bitmap;
 //           the data pass then sends position p of an active segment to s + (Z_p - Z_s) if its
 //           bit is 0, else to s + z + (p - s) - (Z_p - Z_s); every other position is copied.
+//           One CTA takes one chunk (the hardware balances the chunks over the SMs); for
+//           elements up to 8 bytes it copies the chunk's rows into shared memory (cp.async)
+//           while it sets up the chunk's bits and segments.
 // After the planned levels (an odd number, so that the last one writes the workspace buffer)
 // the host reads whether a segment above B is left and runs further pairs of levels if so.
 // The Fisher-Yates pass takes the final segments from the boundary bitmap in batches of 32 on
@@ -252,6 +255,10 @@ __global__ void __launch_bounds__(kRsThreads) rs_chunk_first_kernel(RsArgs a) {
 // positions themselves (nothing is read).
 template <typename E, bool kPerm>
 __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E *in, E *out) {
+  // elements up to 8 bytes: the chunk's rows are copied into shared memory (cp.async) while
+  // the chunk's bits and segments are set up
+  constexpr bool kStage = !kPerm && sizeof(E) <= 8u;
+  __shared__ __align__(16) E sdata[kStage ? kRsChunk : 1u];
   __shared__ uint32_t cw[kRsChunk / 32u];
   __shared__ uint32_t zw[kRsChunk / 32u];
   __shared__ uint4 sg[kRsSegCap];  // (s, e, z, Z_s)
@@ -262,6 +269,21 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
   for (uint32_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
     const uint64_t c0 = static_cast<uint64_t>(ch) * kRsChunk;
     const uint64_t c1 = min(c0 + kRsChunk, a.n);
+    if constexpr (kStage) {
+      const uint32_t cnt = static_cast<uint32_t>(c1 - c0);
+      const E *const src = in + c0;
+      uint32_t i0 = 0;
+      if ((reinterpret_cast<uintptr_t>(in) & 15u) == 0u) {
+        constexpr uint32_t kPer = 16u / sizeof(E);
+        const uint32_t nv = cnt / kPer;
+        for (uint32_t i = tid; i < nv; i += kRsThreads)
+          cp_async_elem(reinterpret_cast<uint4 *>(sdata) + i,
+                        reinterpret_cast<const uint4 *>(src) + i);
+        i0 = nv * kPer;
+      }
+      for (uint32_t i = i0 + tid; i < cnt; i += kRsThreads) cp_async_elem(sdata + i, src + i);
+      cp_async_commit();
+    }
     if (tid < 32u) {
       const uint4 c = rs_block(a.key, a.level, ch * kRsChunkBlocks + lane);
       cw[4u * lane + 0u] = c.x;
@@ -298,6 +320,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
             sg[j] = make_uint4(e.x, e.y, e.x - Zs, a.zseg[k + j] + Zs);
           }
         }
+        if constexpr (kStage) cp_async_wait<0>();  // (the chunk's rows, before the barrier)
         const uint32_t got = static_cast<uint32_t>(__syncthreads_count(in_chunk));
         m += got;
         if (got < kRsThreads) break;  // (uniform: every thread sees the same count)
@@ -322,6 +345,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
           const uint32_t p = p0 + u * kRsThreads;
           if (o0 + u * kRsThreads < span) {
             if constexpr (kPerm) v[u] = static_cast<E>(p);
+            else if constexpr (kStage) v[u] = sdata[p - cbase];
             else v[u] = in[p];
           }
         }
@@ -613,7 +637,9 @@ int sm_count() {
 template <typename E>
 cudaError_t rs_launch_split(const RsArgs &a, const void *in, void *out, bool perm, int sms,
                             cudaStream_t s) {
-  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(a.nchunks, 8ull * sms));
+  // one CTA a chunk: the hardware balances the chunks over the SMs
+  (void)sms;
+  const unsigned grid = a.nchunks;
   if constexpr (sizeof(E) == 4) {
     if (perm) {
       rs_split_kernel<E, true><<<grid, kRsThreads, 0, s>>>(a, static_cast<const E *>(in),

@@ -74,6 +74,30 @@ def test_rs_shuffle_widths_match_oracle(w, n, B):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("w", [4, 8])
+def test_rs_shuffle_of_a_buffer_not_16_byte_aligned(w):
+    """The split passes copy a chunk's rows into shared memory 16 bytes at a time when the
+    source allows it and an element at a time otherwise: the caller's buffer starts w bytes past
+    a 16-byte boundary, the workspace is 256-byte aligned, so the levels alternate the two."""
+    torch = _torch()
+    n, B, seed = 300_007, 64, 21
+    rng = np.random.default_rng(w)
+    arr = rng.integers(0, 2**32, size=(n, w // 4), dtype=np.uint32)
+    want, _ = oracle.rs_shuffle(arr, seed, B)
+    big = torch.from_numpy(np.concatenate([np.zeros(w // 4, np.uint32), arr.reshape(-1)])
+                           .view(np.int32)).to("cuda")
+    assert big.data_ptr() % 16 == 0
+    ptr = big.data_ptr() + w
+    nbytes = ms.ms_rs_workspace_bytes(n, w, B)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_rs_shuffle(ptr, n, w, seed, B, ws.data_ptr(), nbytes,
+                          torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    got = big.cpu().numpy().view(np.uint32)[w // 4:].reshape(n, w // 4)
+    assert np.array_equal(got, want)
+
+
 def test_rs_shuffle_is_the_input_gathered_by_the_perm():
     n, B, seed = 2_000_003, 512, 77
     perm = _gpu_rs_perm(n, seed, B)
