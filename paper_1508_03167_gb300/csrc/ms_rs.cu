@@ -378,15 +378,16 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 
 // Algorithm 1 on every final segment (at most B elements each; a segment starts at every set
 // bit of the boundary bitmap and ends at the next one, or at n). CTAs of eight warps walk
-// windows of kRsFyWinWords bitmap words; warp 0 collects a window's segment starts, in order,
-// into a shared list. Each batch of `lanes` segments (segment k of the batch on lane k) then
+// windows of kRsFyWinWords bitmap words; the eight warps read 256 of them at a time and add
+// their segment starts, in order, to a shared list. Each batch of `lanes` segments (segment k of the batch on lane k) then
 // runs in three phases on 16-bit local indices in shared memory (stride P = 2 mod 64: the lanes'
 // entries at one index sit in distinct banks):
 //   draws   all eight warps (warp w: quads w, w + 8, ... of every segment) write the identity
 //           and the draw of every position i >= 1 of stream (5, 0, s, i); a draw whose first
 //           Philox word rejects every slice is queued by its thread and finished after the loop;
-//   swaps   warp 0 runs each segment's chain i = L-1 .. 1 (one lane a segment, the draws read
-//           four steps ahead);
+//   swaps   warp 0 runs each segment's chain i = L-1 .. 1 (one lane a segment), four steps
+//           at a time: their eight reads together, values forwarded between the four in
+//           registers, then their writes in the chain's order;
 //   write   a warp per segment: out[s + i] = in[s + idx[i]], eight loads a lane in flight.
 constexpr uint32_t kRsFyWinWords = 1024u;
 constexpr uint32_t kRsFyWarps = 8u;
@@ -478,14 +479,32 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
     const uint16_t *const D = Dbuf + lane * P;
     uint32_t i = L;
     while (i >= 5u) {
-      const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
-      const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
-      const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
-      const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
-      rs_swap16(A, i - 1u, j0);
-      rs_swap16(A, i - 2u, j1);
-      rs_swap16(A, i - 3u, j2);
-      rs_swap16(A, i - 4u, j3);
+      // steps k0 > k1 > k2 > k3 with targets j_m <= k_m: the eight reads of the group are made
+      // together, then each step takes its two values from the group's earlier writes to its
+      // targets where there were any (the later write wins), and the writes go out in the
+      // chain's order. Positions above a step are never a later target, so only the targets
+      // j0..j2 can forward.
+      const uint32_t k0 = i - 1u, k1 = i - 2u, k2 = i - 3u, k3 = i - 4u;
+      const uint32_t j0 = min(static_cast<uint32_t>(D[k0]), k0);
+      const uint32_t j1 = min(static_cast<uint32_t>(D[k1]), k1);
+      const uint32_t j2 = min(static_cast<uint32_t>(D[k2]), k2);
+      const uint32_t j3 = min(static_cast<uint32_t>(D[k3]), k3);
+      const uint32_t c0 = A[k0], c1 = A[k1], c2 = A[k2], c3 = A[k3];
+      const uint32_t v0 = A[j0], v1 = A[j1], v2 = A[j2], v3 = A[j3];
+      const uint32_t x1 = k1 == j0 ? c0 : c1;
+      const uint32_t y1 = j1 == j0 ? c0 : v1;
+      const uint32_t x2 = k2 == j1 ? x1 : (k2 == j0 ? c0 : c2);
+      const uint32_t y2 = j2 == j1 ? x1 : (j2 == j0 ? c0 : v2);
+      const uint32_t x3 = k3 == j2 ? x2 : (k3 == j1 ? x1 : (k3 == j0 ? c0 : c3));
+      const uint32_t y3 = j3 == j2 ? x2 : (j3 == j1 ? x1 : (j3 == j0 ? c0 : v3));
+      A[k0] = static_cast<uint16_t>(v0);
+      A[j0] = static_cast<uint16_t>(c0);
+      A[k1] = static_cast<uint16_t>(y1);
+      A[j1] = static_cast<uint16_t>(x1);
+      A[k2] = static_cast<uint16_t>(y2);
+      A[j2] = static_cast<uint16_t>(x2);
+      A[k3] = static_cast<uint16_t>(y3);
+      A[j3] = static_cast<uint16_t>(x3);
       i -= 4u;
     }
     for (; i >= 2u; --i) rs_swap16(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
@@ -514,7 +533,7 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
 }
 
 template <typename E>
-__global__ void __launch_bounds__(kRsFyThreads) rs_fy_kernel(const E *in, E *out, uint64_t n,
+__global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *out, uint64_t n,
                                                             uint2 key, const uint32_t *bnd,
                                                             uint32_t P, uint32_t lanes) {
   extern __shared__ __align__(16) uint16_t fy_smem[];
@@ -530,33 +549,39 @@ __global__ void __launch_bounds__(kRsFyThreads) rs_fy_kernel(const E *in, E *out
   for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * kRsFyWinWords; w0 < nwords;
        w0 += static_cast<uint64_t>(gridDim.x) * kRsFyWinWords) {
     uint32_t cnt = 0;  // starts waiting in the list (the same in every thread)
-    for (uint32_t cw = 0; cw < kRsFyWinWords && w0 + cw < nwords; cw += 32u) {
-      if (warp == 0u) {
-        const uint64_t wi = w0 + cw + lane;
-        uint32_t word = wi < nwords ? bnd[wi] : 0u;
-        const uint32_t c = static_cast<uint32_t>(__popc(word));
-        const uint32_t incl = warp_inclusive_scan(c);
-        uint32_t pos = cnt + incl - c;
-        while (word) {
-          list[pos++] = static_cast<uint32_t>(wi << 5) +
-                        static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
-          word &= word - 1u;
-        }
-        if (lane == 31u) s_cnt = cnt + incl;
-      }
-      __syncthreads();
-      cnt = s_cnt;
-      while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
-        rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
-        if (warp == 0u) {
-          for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
-            const uint32_t v = list[i + lanes];
-            __syncwarp(__activemask());
-            list[i] = v;
+    for (uint32_t cw0 = 0; cw0 < kRsFyWinWords && w0 + cw0 < nwords; cw0 += 32u * kRsFyWarps) {
+      // every warp reads one group of 32 bitmap words, so eight reads are in flight at once;
+      // the groups then join the list in order, warp g emitting group g
+      const uint64_t wi = w0 + cw0 + 32u * warp + lane;
+      const uint32_t grp = (cw0 + 32u * warp < kRsFyWinWords && wi < nwords) ? bnd[wi] : 0u;
+      for (uint32_t g = 0; g < kRsFyWarps; ++g) {
+        if (cw0 + 32u * g >= kRsFyWinWords || w0 + cw0 + 32u * g >= nwords) break;  // (uniform)
+        if (warp == g) {
+          uint32_t word = grp;
+          const uint32_t c = static_cast<uint32_t>(__popc(word));
+          const uint32_t incl = warp_inclusive_scan(c);
+          uint32_t pos = cnt + incl - c;
+          while (word) {
+            list[pos++] = static_cast<uint32_t>(wi << 5) +
+                          static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
+            word &= word - 1u;
           }
+          if (lane == 31u) s_cnt = cnt + incl;
         }
         __syncthreads();
-        cnt -= lanes;
+        cnt = s_cnt;
+        while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
+          rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
+          if (warp == 0u) {
+            for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
+              const uint32_t v = list[i + lanes];
+              __syncwarp(__activemask());
+              list[i] = v;
+            }
+          }
+          __syncthreads();
+          cnt -= lanes;
+        }
       }
     }
     if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, cnt, Abuf, Dbuf, F, sS, sL);
