@@ -316,12 +316,6 @@ __device__ __forceinline__ uint32_t fy8_draw(uint2 key, uint32_t id, uint32_t po
   }
 }
 
-__device__ __forceinline__ void swap16(uint16_t *A, uint32_t i, uint32_t j) {
-  const uint16_t t = A[i];
-  A[i] = A[j];
-  A[j] = t;
-}
-
 template <typename E, bool kPerm, bool kFdr>
 __global__ void __launch_bounds__(kFdrThreads) fy8_kernel(const E *in, E *out, uint64_t n,
                                                          uint32_t c, uint2 key, uint32_t P,
@@ -387,26 +381,14 @@ __global__ void __launch_bounds__(kFdrThreads) fy8_kernel(const E *in, E *out, u
       }
     }
     __syncthreads();
-    // swaps, i = L-1 .. 1 (the draws are read four ahead of the chain and clamped to the block)
+    // swaps, i = L-1 .. 1, four steps a group (the draws clamped to the block)
     if (warp == 0u && lane < kb) {
       const uint64_t k = k0 + lane;
       const uint32_t L = min(static_cast<uint32_t>(boundary(n, c, k + 1) - boundary(n, c, k)),
                              P - 2u);
       uint16_t *const A = Abuf + lane * P;
       const uint16_t *const D = Dbuf + lane * P;
-      uint32_t i = L;
-      while (i >= 5u) {
-        const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
-        const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
-        const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
-        const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
-        swap16(A, i - 1u, j0);
-        swap16(A, i - 2u, j1);
-        swap16(A, i - 3u, j2);
-        swap16(A, i - 4u, j3);
-        i -= 4u;
-      }
-      for (; i >= 2u; --i) swap16(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+      fy_chain16(A, D, L);
     }
     __syncthreads();
     // the blocks through their indices, a warp per block

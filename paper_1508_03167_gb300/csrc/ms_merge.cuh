@@ -45,6 +45,41 @@ __device__ __forceinline__ void swap_smem(E *a, uint32_t i, uint32_t j) {
   a[j] = t;
 }
 
+// Algorithm 1's swap chain on 16-bit local indices: for i = L-1 down to 1, swap A[i] with
+// A[D[i]] (each draw D[i] in [0, i], clamped into it). Four steps k0 > k1 > k2 > k3 at a time:
+// their eight reads are made together, then each step takes its two values from the group's
+// earlier writes to its targets where there were any (the later write wins), and the writes go
+// out in the chain's order, so a group waits for one shared-memory read rather than four.
+// Positions above a step are never a later step's target, so only the targets j0..j2 forward.
+__device__ __forceinline__ void fy_chain16(uint16_t *A, const uint16_t *D, uint32_t L) {
+  uint32_t i = L;
+  while (i >= 5u) {
+    const uint32_t k0 = i - 1u, k1 = i - 2u, k2 = i - 3u, k3 = i - 4u;
+    const uint32_t j0 = min(static_cast<uint32_t>(D[k0]), k0);
+    const uint32_t j1 = min(static_cast<uint32_t>(D[k1]), k1);
+    const uint32_t j2 = min(static_cast<uint32_t>(D[k2]), k2);
+    const uint32_t j3 = min(static_cast<uint32_t>(D[k3]), k3);
+    const uint32_t c0 = A[k0], c1 = A[k1], c2 = A[k2], c3 = A[k3];
+    const uint32_t v0 = A[j0], v1 = A[j1], v2 = A[j2], v3 = A[j3];
+    const uint32_t x1 = k1 == j0 ? c0 : c1;
+    const uint32_t y1 = j1 == j0 ? c0 : v1;
+    const uint32_t x2 = k2 == j1 ? x1 : (k2 == j0 ? c0 : c2);
+    const uint32_t y2 = j2 == j1 ? x1 : (j2 == j0 ? c0 : v2);
+    const uint32_t x3 = k3 == j2 ? x2 : (k3 == j1 ? x1 : (k3 == j0 ? c0 : c3));
+    const uint32_t y3 = j3 == j2 ? x2 : (j3 == j1 ? x1 : (j3 == j0 ? c0 : v3));
+    A[k0] = static_cast<uint16_t>(v0);
+    A[j0] = static_cast<uint16_t>(c0);
+    A[k1] = static_cast<uint16_t>(y1);
+    A[j1] = static_cast<uint16_t>(x1);
+    A[k2] = static_cast<uint16_t>(y2);
+    A[j2] = static_cast<uint16_t>(x2);
+    A[k3] = static_cast<uint16_t>(y3);
+    A[j3] = static_cast<uint16_t>(x3);
+    i -= 4u;
+  }
+  for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+}
+
 // Rejection draw in [0, R) from the slices of one word (R >= 2); false if every slice rejects.
 __device__ __forceinline__ bool draw_from_word(uint32_t word, uint32_t R, uint32_t &x) {
   const uint32_t b = 32u - __clz(R - 1u);

@@ -394,12 +394,6 @@ constexpr uint32_t kRsFyWarps = 8u;
 constexpr uint32_t kRsFyThreads = 32u * kRsFyWarps;
 constexpr uint32_t kRsFyFail = 8u;  // queued second-word draws a thread
 
-__device__ __forceinline__ void rs_swap16(uint16_t *A, uint32_t i, uint32_t j) {
-  const uint16_t t = A[i];
-  A[i] = A[j];
-  A[j] = t;
-}
-
 // One batch: the first kb starts of the list (cnt starts are waiting; the segment of start k
 // ends at start k + 1, else at the next set bit of the bitmap).
 template <typename E>
@@ -472,42 +466,12 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
     }
   }
   __syncthreads();
-  // swaps, i = L-1 .. 1 (the draws are read four ahead of the chain and clamped to the segment)
+  // swaps, i = L-1 .. 1, four steps a group (the draws clamped to the segment)
   if (warp == 0u && lane < kb) {
     const uint32_t L = sL[lane];
     uint16_t *const A = Abuf + lane * P;
     const uint16_t *const D = Dbuf + lane * P;
-    uint32_t i = L;
-    while (i >= 5u) {
-      // steps k0 > k1 > k2 > k3 with targets j_m <= k_m: the eight reads of the group are made
-      // together, then each step takes its two values from the group's earlier writes to its
-      // targets where there were any (the later write wins), and the writes go out in the
-      // chain's order. Positions above a step are never a later target, so only the targets
-      // j0..j2 can forward.
-      const uint32_t k0 = i - 1u, k1 = i - 2u, k2 = i - 3u, k3 = i - 4u;
-      const uint32_t j0 = min(static_cast<uint32_t>(D[k0]), k0);
-      const uint32_t j1 = min(static_cast<uint32_t>(D[k1]), k1);
-      const uint32_t j2 = min(static_cast<uint32_t>(D[k2]), k2);
-      const uint32_t j3 = min(static_cast<uint32_t>(D[k3]), k3);
-      const uint32_t c0 = A[k0], c1 = A[k1], c2 = A[k2], c3 = A[k3];
-      const uint32_t v0 = A[j0], v1 = A[j1], v2 = A[j2], v3 = A[j3];
-      const uint32_t x1 = k1 == j0 ? c0 : c1;
-      const uint32_t y1 = j1 == j0 ? c0 : v1;
-      const uint32_t x2 = k2 == j1 ? x1 : (k2 == j0 ? c0 : c2);
-      const uint32_t y2 = j2 == j1 ? x1 : (j2 == j0 ? c0 : v2);
-      const uint32_t x3 = k3 == j2 ? x2 : (k3 == j1 ? x1 : (k3 == j0 ? c0 : c3));
-      const uint32_t y3 = j3 == j2 ? x2 : (j3 == j1 ? x1 : (j3 == j0 ? c0 : v3));
-      A[k0] = static_cast<uint16_t>(v0);
-      A[j0] = static_cast<uint16_t>(c0);
-      A[k1] = static_cast<uint16_t>(y1);
-      A[j1] = static_cast<uint16_t>(x1);
-      A[k2] = static_cast<uint16_t>(y2);
-      A[j2] = static_cast<uint16_t>(x2);
-      A[k3] = static_cast<uint16_t>(y3);
-      A[j3] = static_cast<uint16_t>(x3);
-      i -= 4u;
-    }
-    for (; i >= 2u; --i) rs_swap16(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+    fy_chain16(A, D, L);
   }
   __syncthreads();
   // the batch's rows through the indices, a warp per segment

@@ -303,27 +303,15 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) tile_kernel(Tile
     }
     __syncthreads();
 
-    // ---- Algorithm 1's swaps, i = L-1 .. 1 (blocks 0..31: the data warp, 32..63: a helper; the
-    // draws are read four ahead of the chain and clamped to the block); meanwhile the control
-    // warp builds level 0's control data
+    // ---- Algorithm 1's swaps, i = L-1 .. 1 (blocks 0..31: the data warp, 32..63: a helper;
+    // four steps a group, the draws clamped to the block); meanwhile the control warp builds
+    // level 0's control data
     if (role == 0u || role == 2u) {
       const uint32_t k = (role == 0u ? 0u : 32u) + lane;
       const uint32_t L = k < nb ? boff[k + 1u] - boff[k] : 0u;
       uint16_t *const A = bufA + k * a.P;
       const uint16_t *const D = bufB + k * a.P;
-      uint32_t i = L;
-      while (i >= 5u) {
-        const uint32_t j0 = min(static_cast<uint32_t>(D[i - 1u]), i - 1u);
-        const uint32_t j1 = min(static_cast<uint32_t>(D[i - 2u]), i - 2u);
-        const uint32_t j2 = min(static_cast<uint32_t>(D[i - 3u]), i - 3u);
-        const uint32_t j3 = min(static_cast<uint32_t>(D[i - 4u]), i - 4u);
-        swap_smem(A, i - 1u, j0);
-        swap_smem(A, i - 2u, j1);
-        swap_smem(A, i - 3u, j2);
-        swap_smem(A, i - 4u, j3);
-        i -= 4u;
-      }
-      for (; i >= 2u; --i) swap_smem(A, i - 1u, min(static_cast<uint32_t>(D[i - 1u]), i - 1u));
+      fy_chain16(A, D, L);
     } else {
       // the other roles (1 and 3 .. kTileWarps-1): level 0's control data (role 1), then its
       // tail draws
