@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 // Algorithm 1 on every final segment (at most B elements each; a segment starts at every set
 // bit of the boundary bitmap and ends at the next one, or at n). CTAs of eight warps walk
 // windows of kRsFyWinWords bitmap words; the eight warps read 256 of them at a time and add
-// their segment starts, in order, to a shared list. Each batch of `lanes` segments (segment k of the batch on lane k) then
+// their segment starts, in order, to a shared list (all at once when they fit it). Each batch of `lanes` segments (segment k of the batch on lane k) then
 // runs in three phases on 16-bit local indices in shared memory (stride P = 2 mod 64: the lanes'
 // entries at one index sit in distinct banks):
 //   draws   all eight warps (warp w: quads w, w + 8, ... of every segment) write the identity
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *
                                                             uint2 key, const uint32_t *bnd,
                                                             uint32_t P, uint32_t lanes) {
   extern __shared__ __align__(16) uint16_t fy_smem[];
-  __shared__ uint32_t sS[32], sL[32], s_cnt;
+  __shared__ uint32_t sS[32], sL[32], s_wt[kRsFyWarps];
   uint16_t *const Abuf = fy_smem;
   uint16_t *const Dbuf = fy_smem + lanes * P;
   uint32_t *const list = reinterpret_cast<uint32_t *>(fy_smem + ((2u * lanes * P + 1u) & ~1u));
@@ -514,26 +514,38 @@ __global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *
        w0 += static_cast<uint64_t>(gridDim.x) * kRsFyWinWords) {
     uint32_t cnt = 0;  // starts waiting in the list (the same in every thread)
     for (uint32_t cw0 = 0; cw0 < kRsFyWinWords && w0 + cw0 < nwords; cw0 += 32u * kRsFyWarps) {
-      // every warp reads one group of 32 bitmap words, so eight reads are in flight at once;
-      // the groups then join the list in order, warp g emitting group g
+      // every warp reads one group of 32 bitmap words (eight reads in flight at once); groups
+      // past the window or the array read as empty
       const uint64_t wi = w0 + cw0 + 32u * warp + lane;
       const uint32_t grp = (cw0 + 32u * warp < kRsFyWinWords && wi < nwords) ? bnd[wi] : 0u;
+      const uint32_t c = static_cast<uint32_t>(__popc(grp));
+      const uint32_t incl = warp_inclusive_scan(c);
+      if (lane == 31u) s_wt[warp] = incl;
+      __syncthreads();
+      uint32_t base = 0, total = 0;
+#pragma unroll
       for (uint32_t g = 0; g < kRsFyWarps; ++g) {
-        if (cw0 + 32u * g >= kRsFyWinWords || w0 + cw0 + 32u * g >= nwords) break;  // (uniform)
-        if (warp == g) {
+        const uint32_t t = s_wt[g];
+        base += g < warp ? t : 0u;
+        total += t;
+      }
+      // if the starts of all eight groups fit the list, every warp adds its group's starts at
+      // once, behind the groups before it; otherwise (dense starts, small cutoffs) warp g adds
+      // group g in round g
+      const bool all = cnt + total <= lanes + 32u * 32u;
+      const uint32_t rounds = all ? 1u : kRsFyWarps;
+      for (uint32_t g = 0; g < rounds; ++g) {
+        if (all || warp == g) {
           uint32_t word = grp;
-          const uint32_t c = static_cast<uint32_t>(__popc(word));
-          const uint32_t incl = warp_inclusive_scan(c);
-          uint32_t pos = cnt + incl - c;
+          uint32_t pos = cnt + (all ? base : 0u) + incl - c;
           while (word) {
             list[pos++] = static_cast<uint32_t>(wi << 5) +
                           static_cast<uint32_t>(__ffs(static_cast<int>(word)) - 1);
             word &= word - 1u;
           }
-          if (lane == 31u) s_cnt = cnt + incl;
         }
         __syncthreads();
-        cnt = s_cnt;
+        cnt += all ? total : s_wt[g];
         while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
           rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
           if (warp == 0u) {
