@@ -21,9 +21,10 @@ table still resolves them so, so the digests stay tied to what the benchmark run
                  seed 7, B = 512: the comparison workload's perm
   max_perm       perm(2^32 - 1), seed 3, B = 511: the largest n the boundary takes (positions
                  near 2^32 exercise every 32-bit index of the GPU path)
+  rs_max         the splitting process on 2^32 - 1 positions, seed 5, B = 512
 
-Run:  python tests/golden/make_fullsize_digests.py [name ...]   (all rows: about 30 minutes on
-one core, ~34 GB RAM; with names, only those rows are recomputed and the others kept)
+Run:  python tests/golden/make_fullsize_digests.py [name ...]   (all rows: about an hour on one
+core, ~38 GB RAM; with names, only those rows are recomputed and the others kept)
 """
 from __future__ import annotations
 
@@ -60,6 +61,7 @@ C3_B = 256
 C4_B = 256
 RS = dict(name="rs_perm", n=1 << 30, w=4, seed=7, B=512)
 MAX = dict(name="max_perm", n=(1 << 32) - 1, w=4, seed=3, B=511)
+RS_MAX = dict(name="rs_max", n=(1 << 32) - 1, w=4, seed=5, B=512)
 
 
 def sha(a: np.ndarray) -> str:
@@ -119,10 +121,12 @@ def main(only: set[str]) -> None:
         emit(f"c4_u64_{i}", big[i], 8, 1 + i, C4_B, sha(out), time.time() - t)
         del out
 
-    if want(RS["name"]):
+    for cfg in (RS, RS_MAX):
+        if not want(cfg["name"]):
+            continue
         t = time.time()
-        out, _ = oracle.rs_perm(RS["n"], RS["seed"], RS["B"])
-        emit(RS["name"], RS["n"], 4, RS["seed"], RS["B"], sha(out), time.time() - t)
+        out, _ = oracle.rs_perm(cfg["n"], cfg["seed"], cfg["B"])
+        emit(cfg["name"], cfg["n"], 4, cfg["seed"], cfg["B"], sha(out), time.time() - t)
         del out
 
     with open(OUT, "w") as f:

@@ -182,3 +182,27 @@ def test_max_size_perm_digest():
     assert h.hexdigest() == g["digest"]
     del out
     torch.cuda.empty_cache()
+
+
+def test_rao_sandelius_max_size_digest():
+    """The splitting process on n = 2^32 - 1 positions (seed 5, cutoff 512): segment bounds,
+    chunk and bitmap indices of every split level and of the Fisher-Yates pass near 2^32. The
+    result is hashed from the device in 1 GiB slices."""
+    import torch
+
+    g = _digests()["rs_max"]
+    out = torch.empty(g["n"], dtype=torch.int32, device="cuda")
+    nbytes = ms.ms_rs_workspace_bytes(g["n"], 4, g["B"])
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = ms.ms_rs_perm(out.data_ptr(), g["n"], g["seed"], g["B"], ws.data_ptr(), nbytes,
+                       torch.cuda.current_stream().cuda_stream)
+    assert st == ms.MS_OK, ms.ms_status_string(st)
+    torch.cuda.synchronize()
+    del ws
+    h = hashlib.sha256()
+    step = 1 << 28
+    for i in range(0, g["n"], step):
+        h.update(out[i:i + step].cpu().numpy())
+    assert h.hexdigest() == g["digest"]
+    del out
+    torch.cuda.empty_cache()
