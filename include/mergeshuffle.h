@@ -347,7 +347,8 @@ ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *p, void *d_
  *   most B elements stay. Once none is above B, every segment [s, e) is shuffled by Algorithm 1
  *   with the uniform draws of stream (tag 5, level 0, id = s, pos = i) defined above.
  *   ms_rs_workspace_bytes  device workspace for (n, w, B): a second buffer of n*w bytes, the
- *                          per-level bit counts (n/128 + n/1024 bytes), two lists of active
+ *                          bit counts of every planned level (n/128 + n/1024 bytes a level,
+ *                          made at once before the first level) and of one more, two lists of active
  *                          segments (8 bytes each, at most n/(B+1)), 12 bytes of split data per
  *                          active segment and a bitmap of the segment starts (n/8 bytes);
  *                          0 for invalid arguments.

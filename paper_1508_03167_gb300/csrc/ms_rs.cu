@@ -12,7 +12,9 @@
 //
 // One split level is one streaming pass over the array (read n*w, write n*w):
 //   count   zeros among the bits of every 128-position block and 4096-position chunk (Philox
-//           only, no array traffic), then an exclusive scan of the chunk counts;
+//           only, no array traffic), then an exclusive scan of the chunk counts; the bits depend
+//           only on the seed and the positions, so the planned levels' counts are made by one
+//           launch and one scan before the first level;
 //   split   per active segment its zero count z (from the prefix) and its children: a child
 //           larger than B joins the next level's active list (an ordered compaction: count,
 //           single-CTA scan, write), and a split point s + z is marked in the boundary bitmap;
@@ -84,7 +86,7 @@ __device__ __forceinline__ uint32_t rs_block_zeros(const uint4 &c, uint64_t base
 // Z_p: zeros among the bits of positions [0, p), p <= n (after the chunk scan)
 __device__ uint32_t rs_zeros_before(const RsArgs &a, uint64_t p) {
   const uint64_t chunk = p / kRsChunk;
-  uint32_t Z = a.zc[chunk];
+  uint32_t Z = a.zc[chunk] - a.zc[0];
   if (chunk >= a.nchunks) return Z;
   const uint32_t blk_in = static_cast<uint32_t>((p / 128u) % kRsChunkBlocks);
   const uint8_t *zb = a.zb + chunk * kRsChunkBlocks;
@@ -113,6 +115,30 @@ __global__ void __launch_bounds__(kRsThreads) rs_count_kernel(RsArgs a) {
     a.zb[blk] = static_cast<uint8_t>(z);
     const uint32_t tot = warp_sum(z);
     if (lane == 0) a.zc[ch] = tot;
+  }
+}
+
+// the zero counts of every planned level at once (they depend on the seed and the positions
+// only): one warp per (level, chunk), one lane per block; level l's chunk counts go to
+// zca[l * (nchunks + 1) + chunk], with a zero after its last chunk, so that one exclusive scan
+// over all levels gives each level's prefix relative to its first entry (uint32 arithmetic
+// wraps consistently: a level's own prefixes stay below 2^32)
+__global__ void __launch_bounds__(kRsThreads) rs_count_all_kernel(RsArgs a, uint32_t levels,
+                                                                 uint32_t *zca, uint8_t *zba) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t f = (static_cast<uint64_t>(blockIdx.x) * kRsThreads + threadIdx.x) >> 5;
+  if (f >= static_cast<uint64_t>(levels) * a.nchunks) return;
+  const uint32_t l = static_cast<uint32_t>(f / a.nchunks);
+  const uint32_t ch = static_cast<uint32_t>(f - static_cast<uint64_t>(l) * a.nchunks);
+  const uint32_t blk = ch * kRsChunkBlocks + lane;
+  const uint4 c = rs_block(a.key, l, blk);
+  const uint32_t z = rs_block_zeros(c, 128ull * blk, a.n);
+  zba[(static_cast<uint64_t>(l) * a.nchunks) * kRsChunkBlocks + blk] = static_cast<uint8_t>(z);
+  const uint32_t tot = warp_sum(z);
+  uint32_t *const zl = zca + static_cast<uint64_t>(l) * (a.nchunks + 1u);
+  if (lane == 0) {
+    zl[ch] = tot;
+    if (ch == 0) zl[a.nchunks] = 0u;
   }
 }
 
@@ -302,7 +328,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
     }
     if (tid == 0) s_first = a.cfirst[ch];
     __syncthreads();
-    const uint32_t Zc = a.zc[ch];
+    const uint32_t Zc = a.zc[ch] - a.zc[0];
     uint32_t k = s_first;
     uint64_t span_lo = c0;
     for (;;) {
@@ -590,14 +616,28 @@ size_t up256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 // their counts, the per-segment split data, and the boundary bitmap.
 struct RsLayout {
   uint32_t nchunks = 0, maxact = 0;
-  size_t buf = 0, zc = 0, zb = 0, act0 = 0, act1 = 0, ctl = 0, zseg = 0, zs = 0, cnt = 0,
-         bnd = 0, tsum = 0, cfirst = 0, total = 0;
+  uint32_t plevels = 0;
+  size_t buf = 0, zc = 0, zb = 0, zca = 0, zba = 0, act0 = 0, act1 = 0, ctl = 0, zseg = 0,
+         zs = 0, cnt = 0, bnd = 0, tsum = 0, cfirst = 0, total = 0;
 };
+
+// planned split levels: c + 1 (segments then average at most B/2, so one above B is rare),
+// made odd so that the last one writes the workspace buffer
+uint32_t rs_planned_levels(uint64_t n, uint32_t B) {
+  if (n <= B) return 0u;
+  uint32_t c = 0;
+  while ((n >> c) > B) ++c;
+  uint32_t levels = c + 1u;
+  if (levels % 2u == 0u) ++levels;
+  return levels;
+}
 
 RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   RsLayout L;
   L.nchunks = static_cast<uint32_t>((n + kRsChunk - 1u) / kRsChunk);
   L.maxact = static_cast<uint32_t>(n / (static_cast<uint64_t>(B) + 1u) + 2u);
+  L.plevels = rs_planned_levels(n, B);
+  const uint64_t nall = static_cast<uint64_t>(L.plevels) * (L.nchunks + 1ull);
   size_t off = 0;
   L.buf = off;
   off += up256(n * w);
@@ -605,6 +645,10 @@ RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   off += up256((L.nchunks + 1ull) * 4u);
   L.zb = off;
   off += up256(static_cast<size_t>(L.nchunks) * kRsChunkBlocks);
+  L.zca = off;
+  off += up256(nall * 4u);
+  L.zba = off;
+  off += up256(static_cast<size_t>(L.plevels) * L.nchunks * kRsChunkBlocks);
   L.act0 = off;
   off += up256(L.maxact * 8ull);
   L.act1 = off;
@@ -620,7 +664,8 @@ RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   L.bnd = off;
   off += up256(((n + 31u) / 32u + 1u) * 4u);
   L.tsum = off;
-  off += up256((std::max<uint64_t>(L.maxact, L.nchunks) / kRsScanTile + 2u) * 4u);
+  off += up256((std::max<uint64_t>(std::max<uint64_t>(L.maxact, L.nchunks), nall) / kRsScanTile +
+                 2u) * 4u);
   L.cfirst = off;
   off += up256(L.nchunks * 4ull);
   L.total = off;
@@ -653,10 +698,10 @@ cudaError_t rs_launch_split(const RsArgs &a, const void *in, void *out, bool per
   return cudaGetLastError();
 }
 
-// one split level: bit counts and their scan, the segments' splits and the next active list,
-// then the data pass from `in` to `out`
+// one split level: bit counts and their scan (unless the planned levels' were made at once),
+// the segments' splits and the next active list, then the data pass from `in` to `out`
 cudaError_t rs_level(RsArgs a, uint32_t maxact, const void *in, void *out, uint32_t w,
-                     bool perm, int sms, cudaStream_t s) {
+                     bool perm, bool counted, int sms, cudaStream_t s) {
   const unsigned g_chunks =
       static_cast<unsigned>(std::min<uint64_t>((a.nchunks * 32ull + kRsThreads - 1) / kRsThreads,
                                                8ull * sms));
@@ -664,12 +709,14 @@ cudaError_t rs_level(RsArgs a, uint32_t maxact, const void *in, void *out, uint3
       std::min<uint64_t>((maxact + kRsThreads - 1ull) / kRsThreads, 8ull * sms));
   const unsigned g_tiles = static_cast<unsigned>(std::min<uint64_t>(
       (std::max<uint64_t>(maxact, a.nchunks) + kRsScanTile - 1u) / kRsScanTile, 8ull * sms));
-  rs_count_kernel<<<g_chunks, kRsThreads, 0, s>>>(a);
-  // exclusive prefix of the chunk zeros (the total after the last chunk)
-  rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
-  rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, nullptr, a.nchunks,
-                                                    a.zc + a.nchunks);
-  rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
+  if (!counted) {
+    rs_count_kernel<<<g_chunks, kRsThreads, 0, s>>>(a);
+    // exclusive prefix of the chunk zeros (the total after the last chunk)
+    rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
+    rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, nullptr, a.nchunks,
+                                                      a.zc + a.nchunks);
+    rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.zc, nullptr, a.nchunks, a.tsum);
+  }
   rs_children_kernel<<<g_segs, kRsThreads, 0, s>>>(a);
   // the next active list: exclusive prefix of the children kept, its total is the list size
   rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(a.cnt, a.act_n, 0u, a.tsum);
@@ -763,14 +810,21 @@ ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, u
     return MS_ERR_CUDA;
   rs_init_kernel<<<1, 32, 0, s>>>(a, act[0], ctl);
   if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
-  // planned levels: c + 1 (segments then average at most B/2, so one above B is rare), made
-  // odd so that the last one writes W
-  uint32_t levels = 0;
-  if (n > B) {
-    uint32_t c = 0;
-    while ((n >> c) > B) ++c;
-    levels = c + 1u;
-    if (levels % 2u == 0u) ++levels;
+  const uint32_t levels = L.plevels;
+  uint32_t *const zca = reinterpret_cast<uint32_t *>(base + L.zca);
+  uint8_t *const zba = reinterpret_cast<uint8_t *>(base + L.zba);
+  if (levels > 0) {
+    // the planned levels' zero counts, then one exclusive scan over all of them
+    const uint64_t warps = static_cast<uint64_t>(levels) * L.nchunks;
+    const uint32_t nall = levels * (L.nchunks + 1u);
+    const unsigned g_tiles = static_cast<unsigned>(
+        std::min<uint64_t>((nall + kRsScanTile - 1u) / kRsScanTile, 8ull * sms));
+    rs_count_all_kernel<<<static_cast<unsigned>((warps * 32u + kRsThreads - 1u) / kRsThreads),
+                          kRsThreads, 0, s>>>(a, levels, zca, zba);
+    rs_scan_reduce_kernel<<<g_tiles, kRsThreads, 0, s>>>(zca, nullptr, nall, a.tsum);
+    rs_scan_tiles_kernel<<<1, kRsScanThreads, 0, s>>>(a.tsum, nullptr, nall, ctl + 2);
+    rs_scan_down_kernel<<<g_tiles, kRsThreads, 0, s>>>(zca, nullptr, nall, a.tsum);
+    if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
   }
   uint32_t lv = 0;
   auto run_levels = [&](uint32_t upto) -> bool {
@@ -783,7 +837,13 @@ ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, u
       l.nxt_n = ctl + ((lv + 1u) % 2u);
       const void *in = (lv % 2u == 0u) ? data : W;
       void *out = (lv % 2u == 0u) ? W : data;
-      if (rs_failed(rs_level(l, L.maxact, in, out, w, perm && lv == 0u, sms, s))) return false;
+      const bool counted = lv < levels;
+      if (counted) {
+        l.zc = zca + static_cast<uint64_t>(lv) * (L.nchunks + 1u);
+        l.zb = zba + static_cast<uint64_t>(lv) * L.nchunks * kRsChunkBlocks;
+      }
+      if (rs_failed(rs_level(l, L.maxact, in, out, w, perm && lv == 0u, counted, sms, s)))
+        return false;
     }
     return true;
   };
