@@ -119,15 +119,31 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   }
   Zs -= zrun;  // zeros before word j0
   const uint32_t n2 = N - n1;
-  uint32_t T = N;
+  const uint32_t Z0 = Zs;
   for (uint32_t j = j0; j < j1; ++j) {
-    const uint32_t w = cz[j].x;
     cz[j].y = Zs;
-    const uint32_t Os = 32u * j - Zs;
-    const uint32_t zeros = static_cast<uint32_t>(__popc(~w));
-    if (Zs <= n1 && n1 < Zs + zeros) T = min(T, 32u * j + select_set_bit(~w, n1 - Zs));
-    if (Os <= n2 && n2 < Os + (32u - zeros)) T = min(T, 32u * j + select_set_bit(w, n2 - Os));
-    Zs += zeros;
+    Zs += static_cast<uint32_t>(__popc(~cz[j].x));
+  }
+  // the break step: the (n1+1)-th zero or the (n2+1)-th one, whichever comes first. A lane
+  // looks into its words only if its zero (one) ranks cover n1 (n2), at most two lanes a merge,
+  // and finds the word by a binary search over the stored prefixes (zeros before word j are
+  // cz[j].y, ones 32 j - cz[j].y, both non-decreasing in j)
+  uint32_t T = N;
+  auto find = [&](bool ones, uint32_t rank) -> uint32_t {
+    uint32_t lo = j0, hi = j1;  // the last word whose count before it is at most rank
+    while (hi - lo > 1u) {
+      const uint32_t mid = (lo + hi) >> 1;
+      const uint32_t before = ones ? 32u * mid - cz[mid].y : cz[mid].y;
+      if (before <= rank) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t w = cz[lo].x;
+    const uint32_t before = ones ? 32u * lo - cz[lo].y : cz[lo].y;
+    return 32u * lo + select_set_bit(ones ? w : ~w, rank - before);
+  };
+  if (j0 < j1) {
+    if (Z0 <= n1 && n1 < Zs) T = min(T, find(false, n1));
+    if (32u * j0 - Z0 <= n2 && n2 < 32u * j1 - Zs) T = min(T, find(true, n2));
   }
 #pragma unroll
   for (uint32_t o = 1; o < 32u; o <<= 1)
