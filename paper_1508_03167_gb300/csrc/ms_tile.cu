@@ -95,6 +95,7 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   uint2 *const cz = c.cz + woff;
   // coin words (one Philox block: four words, 128 steps)
   const uint32_t nblk = (Wm + 3u) >> 2;
+#pragma unroll 2
   for (uint32_t jb = sub; jb < nblk; jb += G) {
     const uint4 blk = coin_block(key, lv, idbase + r, jb);
     const uint32_t j = 4u * jb;
@@ -110,6 +111,7 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   const uint32_t C = (Wm + G - 1u) >> lgG;
   const uint32_t j0 = min(sub * C, Wm), j1 = min(j0 + C, Wm);
   uint32_t zrun = 0;
+#pragma unroll 4
   for (uint32_t j = j0; j < j1; ++j) zrun += static_cast<uint32_t>(__popc(~cz[j].x));
   uint32_t Zs = zrun;
 #pragma unroll
@@ -120,6 +122,7 @@ __device__ __noinline__ void level_setup(uint2 key, uint32_t d, uint32_t tcap,
   Zs -= zrun;  // zeros before word j0
   const uint32_t n2 = N - n1;
   const uint32_t Z0 = Zs;
+#pragma unroll 4
   for (uint32_t j = j0; j < j1; ++j) {
     cz[j].y = Zs;
     Zs += static_cast<uint32_t>(__popc(~cz[j].x));
