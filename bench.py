@@ -780,7 +780,9 @@ def run_rs(args, t_ms_mergeshuffle=None, steps: int = 5, warmup: int = 2) -> dic
     c = 0
     while (n >> c) > B:
         c += 1
-    levels = c + 1 + ((c + 1) % 2 == 0)
+    # the library plans c + 1 levels, made odd by one more unless the Fisher-Yates pass runs in
+    # place (4-byte rows, B <= 512)
+    levels = c + 1 + ((c + 1) % 2 == 0 and B > 512)
     # algorithmic bytes: the first split level only writes (4n), every other split level and the
     # Fisher-Yates pass read and write the array
     nb = 4 * n + (levels - 1) * 8 * n + 8 * n

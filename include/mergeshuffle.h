@@ -356,8 +356,9 @@ ms_status ms_random_bits(uint64_t n, uint64_t seed, const ms_params *p, void *d_
  *                          1 <= B <= MS_MAX_B, n <= 2^32 - 1, d_ws 256-byte aligned.
  *   ms_rs_perm             fill d_out[0..n) with the permutation ms_rs_shuffle applies to the
  *                          identity (the first level generates it instead of reading it).
- * Each split level is one pass over the array. The planned number of levels (c + 1 or c + 2,
- * odd, c = min{c : floor(n / 2^c) <= B}) leaves a segment above B only rarely for large B;
+ * Each split level is one pass over the array. The planned number of levels (c + 1, made odd
+ * by one more unless w = 4 and B <= 512, where the Fisher-Yates pass runs in place;
+ * c = min{c : floor(n / 2^c) <= B}) leaves a segment above B only rarely for large B;
  * the call then synchronises the stream once to read whether one is left, and runs further
  * pairs of levels if so (at most 4096 levels: MS_ERR_UNSUPPORTED beyond). So unlike ms_shuffle
  * these calls wait for their stream and cannot be captured into a CUDA graph.

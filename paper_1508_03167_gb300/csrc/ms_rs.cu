@@ -23,8 +23,9 @@
 //           One CTA takes one chunk (the hardware balances the chunks over the SMs); for
 //           elements up to 8 bytes it copies the chunk's rows into shared memory (cp.async)
 //           while it sets up the chunk's bits and segments.
-// After the planned levels (an odd number, so that the last one writes the workspace buffer)
-// the host reads whether a segment above B is left and runs further pairs of levels if so.
+// After the planned levels (c + 1; made odd, so that the last one writes the workspace buffer,
+// unless the Fisher-Yates pass can run in place: 4-byte rows, B <= 512) the host reads whether
+// a segment above B is left and runs further pairs of levels if so.
 // The Fisher-Yates pass takes the final segments from the boundary bitmap in batches of 32 on
 // eight-warp CTAs: all warps make the draws, one lane per segment runs its swap chain on 16-bit
 // local indices in shared memory, and a warp per segment writes it through them.
@@ -416,13 +417,14 @@ __global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E 
 //           registers, then their writes in the chain's order;
 //   write   a warp per segment: out[s + i] = in[s + idx[i]], eight loads a lane in flight.
 constexpr uint32_t kRsFyWinWords = 1024u;
+constexpr uint32_t kRsFyInPlaceMax = 512u;  // largest final segment the in-place pass takes
 constexpr uint32_t kRsFyWarps = 8u;
 constexpr uint32_t kRsFyThreads = 32u * kRsFyWarps;
 constexpr uint32_t kRsFyFail = 8u;  // queued second-word draws a thread
 
 // One batch: the first kb starts of the list (cnt starts are waiting; the segment of start k
 // ends at start k + 1, else at the next set bit of the bitmap).
-template <typename E>
+template <typename E, bool kInPlace>
 __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const uint32_t *bnd,
                             uint32_t P, const uint32_t *list, uint32_t kb, uint32_t cnt,
                             uint16_t *Abuf, uint16_t *Dbuf, uint16_t *F, uint32_t *sS,
@@ -501,6 +503,29 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
   }
   __syncthreads();
   // the batch's rows through the indices, a warp per segment
+  if constexpr (kInPlace) {
+    // in place (4-byte rows, segments of at most 512 = 16 x 32 rows): the warp reads the whole
+    // segment before it writes any of it back
+    constexpr uint32_t kRowsAll = kRsFyInPlaceMax / 32u;
+    for (uint32_t k = warp; k < kb; k += kRsFyWarps) {
+      const uint32_t s_pos = sS[k], L = sL[k];
+      const uint16_t *const A = Abuf + k * P;
+      E v[kRowsAll];
+#pragma unroll
+      for (uint32_t u = 0; u < kRowsAll; ++u) {
+        const uint32_t i = 32u * u + lane;
+        if (i < L) v[u] = in[static_cast<uint64_t>(s_pos) + min(static_cast<uint32_t>(A[i]), L - 1u)];
+      }
+      __syncwarp();
+#pragma unroll
+      for (uint32_t u = 0; u < kRowsAll; ++u) {
+        const uint32_t i = 32u * u + lane;
+        if (i < L) out[static_cast<uint64_t>(s_pos) + i] = v[u];
+      }
+    }
+    __syncthreads();
+    return;
+  }
   constexpr uint32_t kRows = sizeof(E) >= 16u ? 4u : 8u;
   for (uint32_t k = warp; k < kb; k += kRsFyWarps) {
     const uint32_t s_pos = sS[k], L = sL[k];
@@ -522,7 +547,7 @@ __device__ void rs_fy_batch(const E *in, E *out, uint64_t n, uint2 key, const ui
   __syncthreads();
 }
 
-template <typename E>
+template <typename E, bool kInPlace>
 __global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *out, uint64_t n,
                                                             uint2 key, const uint32_t *bnd,
                                                             uint32_t P, uint32_t lanes) {
@@ -573,7 +598,7 @@ __global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *
         __syncthreads();
         cnt += all ? total : s_wt[g];
         while (cnt > lanes) {  // (a full batch; the one after it supplies its last end)
-          rs_fy_batch<E>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
+          rs_fy_batch<E, kInPlace>(in, out, n, key, bnd, P, list, lanes, cnt, Abuf, Dbuf, F, sS, sL);
           if (warp == 0u) {
             for (uint32_t i = lane; i + lanes < cnt; i += 32u) {
               const uint32_t v = list[i + lanes];
@@ -586,7 +611,8 @@ __global__ void __launch_bounds__(kRsFyThreads, 3) rs_fy_kernel(const E *in, E *
         }
       }
     }
-    if (cnt) rs_fy_batch<E>(in, out, n, key, bnd, P, list, cnt, cnt, Abuf, Dbuf, F, sS, sL);
+    if (cnt) rs_fy_batch<E, kInPlace>(in, out, n, key, bnd, P, list, cnt, cnt, Abuf, Dbuf, F, sS,
+                                     sL);
   }
 }
 
@@ -621,14 +647,19 @@ struct RsLayout {
          zs = 0, cnt = 0, bnd = 0, tsum = 0, cfirst = 0, total = 0;
 };
 
-// planned split levels: c + 1 (segments then average at most B/2, so one above B is rare),
-// made odd so that the last one writes the workspace buffer
-uint32_t rs_planned_levels(uint64_t n, uint32_t B) {
+// whether the Fisher-Yates pass can run in place in the caller's buffer (4-byte rows, final
+// segments of at most kRsFyInPlaceMax rows)
+bool rs_fy_in_place(uint32_t w, uint32_t B) { return w == 4u && B <= kRsFyInPlaceMax; }
+
+// planned split levels: c + 1 (segments then average at most B/2, so one above B is rare);
+// unless the Fisher-Yates pass can run in place, made odd so that the last one writes the
+// workspace buffer
+uint32_t rs_planned_levels(uint64_t n, uint32_t w, uint32_t B) {
   if (n <= B) return 0u;
   uint32_t c = 0;
   while ((n >> c) > B) ++c;
   uint32_t levels = c + 1u;
-  if (levels % 2u == 0u) ++levels;
+  if (levels % 2u == 0u && !rs_fy_in_place(w, B)) ++levels;
   return levels;
 }
 
@@ -636,7 +667,7 @@ RsLayout rs_layout(uint64_t n, uint32_t w, uint32_t B) {
   RsLayout L;
   L.nchunks = static_cast<uint32_t>((n + kRsChunk - 1u) / kRsChunk);
   L.maxact = static_cast<uint32_t>(n / (static_cast<uint64_t>(B) + 1u) + 2u);
-  L.plevels = rs_planned_levels(n, B);
+  L.plevels = rs_planned_levels(n, w, B);
   const uint64_t nall = static_cast<uint64_t>(L.plevels) * (L.nchunks + 1ull);
   size_t off = 0;
   L.buf = off;
@@ -747,7 +778,13 @@ cudaError_t rs_launch_fy(const void *in, void *out, uint64_t n, uint2 key, const
   // bitmap words) and the threads' queues of second-word draws
   const size_t smem = ((2u * static_cast<size_t>(lanes) * P + 1u) & ~static_cast<size_t>(1u)) * 2u +
                       (lanes + 32u * 32u + 32u) * 4u + kRsFyThreads * kRsFyFail * 2u;
-  auto kern = rs_fy_kernel<E>;
+  // (in place only for 4-byte rows and final segments of at most kRsFyInPlaceMax: the planner
+  // gives an even number of levels only then)
+  if (in == out && (sizeof(E) != 4u || B > kRsFyInPlaceMax)) return cudaErrorInvalidValue;
+  auto kern = rs_fy_kernel<E, false>;
+  if constexpr (sizeof(E) == 4u) {
+    if (in == out) kern = rs_fy_kernel<E, true>;
+  }
   cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -859,20 +896,29 @@ ms_status rs_run(void *data, bool perm, uint64_t n, uint32_t w, uint64_t seed, u
       if (lv + 2u > 4096u) return MS_ERR_UNSUPPORTED;
       if (!run_levels(lv + 2u)) return MS_ERR_CUDA;
     }
-  } else if (perm) {
-    rs_iota_kernel<<<static_cast<unsigned>(std::min<uint64_t>((n + 255u) / 256u, 8ull * sms)),
-                     256, 0, s>>>(static_cast<uint32_t *>(W), n);
-    if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
-  } else if (rs_failed(cudaMemcpyAsync(W, data, n * w, cudaMemcpyDeviceToDevice, s))) {
-    return MS_ERR_CUDA;
   }
-  // the data now sits in W (an odd number of levels, or the copy above): Algorithm 1 on every
-  // final segment, from W into the caller's buffer
+  // the data sits in W after an odd number of levels, in the caller's buffer after an even
+  // number (the Fisher-Yates pass then runs in place); with no level at all it is the input
+  const bool in_place = rs_fy_in_place(w, B);
+  void *src = (lv % 2u == 1u) ? W : data;
+  if (levels == 0) {
+    void *dst0 = in_place ? data : W;
+    if (perm) {
+      rs_iota_kernel<<<static_cast<unsigned>(std::min<uint64_t>((n + 255u) / 256u, 8ull * sms)),
+                       256, 0, s>>>(static_cast<uint32_t *>(dst0), n);
+      if (rs_failed(cudaGetLastError())) return MS_ERR_CUDA;
+    } else if (!in_place &&
+               rs_failed(cudaMemcpyAsync(W, data, n * w, cudaMemcpyDeviceToDevice, s))) {
+      return MS_ERR_CUDA;
+    }
+    src = dst0;
+  }
+  // Algorithm 1 on every final segment, from src into the caller's buffer
   cudaError_t e;
   switch (w) {
-    case 4: e = rs_launch_fy<uint32_t>(W, data, n, a.key, a.bnd, B, sms, s); break;
-    case 8: e = rs_launch_fy<uint2>(W, data, n, a.key, a.bnd, B, sms, s); break;
-    default: e = rs_launch_fy<uint4>(W, data, n, a.key, a.bnd, B, sms, s); break;
+    case 4: e = rs_launch_fy<uint32_t>(src, data, n, a.key, a.bnd, B, sms, s); break;
+    case 8: e = rs_launch_fy<uint2>(src, data, n, a.key, a.bnd, B, sms, s); break;
+    default: e = rs_launch_fy<uint4>(src, data, n, a.key, a.bnd, B, sms, s); break;
   }
   return rs_failed(e) ? MS_ERR_CUDA : MS_OK;
 }
