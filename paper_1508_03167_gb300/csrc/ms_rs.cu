@@ -281,7 +281,9 @@ __global__ void __launch_bounds__(kRsThreads) rs_chunk_first_kernel(RsArgs a) {
 // segment's split, or stays if no active segment holds it. Level 0 of a perm writes the
 // positions themselves (nothing is read).
 template <typename E, bool kPerm>
-__global__ void __launch_bounds__(kRsThreads) rs_split_kernel(RsArgs a, const E *in, E *out) {
+// (4-byte rows: eight CTAs an SM, 32 registers, as the shared memory allows)
+__global__ void __launch_bounds__(kRsThreads, sizeof(E) == 4u ? 8 : (sizeof(E) == 8u ? 6 : 4))
+    rs_split_kernel(RsArgs a, const E *in, E *out) {
   // elements up to 8 bytes: the chunk's rows are copied into shared memory (cp.async) while
   // the chunk's bits and segments are set up
   constexpr bool kStage = !kPerm && sizeof(E) <= 8u;
